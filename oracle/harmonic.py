@@ -1,0 +1,124 @@
+"""Spin spherical-harmonic and Wigner transforms on MW sampling (oracle; test infrastructure only).
+
+Definitions followed
+--------------------
+* Forward spin SHT (Sec. 2.1, Eq. 2):  f_lm = int f(omega) sY*_lm(omega) dOmega, and the
+  inverse (Eq. 3): f = sum_lm f_lm sY_lm, band-limited at L.
+* Forward Wigner transform (Sec. 2.2, Eq. 4): F^l_mn = int f(rho) D^l_mn(rho) dOmega(rho)
+  (no conjugate), inverse (Eq. 5): f = sum (2l+1)/(8 pi^2) F^l_mn D^l*_mn.
+* D^l_mn(alpha, beta, gamma) = d^l_mn(beta) exp(-i(m alpha + n gamma)) (Sec. 5.2, Eq. 47).
+* sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) exp(i m phi) (the MW
+  convention; the paper is silent).  For s = 0 this is the Condon-Shortley Y_lm.
+
+Algorithm (McEwen-Wiaux, which the paper's benchmark sampling refers to; Sec. 4.4):
+the alpha/phi and gamma integrals are exact DFT sums over the equispaced samples
+(Eq. 48's "Fourier transform" factor); the colatitude integral of a band-limited
+column G(theta) against d^l_mn(theta) sin(theta) is done exactly by
+  (1) extending G to [0, 2 pi) with G(2 pi - theta) = (-1)^(m+n) G(theta) (the parity
+      of d^l_mn, since d^l_mn(-beta) = (-1)^(m-n) d^l_mn(beta)),
+  (2) taking its 2L-1 Fourier coefficients Ghat(p) from the 2L-1 extended samples,
+  (3) forming I(k) = int_0^pi G(theta) e^{i k theta} sin(theta) = sum_p Ghat(p) w(p + k)
+      with the closed-form weights w of ``sampling.sin_weight``,
+  (4) contracting with the Fourier coefficients of d^l_mn (``wigner.fourier_coeffs``).
+All DFTs are direct O(n^2) sums written as matrix products.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import sampling, wigner
+
+
+def _mrange(L):
+    return np.arange(-(L - 1), L)
+
+
+def _colatitude_integrals(G: np.ndarray, L: int, parity: np.ndarray) -> np.ndarray:
+    """I[k, col] = int_0^pi G_col(theta) exp(i k theta) sin(theta) d theta for |k| <= L-1.
+
+    G is [L, ncol] (samples on the L MW colatitudes); parity[col] = +-1 is the
+    reflection sign of the column's periodic extension.
+    """
+    ncol = G.shape[1]
+    Gext = np.zeros((2 * L - 1, ncol), dtype=np.complex128)
+    Gext[:L] = G
+    # theta_{2L-2-t} = 2 pi - theta_t for t = 0..L-2
+    Gext[L:] = parity[None, :] * G[L - 2::-1] if L > 1 else Gext[L:]
+    th = sampling.thetas_extended(L)
+    p = _mrange(L)
+    Fwd = np.exp(-1j * np.outer(p, th)) / (2 * L - 1)   # [p, u]
+    Ghat = Fwd @ Gext                                     # [p, col]
+    k = _mrange(L)
+    Wk = sampling.sin_weight(k[:, None] + p[None, :])     # [k, p]
+    return Wk @ Ghat
+
+
+def sht_inverse(flm: np.ndarray, L: int, spin: int = 0) -> np.ndarray:
+    """Inverse spin SHT (Eq. 3).  flm [L, 2L-1] -> f [L theta, 2L-1 phi] (complex)."""
+    ms = _mrange(L)
+    Cmk = np.zeros((2 * L - 1, 2 * L - 1), dtype=np.complex128)   # [m, k]
+    for l in range(abs(spin), L):
+        Cl = wigner.fourier_coeffs(l, [-spin])[:, 0, :]            # [m, k] for |m|,|k| <= l
+        norm = (-1.0) ** spin * np.sqrt((2 * l + 1) / (4 * np.pi))
+        sl = slice(L - 1 - l, L + l)
+        Cmk[sl, sl] += norm * flm[l, sl][:, None] * Cl
+    th = sampling.thetas(L)
+    G = Cmk @ np.exp(1j * np.outer(ms, th))                        # [m, t]
+    E = np.exp(1j * np.outer(ms, sampling.phis(L)))                 # [m, p]
+    return G.T @ E
+
+
+def sht_forward(f: np.ndarray, L: int, spin: int = 0) -> np.ndarray:
+    """Forward spin SHT (Eq. 2) of MW samples f [L, 2L-1] -> flm [L, 2L-1]."""
+    ms = _mrange(L)
+    E = np.exp(-1j * np.outer(sampling.phis(L), ms))                # [p, m]
+    G = (2 * np.pi / (2 * L - 1)) * (np.asarray(f, dtype=np.complex128) @ E)   # [t, m]
+    parity = (-1.0) ** ((ms + spin) % 2)
+    I = _colatitude_integrals(G, L, parity)                         # [k, m]
+    flm = np.zeros((L, 2 * L - 1), dtype=np.complex128)
+    for l in range(abs(spin), L):
+        Cl = wigner.fourier_coeffs(l, [-spin])[:, 0, :]             # [m, k]
+        sl = slice(L - 1 - l, L + l)
+        norm = (-1.0) ** spin * np.sqrt((2 * l + 1) / (4 * np.pi))
+        flm[l, sl] = norm * np.einsum('mk,km->m', Cl, I[sl, sl])
+    return flm
+
+
+def wigner_inverse(flmn: np.ndarray, L: int, N: int) -> np.ndarray:
+    """Inverse Wigner transform (Eq. 5).  flmn [2N-1, L, 2L-1] -> f [2N-1 gamma, L beta, 2L-1 alpha]."""
+    ms = _mrange(L)
+    ns = np.arange(-(N - 1), N)
+    Cnmk = np.zeros((2 * N - 1, 2 * L - 1, 2 * L - 1), dtype=np.complex128)   # [n, m, k]
+    for l in range(L):
+        Cl = wigner.fourier_coeffs(l, ns)                            # [m, n, k]
+        sl = slice(L - 1 - l, L + l)
+        coef = (2 * l + 1) / (8 * np.pi ** 2) * flmn[:, l, sl]       # [n, m]
+        Cnmk[:, sl, sl] += np.transpose(Cl, (1, 0, 2)) * coef[:, :, None]
+    betas = sampling.thetas(L)
+    G = Cnmk @ np.exp(1j * np.outer(ms, betas))                      # [n, m, b]
+    Ea = np.exp(1j * np.outer(ms, sampling.phis(L)))                  # [m, a]
+    Eg = np.exp(1j * np.outer(ns, sampling.gammas(N)))               # [n, g]
+    H = np.einsum('nmb,ma->nba', G, Ea)                              # alpha sum
+    return np.einsum('nba,ng->gba', H, Eg)                           # gamma sum
+
+
+def wigner_forward(f: np.ndarray, L: int, N: int) -> np.ndarray:
+    """Forward Wigner transform (Eq. 4) of MW SO(3) samples f [2N-1, L, 2L-1] -> flmn."""
+    ms = _mrange(L)
+    ns = np.arange(-(N - 1), N)
+    Ea = np.exp(-1j * np.outer(sampling.phis(L), ms))                # [a, m]
+    Eg = np.exp(-1j * np.outer(sampling.gammas(N), ns))              # [g, n]
+    f = np.asarray(f, dtype=np.complex128)
+    G = np.einsum('gba,am->gbm', f, Ea)
+    G = np.einsum('gbm,gn->nbm', G, Eg)
+    G *= (2 * np.pi / (2 * L - 1)) * (2 * np.pi / (2 * N - 1))      # [n, b, m]
+    parity = (-1.0) ** ((ms[None, :] + ns[:, None]) % 2)              # [n, m]
+    Gcols = np.transpose(G, (1, 0, 2)).reshape(L, -1)
+    I = _colatitude_integrals(Gcols, L, parity.reshape(-1))
+    I = I.reshape(2 * L - 1, 2 * N - 1, 2 * L - 1)                  # [k, n, m]
+    flmn = np.zeros((2 * N - 1, L, 2 * L - 1), dtype=np.complex128)
+    for l in range(L):
+        Cl = wigner.fourier_coeffs(l, ns)                            # [m, n, k]
+        sl = slice(L - 1 - l, L + l)
+        flmn[:, l, sl] = np.einsum('mnk,knm->nm', Cl, I[sl][:, :, sl])
+    return flmn
