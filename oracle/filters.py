@@ -5,7 +5,8 @@ Follows App. A of the paper:
 * s_lambda(t) = s(2 lambda/(lambda-1) (t - 1/lambda) - 1), support [1/lambda, 1] (Eq. A2);
 * k_lambda(t) = int_t^1 s_lambda(u)^2/u du / int_{1/lambda}^1 s_lambda(u)^2/u du (Eq. A4),
   equal to 1 for t <= 1/lambda and 0 for t >= 1;
-* kappa_lambda(t) = sqrt(k_lambda(t/lambda) - k_lambda(t)) (Eq. A5);
+* kappa_lambda(t) = sqrt(k_lambda(t/lambda) - k_lambda(t)) (Eq. A5), the difference evaluated as
+  the single integral of s_lambda^2/u over [t/lambda, t] (same quantity, no cancellation);
 * azimuthal tiling zeta_lm = xi mu sqrt(2^-q binom(q, (q-m)/2)) (Eq. A6) with xi = 1 for
   even N-1 and i otherwise, mu = [1 - (-1)^(N+m)]/2, q = min(N-1, l - [1 + (-1)^(N+l)]/2);
 * Psi^j_lm = sqrt((2l+1)/(8 pi^2)) kappa^j(l) zeta_lm (Eq. A9, radial factor dropped);
@@ -48,11 +49,14 @@ def _k_norm(lam: float) -> float:
     return _quad(1.0 / lam, lam)
 
 
-def _quad(t: float, lam: float) -> float:
-    # QUADPACK reports round-off once it reaches ~1e-16 absolute accuracy; that is the goal.
+def _quad(t: float, lam: float, upper: float = 1.0) -> float:
+    """int_t^upper s_lambda(u)^2/u du (QUADPACK; it reports round-off once it reaches ~1e-16
+    relative accuracy, which is the goal)."""
+    if upper <= t:
+        return 0.0
     with warnings.catch_warnings():
         warnings.simplefilter("ignore", integrate.IntegrationWarning)
-        val, _ = integrate.quad(_integrand, t, 1.0, args=(lam,), epsabs=0.0, epsrel=1.2e-14,
+        val, _ = integrate.quad(_integrand, t, upper, args=(lam,), epsabs=0.0, epsrel=1.2e-14,
                                 limit=500)
     return val
 
@@ -66,9 +70,19 @@ def k_lambda(t: float, lam: float) -> float:
     return _quad(t, lam) / _k_norm(lam)
 
 
+@lru_cache(maxsize=200000)
 def kappa_lambda(t: float, lam: float) -> float:
-    d = k_lambda(t / lam, lam) - k_lambda(t, lam)
-    return math.sqrt(d) if d > 0.0 else 0.0
+    """kappa_lambda(t) = sqrt(k_lambda(t/lambda) - k_lambda(t)) (Eq. A5).
+
+    With Eq. A4 the difference is one integral, int_{t/lambda}^{t} s_lambda(u)^2/u du over the
+    normalisation; it is evaluated that way so that values near the support edges keep their
+    relative precision (k(t/lambda) - k(t) computed as a difference of two numbers close to 1
+    underflows to 0 where the true value is ~1e-17)."""
+    a = max(t / lam, 1.0 / lam)
+    b = min(t, 1.0)
+    if b <= a:
+        return 0.0
+    return math.sqrt(_quad(a, lam, b) / _k_norm(lam))
 
 
 def eta_lambda(t: float, lam: float) -> float:

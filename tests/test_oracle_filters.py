@@ -70,3 +70,22 @@ def test_scales():
                                                         (6, 128, 8), (7, 256, 8), (8, 256, 8)]
     assert filters.scaling_bandlimit(256, 2.0, 2) == 4
     assert filters.scale_bandlimits(32, 4, 2.0, 0)[0] == (0, 2, 2)
+
+
+def test_kappa_near_support_edges():
+    """kappa^2 keeps full relative precision at the support edges (30-digit tanh-sinh pin),
+    where k(t/lambda) - k(t) as a difference of two numbers near 1 would round to 0."""
+    lam = 2.0
+    with mp.workdps(30):
+        def s(u):
+            return mp.exp(-1 / (1 - u * u)) if -1 < u < 1 else mp.mpf(0)
+
+        def f(u):
+            return s(2 * lam / (lam - 1) * (u - 1 / lam) - 1) ** 2 / u
+        norm = mp.quad(f, [1 / lam, 0.75, 1])
+        for l in [65, 66, 70, 100, 250, 255]:
+            t = l / 128.0
+            ref = float(mp.sqrt(mp.quad(f, [max(t / lam, 1 / lam), min(t, 1)]) / norm))
+            got = filters.kappa_lambda(t, lam)
+            # relative 1e-14, with an absolute floor far below what any output can resolve
+            assert abs(got - ref) <= 1e-14 * ref + 1e-18, (l, got, ref)
