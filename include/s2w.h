@@ -1,0 +1,163 @@
+/*
+ * s2w.h -- C ABI of the GB300 directional wavelet transform library (libs2w.so).
+ *
+ * The library computes the scale-discretised directional wavelet transform on the
+ * sphere (Sec. 3.1 and Algorithm 1 of "Differentiable and accelerated directional
+ * wavelet transforms on the sphere and ball", Price et al. 2024) on McEwen-Wiaux
+ * (MW) sampling, together with the harmonic transforms it is built from: the spin
+ * spherical-harmonic transform Y (Sec. 2.1, Eqs. 2-3) and the Wigner transform D
+ * (Sec. 2.2, Eqs. 4-5), and the Fourier-Laguerre radial transform of the ball
+ * (Sec. 2.3, Eqs. 6-8).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Ownership   Every data pointer is a DEVICE pointer owned by the caller unless an
+ *             argument says otherwise.  A plan owns its tables and a workspace
+ *             sized for its batch; execute calls allocate nothing and do not
+ *             synchronise the host, so they can be issued back to back on a stream.
+ * Streams     `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *             stream).  All work of a call is enqueued on that stream; calls that
+ *             share one plan must not run concurrently (they share its workspace).
+ * Elements    float64.  A plan with reality=1 and spin=0 takes and returns REAL
+ *             pixel arrays (double); otherwise pixel arrays are complex,
+ *             interleaved (re, im) pairs of double.  Harmonic-space arrays are
+ *             always complex interleaved.
+ * Layouts     (row-major, batch outermost; `b` = batch index)
+ *   map       [b][L theta][2L-1 phi], theta_t = pi(2t+1)/(2L-1), phi_p = 2 pi p/(2L-1)
+ *   wav       scales j = J0..J concatenated; scale j is [b][2N_j-1 gamma][L_j beta][2L_j-1 alpha]
+ *             with gamma_g = 2 pi g/(2N_j-1) and alpha, beta on the MW grid at L_j
+ *   scal      [b][L_Phi][2L_Phi-1] (MW grid at the scaling band-limit L_Phi)
+ *   flm       [b][L][Mc] with Mc = L (m = 0..L-1) for real plans and Mc = 2L-1
+ *             (index m + L - 1) otherwise; real signals obey f_{l,-m} = (-1)^m conj f_lm
+ *   flmn      [b][2N_j-1][L_j][Mc_j], n index n + N_j - 1, m indexed as for flm at L_j
+ * Errors      Every call returns an s2w_status.  Parameters are validated at plan
+ *             creation and on each call (null or misaligned pointers, bad scale
+ *             index).  s2w_last_error() returns a thread-local message for the most
+ *             recent failure.  Device-side problems are recorded in a per-plan error
+ *             word that s2w_check() reads; nothing traps or aborts.
+ */
+#ifndef S2W_H
+#define S2W_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  S2W_OK = 0,
+  S2W_EINVAL = 1,        /* bad parameter or pointer */
+  S2W_ENOMEM = 2,        /* device allocation failed at plan creation */
+  S2W_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  S2W_ETIMEOUT = 4,      /* a bounded device wait gave up */
+  S2W_EUNSUPPORTED = 5,  /* parameters valid but not supported by this build */
+  S2W_ENONFINITE = 6     /* a kernel detected a non-finite input */
+} s2w_status;
+
+typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2 } s2w_precision;
+
+/* Problem statement of the sphere transform (Algorithm 1; Sec. 3.3; App. A).
+ *   L        angular band-limit, harmonic degrees l < L            (2 <= L <= 1024)
+ *   N        azimuthal band-limit of the wavelets, |n| < N          (1 <= N <= L)
+ *   J0       lowest wavelet scale; the scaling function covers l < lambda^J0
+ *   spin     spin of the signal, |spin| < L
+ *   reality  1 for real spin-0 signals (real pixel arrays, m >= 0 stored)
+ *   batch    number of maps transformed per call                   (>= 1)
+ *   precision  s2w_precision; only S2W_FP64 is implemented in this build
+ *   precompute 0 (Wigner-d functions by recursion inside the kernels)
+ *   lambda   dilation factor lambda > 1 (Eq. A2); scale j uses band-limit
+ *            L_j = min(ceil(lambda^(j+1)), L) and N_j = min(N, L_j), j = J0..J with J
+ *            the smallest integer such that lambda^J >= L; L_Phi = min(ceil(lambda^J0), L). */
+typedef struct {
+  int L, N, J0, spin, reality, batch, precision, precompute;
+  double lambda;
+} s2w_params;
+
+typedef struct s2w_plan s2w_plan;
+
+/* Builds every table the transforms need (filters, quadrature matrices, Wigner-d
+ * seeds, DFT twiddles) in float64 on the host, uploads them and allocates the
+ * workspace.  Blocks until the uploads are complete.  *out receives the plan;
+ * on failure *out is NULL and nothing is leaked.  `stream` is only used for the
+ * uploads. */
+s2w_status s2w_plan_create(const s2w_params* params, void* stream, s2w_plan** out);
+
+/* Frees the plan.  The caller must make sure no work using it is still queued. */
+s2w_status s2w_plan_destroy(s2w_plan* plan);
+
+/* Sizes (in elements of the plan's pixel type, per map) of the map, the
+ * concatenated wavelet coefficients and the scaling coefficients; the number of
+ * scales; wav_offsets[0..nscales] (element offsets of each scale inside one map's
+ * wavelet block, last = total); and per scale L_j, N_j.  Any output pointer may be
+ * NULL.  Arrays must hold nscales (+1 for offsets) entries; query nscales first with
+ * the others NULL.  *L_phi receives the scaling band-limit. */
+s2w_status s2w_query_layout(const s2w_plan* plan, int64_t* map_elems, int64_t* wav_elems,
+                            int64_t* scal_elems, int* nscales, int64_t* wav_offsets,
+                            int* Lj, int* Nj, int* L_phi);
+
+/* Analysis (Algorithm 1, Eqs. 40-41): f [batch][map] -> wav, scal. */
+s2w_status s2w_forward(const s2w_plan* plan, const void* f, void* wav, void* scal, void* stream);
+
+/* Synthesis (Algorithm 1, Eq. 42): wav, scal -> f.  Exact inverse of s2w_forward on
+ * band-limited signals (the admissibility condition, Eq. 30). */
+s2w_status s2w_inverse(const s2w_plan* plan, const void* wav, const void* scal, void* f,
+                       void* stream);
+
+/* Forward spin SHT (Eq. 2) of the plan's batch of maps at band-limit L and spin: f -> flm. */
+s2w_status s2w_sht_forward(const s2w_plan* plan, const void* f, void* flm, void* stream);
+
+/* Inverse spin SHT (Eq. 3): flm -> f. */
+s2w_status s2w_sht_inverse(const s2w_plan* plan, const void* flm, void* f, void* stream);
+
+/* Forward Wigner transform (Eq. 4) at the band-limits (L_j, N_j) of wavelet scale
+ * index `scale` (0 = J0): SO(3) samples laid out like one scale of `wav` -> flmn
+ * (all |n| < N_j, layout above). */
+s2w_status s2w_wigner_forward(const s2w_plan* plan, int scale, const void* f, void* flmn,
+                              void* stream);
+
+/* Inverse Wigner transform (Eq. 5) at (L_j, N_j): flmn -> SO(3) samples. */
+s2w_status s2w_wigner_inverse(const s2w_plan* plan, int scale, const void* flmn, void* f,
+                              void* stream);
+
+/* Synchronises the plan's last stream, then reads and clears the device error word.
+ * Returns S2W_OK, S2W_ECUDA (asynchronous CUDA error) or the recorded status. */
+s2w_status s2w_check(const s2w_plan* plan);
+
+/* Message for the most recent failing call on this thread ("" if none). */
+const char* s2w_last_error(void);
+
+/* Library version string. */
+const char* s2w_version(void);
+
+/* ---- tracing ------------------------------------------------------------------------
+ * Kernel kinds reported by the tracer:
+ *   0 "dft_forward"   pixels -> m-columns (azimuthal + gamma DFTs)
+ *   1 "dft_inverse"   m-columns -> pixels
+ *   2 "wigner_inverse" inverse l-contraction with the fused Wigner-d recursion
+ *   3 "wigner_forward" colatitude quadrature + forward l-contraction
+ * When tracing is on, every kernel launch of the plan is bracketed by two CUDA events
+ * recorded on the launching stream (events come from a pool created by
+ * s2w_trace_enable; launches beyond its capacity are not recorded).  Besides the device
+ * time, the tracer accumulates each launch's ALGORITHMIC float64 operation count:
+ *   dft_*      2.5 n log2 n per real ring transform of length n (half a complex FFT) plus
+ *              8 per gamma-DFT multiply-add;
+ *   wigner_*   per contraction term (beta, m, n, l >= max|m|,|n|): 5 for the recursion
+ *              step plus 4 per map (complex coefficient times real d^l_mn);
+ *              the dense colatitude quadrature of wigner_forward is not counted. */
+s2w_status s2w_trace_enable(s2w_plan* plan, int on, int capacity);
+/* Clears the recorded launches (does not synchronise). */
+s2w_status s2w_trace_reset(s2w_plan* plan);
+/* Synchronises the recorded events and returns, for kernel kind `kind`, the number of
+ * recorded launches, their summed device time in milliseconds and summed algorithmic
+ * float64 operations.  Any output pointer may be NULL. */
+s2w_status s2w_trace_read(const s2w_plan* plan, int kind, int64_t* launches, double* ms,
+                          double* flops);
+/* Name of a kernel kind ("" if out of range). */
+const char* s2w_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S2W_H */

@@ -1,0 +1,228 @@
+"""Python binding of libs2w.so, the GB300 directional wavelet transform library.
+
+Thin ctypes marshalling over the C ABI declared in ``include/s2w.h``: every step of
+every transform runs in the library's CUDA kernels; PyTorch only provides device
+memory and the CUDA stream.  There is no fallback: if the compiled library is
+missing or fails to load, ``load()`` raises.
+
+Arrays are torch tensors on the GPU, C-contiguous, float64 (real spin-0 plans) or
+complex128, with the layouts of ``include/s2w.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libs2w.so")
+_lib = None
+
+S2W_FP64, S2W_FP32_SPLIT, S2W_BF16 = 0, 1, 2
+STATUS = {0: "S2W_OK", 1: "S2W_EINVAL", 2: "S2W_ENOMEM", 3: "S2W_ECUDA", 4: "S2W_ETIMEOUT",
+          5: "S2W_EUNSUPPORTED", 6: "S2W_ENONFINITE"}
+
+# every symbol include/s2w.h declares
+EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forward", "s2w_inverse",
+           "s2w_sht_forward", "s2w_sht_inverse", "s2w_wigner_forward", "s2w_wigner_inverse",
+           "s2w_check", "s2w_last_error", "s2w_version", "s2w_trace_enable", "s2w_trace_reset",
+           "s2w_trace_read", "s2w_kernel_name"]
+KERNEL_KINDS = 4
+
+
+class S2WError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("N", ctypes.c_int), ("J0", ctypes.c_int), ("spin", ctypes.c_int),
+                ("reality", ctypes.c_int), ("batch", ctypes.c_int), ("precision", ctypes.c_int),
+                ("precompute", ctypes.c_int), ("lam", ctypes.c_double)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libs2w.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libs2w.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i64p, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)
+    lib.s2w_plan_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+    lib.s2w_plan_destroy.argtypes = [vp]
+    lib.s2w_query_layout.argtypes = [vp, i64p, i64p, i64p, ip, i64p, ip, ip, ip]
+    lib.s2w_forward.argtypes = [vp, vp, vp, vp, vp]
+    lib.s2w_inverse.argtypes = [vp, vp, vp, vp, vp]
+    lib.s2w_sht_forward.argtypes = [vp, vp, vp, vp]
+    lib.s2w_sht_inverse.argtypes = [vp, vp, vp, vp]
+    lib.s2w_wigner_forward.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.s2w_wigner_inverse.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.s2w_check.argtypes = [vp]
+    lib.s2w_last_error.restype = ctypes.c_char_p
+    lib.s2w_version.restype = ctypes.c_char_p
+    lib.s2w_trace_enable.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.s2w_trace_reset.argtypes = [vp]
+    lib.s2w_trace_read.argtypes = [vp, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
+    lib.s2w_kernel_name.argtypes = [ctypes.c_int]
+    lib.s2w_kernel_name.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("s2w_last_error", "s2w_version", "s2w_kernel_name"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise S2WError(status, _lib.s2w_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, real: bool, name: str):
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    want = torch.float64 if real else torch.complex128
+    if t.dtype != want:
+        raise ValueError(f"{name} must be {want}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A transform plan: the parameters of Algorithm 1 plus the batch size.
+
+    Parameters follow the paper's statement of the problem: band-limits L and N,
+    dilation ``lam`` (lambda), lowest scale J0, spin, reality of the signal and the
+    number of maps per call.
+    """
+
+    def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, spin: int = 0,
+                 reality: bool = False, batch: int = 1, precision: int = S2W_FP64, stream=None):
+        lib = load()
+        self.params = Params(L, N, J0, spin, int(reality), batch, precision, 0, float(lam))
+        h = ctypes.c_void_p()
+        _check(lib.s2w_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.L, self.N, self.lam, self.J0, self.spin = L, N, lam, J0, spin
+        self.real = bool(reality) and spin == 0
+        self.batch = batch
+        me, we, se = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        ns, lphi = ctypes.c_int(), ctypes.c_int()
+        _check(lib.s2w_query_layout(h, ctypes.byref(me), ctypes.byref(we), ctypes.byref(se),
+                                    ctypes.byref(ns), None, None, None, ctypes.byref(lphi)))
+        n = ns.value
+        offs = (ctypes.c_int64 * (n + 1))()
+        Lj = (ctypes.c_int * n)()
+        Nj = (ctypes.c_int * n)()
+        _check(lib.s2w_query_layout(h, None, None, None, None, offs, Lj, Nj, None))
+        self.map_elems, self.wav_elems, self.scal_elems = me.value, we.value, se.value
+        self.nscales, self.L_phi = n, lphi.value
+        self.wav_offsets = list(offs)
+        self.Lj, self.Nj = list(Lj), list(Nj)
+        self.Mc = L if self.real else 2 * L - 1
+
+    # ------------------------------------------------------------------ buffers
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.real else torch.complex128
+
+    def empty_map(self, device="cuda"):
+        import torch
+        return torch.empty((self.batch, self.L, 2 * self.L - 1), dtype=self.dtype, device=device)
+
+    def empty_wav(self, device="cuda"):
+        import torch
+        return torch.empty((self.batch, self.wav_elems), dtype=self.dtype, device=device)
+
+    def empty_scal(self, device="cuda"):
+        import torch
+        return torch.empty((self.batch, self.L_phi, 2 * self.L_phi - 1), dtype=self.dtype, device=device)
+
+    def empty_flm(self, device="cuda"):
+        import torch
+        return torch.empty((self.batch, self.L, self.Mc), dtype=torch.complex128, device=device)
+
+    def scale_shape(self, s: int):
+        return (2 * self.Nj[s] - 1, self.Lj[s], 2 * self.Lj[s] - 1)
+
+    def empty_flmn(self, s: int, device="cuda"):
+        import torch
+        Lj, Nj = self.Lj[s], self.Nj[s]
+        Mcj = Lj if self.real else 2 * Lj - 1
+        return torch.empty((self.batch, 2 * Nj - 1, Lj, Mcj), dtype=torch.complex128, device=device)
+
+    def scale_view(self, wav, s: int):
+        """View of scale index s of a [batch, wav_elems] tensor as [batch, 2N_j-1, L_j, 2L_j-1]."""
+        a, b = self.wav_offsets[s], self.wav_offsets[s + 1]
+        return wav[:, a:b].view(self.batch, *self.scale_shape(s))
+
+    # ------------------------------------------------------------------ transforms
+    def forward(self, f, wav, scal, stream=None):
+        _check(_lib.s2w_forward(self._h, _ptr(f, self.real, "f"), _ptr(wav, self.real, "wav"),
+                                _ptr(scal, self.real, "scal"), _stream(stream)))
+
+    def inverse(self, wav, scal, f, stream=None):
+        _check(_lib.s2w_inverse(self._h, _ptr(wav, self.real, "wav"), _ptr(scal, self.real, "scal"),
+                                _ptr(f, self.real, "f"), _stream(stream)))
+
+    def sht_forward(self, f, flm, stream=None):
+        _check(_lib.s2w_sht_forward(self._h, _ptr(f, self.real, "f"), _ptr(flm, False, "flm"),
+                                    _stream(stream)))
+
+    def sht_inverse(self, flm, f, stream=None):
+        _check(_lib.s2w_sht_inverse(self._h, _ptr(flm, False, "flm"), _ptr(f, self.real, "f"),
+                                    _stream(stream)))
+
+    def wigner_forward(self, s: int, f, flmn, stream=None):
+        _check(_lib.s2w_wigner_forward(self._h, s, _ptr(f, self.real, "f"), _ptr(flmn, False, "flmn"),
+                                       _stream(stream)))
+
+    def wigner_inverse(self, s: int, flmn, f, stream=None):
+        _check(_lib.s2w_wigner_inverse(self._h, s, _ptr(flmn, False, "flmn"), _ptr(f, self.real, "f"),
+                                       _stream(stream)))
+
+    def check(self):
+        _check(_lib.s2w_check(self._h))
+
+    # ------------------------------------------------------------------ tracing
+    def trace(self, on: bool = True, capacity: int = 4096):
+        _check(_lib.s2w_trace_enable(self._h, int(on), capacity))
+
+    def trace_reset(self):
+        _check(_lib.s2w_trace_reset(self._h))
+
+    def trace_read(self):
+        """{kernel name: (launches, device ms, algorithmic float64 ops)} since the last reset."""
+        out = {}
+        for k in range(KERNEL_KINDS):
+            n, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            _check(_lib.s2w_trace_read(self._h, k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl)))
+            out[_lib.s2w_kernel_name(k).decode()] = (n.value, ms.value, fl.value)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.s2w_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load().s2w_version().decode()

@@ -1,0 +1,365 @@
+// C ABI (include/s2w.h): plan lifetime, layout queries and the execute calls that
+// sequence the kernels of one transform on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "s2w_internal.h"
+
+using namespace s2w;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+s2w_status fail(s2w_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+s2w_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(S2W_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define S2W_CUDA(call, where)                          \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+s2w_status check_ptr(const void* p, bool real_elems, const char* name) {
+  if (p == nullptr) return fail(S2W_EINVAL, std::string(name) + " is NULL");
+  if (!aligned(p, real_elems ? 8 : 16)) return fail(S2W_EINVAL, std::string(name) + " is misaligned");
+  return S2W_OK;
+}
+
+int Mc_at(const s2w_plan* P, int L) { return P->real ? L : 2 * L - 1; }
+int mlo_at(const s2w_plan* P, int L) { return P->real ? 0 : -(L - 1); }
+
+const GridTables& grid_of(const s2w_plan* P, const TransformSpec& t) { return P->grids[t.grid]; }
+
+CoefArgs flm_ws_args(const s2w_plan* P) {
+  CoefArgs c;
+  c.coef = P->flm_ws;
+  c.s_b = (int64_t)P->p.L * P->Mc;
+  c.s_n = 0;
+  c.s_l = P->Mc;
+  c.mlo = P->mlo;
+  return c;
+}
+
+ColumnArgs cols(const s2w_plan* P, int nact, int L) {
+  ColumnArgs c;
+  c.G = P->g_ws;
+  c.B = P->p.batch;
+  c.nact = nact;
+  c.L = L;
+  c.Mc = Mc_at(P, L);
+  c.mlo = mlo_at(P, L);
+  return c;
+}
+
+// ---- tracing: events around each launch plus its algorithmic float64 operation count
+enum Kind { K_DFT_FWD = 0, K_DFT_INV = 1, K_WIG_INV = 2, K_WIG_FWD = 3, K_NKINDS = 4 };
+const char* kKindNames[K_NKINDS] = {"dft_forward", "dft_inverse", "wigner_inverse", "wigner_forward"};
+
+double contraction_terms(const s2w_plan* P, const TransformSpec& t) {
+  const int L = t.L, mlo = mlo_at(P, L), Mc = Mc_at(P, L);
+  double T = 0.0;
+  for (int mi = 0; mi < Mc; ++mi)
+    for (int n : t.nvals_h) {
+      const int l0 = std::max(std::abs(mlo + mi), std::abs(n));
+      if (l0 < L) T += double(L) * double(L - l0);
+    }
+  return T;
+}
+
+double dft_flops(const s2w_plan* P, const TransformSpec& t) {
+  const double n = 2.0 * t.L - 1.0, B = P->p.batch, Ng = 2.0 * t.N - 1.0;
+  const double ring = (P->real ? 2.5 : 5.0) * n * std::log2(n);
+  return B * Ng * t.L * ring + 8.0 * B * t.L * Mc_at(P, t.L) * t.nact * Ng;
+}
+
+struct TraceScope {
+  s2w_plan* P;
+  cudaStream_t st;
+  bool on = false;
+  size_t slot = 0;
+  TraceScope(s2w_plan* P_, cudaStream_t st_, int kind, double flops) : P(P_), st(st_) {
+    if (!P->trace_on) return;
+    slot = 2 * P->trace_rec.size();
+    if (slot + 2 > P->trace_ev.size()) return;
+    on = true;
+    cudaEventRecord(P->trace_ev[slot], st);
+    P->trace_rec.push_back({kind, flops});
+  }
+  ~TraceScope() {
+    if (on) cudaEventRecord(P->trace_ev[slot + 1], st);
+  }
+};
+
+// pixels -> harmonic accumulation: out += mult_fwd * (forward transform of pix)
+s2w_status fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, int64_t pix_sb, CoefArgs out,
+                         cudaStream_t st) {
+  const GridTables& g = grid_of(P, t);
+  ColumnArgs c = cols(P, t.nact, t.L);
+  {
+    TraceScope ts(P, st, K_DFT_FWD, P->trace_on ? dft_flops(P, t) : 0.0);
+    S2W_CUDA(launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st), "azimuthal DFT (forward)");
+  }
+  {
+    TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
+    S2W_CUDA(launch_wigner_forward(P, g, t, c, out, st), "forward contraction");
+  }
+  return S2W_OK;
+}
+
+// harmonic -> pixels: pix = inverse transform of (mult_inv * coef)
+s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void* pix, int64_t pix_sb,
+                         cudaStream_t st) {
+  const GridTables& g = grid_of(P, t);
+  ColumnArgs c = cols(P, t.nact, t.L);
+  {
+    TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
+    S2W_CUDA(launch_wigner_inverse(P, g, t, in, c, st), "inverse contraction");
+  }
+  {
+    TraceScope ts(P, st, K_DFT_INV, P->trace_on ? dft_flops(P, t) : 0.0);
+    S2W_CUDA(launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st), "azimuthal DFT (inverse)");
+  }
+  return S2W_OK;
+}
+
+size_t pix_bytes(const s2w_plan* P) { return P->real ? sizeof(double) : sizeof(double2); }
+
+}  // namespace
+
+extern "C" {
+
+const char* s2w_last_error(void) { return g_last_error.c_str(); }
+
+const char* s2w_version(void) { return "s2w-gb300 0.1 (sm_103a, float64)"; }
+
+s2w_status s2w_plan_create(const s2w_params* params, void* stream, s2w_plan** out) {
+  if (out == nullptr) return fail(S2W_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (params == nullptr) return fail(S2W_EINVAL, "params is NULL");
+  s2w_plan* P = new (std::nothrow) s2w_plan();
+  if (P == nullptr) return fail(S2W_ENOMEM, "host allocation failed");
+  std::string err;
+  s2w_status s = build_plan(*params, (cudaStream_t)stream, P, err);
+  if (s != S2W_OK) {
+    free_plan(P);
+    delete P;
+    return fail(s, err);
+  }
+  P->last_stream = (cudaStream_t)stream;
+  *out = P;
+  g_last_error.clear();
+  return S2W_OK;
+}
+
+s2w_status s2w_plan_destroy(s2w_plan* plan) {
+  if (plan == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  for (cudaEvent_t e : plan->trace_ev) cudaEventDestroy(e);
+  plan->trace_ev.clear();
+  free_plan(plan);
+  delete plan;
+  return S2W_OK;
+}
+
+s2w_status s2w_query_layout(const s2w_plan* P, int64_t* map_elems, int64_t* wav_elems, int64_t* scal_elems,
+                            int* nscales, int64_t* wav_offsets, int* Lj, int* Nj, int* L_phi) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  if (map_elems) *map_elems = P->map_elems;
+  if (wav_elems) *wav_elems = P->wav_elems;
+  if (scal_elems) *scal_elems = P->scal_elems;
+  if (nscales) *nscales = P->nscales;
+  if (L_phi) *L_phi = P->L_phi;
+  for (int s = 0; s < P->nscales; ++s) {
+    if (wav_offsets) wav_offsets[s] = P->wav_off[s];
+    if (Lj) Lj[s] = P->Lj[s];
+    if (Nj) Nj[s] = P->Nj[s];
+  }
+  if (wav_offsets) wav_offsets[P->nscales] = P->wav_off[P->nscales];
+  return S2W_OK;
+}
+
+s2w_status s2w_forward(const s2w_plan* cP, const void* f, void* wav, void* scal, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  s2w_status s;
+  if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(wav, P->real, "wav")) ||
+      (s = check_ptr(scal, P->real, "scal")))
+    return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const int64_t B = P->p.batch;
+  // f_lm = Y f  (Eq. 2)
+  S2W_CUDA(launch_zero(P->flm_ws, B * (int64_t)P->p.L * P->Mc * sizeof(double2), st), "zero f_lm");
+  if ((s = fwd_transform(P, P->sht, f, P->map_elems, flm_ws_args(P), st))) return s;
+  // scaling map W^Phi = Y^-1 (Phi f_lm) at L_Phi  (Eq. 41)
+  if ((s = inv_transform(P, P->scal_t, flm_ws_args(P), scal, P->scal_elems, st))) return s;
+  // wavelet maps W^j = D^-1 (N Psi^j f_lm) at (L_j, N_j)  (Eq. 40)
+  char* wbase = static_cast<char*>(wav);
+  for (int sc = 0; sc < P->nscales; ++sc) {
+    void* pix = wbase + P->wav_off[sc] * pix_bytes(P);
+    if ((s = inv_transform(P, P->wav_t[sc], flm_ws_args(P), pix, P->wav_elems, st))) return s;
+  }
+  return S2W_OK;
+}
+
+s2w_status s2w_inverse(const s2w_plan* cP, const void* wav, const void* scal, void* f, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  s2w_status s;
+  if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(wav, P->real, "wav")) ||
+      (s = check_ptr(scal, P->real, "scal")))
+    return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const int64_t B = P->p.batch;
+  S2W_CUDA(launch_zero(P->flm_ws, B * (int64_t)P->p.L * P->Mc * sizeof(double2), st), "zero f_lm");
+  // f_lm = Phi Y W^Phi + sum_j Psi^j+ D W^j  (Eq. 42)
+  if ((s = fwd_transform(P, P->scal_t, scal, P->scal_elems, flm_ws_args(P), st))) return s;
+  const char* wbase = static_cast<const char*>(wav);
+  for (int sc = 0; sc < P->nscales; ++sc) {
+    const void* pix = wbase + P->wav_off[sc] * pix_bytes(P);
+    if ((s = fwd_transform(P, P->wav_t[sc], pix, P->wav_elems, flm_ws_args(P), st))) return s;
+  }
+  // f = Y^-1 f_lm
+  return inv_transform(P, P->sht, flm_ws_args(P), f, P->map_elems, st);
+}
+
+s2w_status s2w_sht_forward(const s2w_plan* cP, const void* f, void* flm, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  s2w_status s;
+  if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(flm, false, "flm"))) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  CoefArgs out = flm_ws_args(P);
+  out.coef = static_cast<double2*>(flm);
+  S2W_CUDA(launch_zero(flm, (int64_t)P->p.batch * P->p.L * P->Mc * sizeof(double2), st), "zero flm");
+  return fwd_transform(P, P->sht, f, P->map_elems, out, st);
+}
+
+s2w_status s2w_sht_inverse(const s2w_plan* cP, const void* flm, void* f, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  s2w_status s;
+  if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(flm, false, "flm"))) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  CoefArgs in = flm_ws_args(P);
+  in.coef = static_cast<const double2*>(flm);
+  return inv_transform(P, P->sht, in, f, P->map_elems, st);
+}
+
+static CoefArgs raw_args(const s2w_plan* P, int sc, const void* flmn) {
+  const int Lj = P->Lj[sc], Nj = P->Nj[sc], Mcj = Mc_at(P, Lj);
+  CoefArgs c;
+  c.coef = static_cast<const double2*>(flmn);
+  c.s_l = Mcj;
+  c.s_n = (int64_t)Lj * Mcj;
+  c.s_b = (int64_t)(2 * Nj - 1) * Lj * Mcj;
+  c.mlo = mlo_at(P, Lj);
+  return c;
+}
+
+s2w_status s2w_wigner_forward(const s2w_plan* cP, int scale, const void* f, void* flmn, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  if (scale < 0 || scale >= P->nscales) return fail(S2W_EINVAL, "scale index out of range");
+  s2w_status s;
+  if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(flmn, false, "flmn"))) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  CoefArgs out = raw_args(P, scale, flmn);
+  S2W_CUDA(launch_zero(flmn, out.s_b * P->p.batch * (int64_t)sizeof(double2), st), "zero flmn");
+  const int Lj = P->Lj[scale], Nj = P->Nj[scale];
+  return fwd_transform(P, P->raw_t[scale], f, (int64_t)(2 * Nj - 1) * Lj * (2 * Lj - 1), out, st);
+}
+
+s2w_status s2w_wigner_inverse(const s2w_plan* cP, int scale, const void* flmn, void* f, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  if (scale < 0 || scale >= P->nscales) return fail(S2W_EINVAL, "scale index out of range");
+  s2w_status s;
+  if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(flmn, false, "flmn"))) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const int Lj = P->Lj[scale], Nj = P->Nj[scale];
+  return inv_transform(P, P->raw_t[scale], raw_args(P, scale, flmn), f,
+                       (int64_t)(2 * Nj - 1) * Lj * (2 * Lj - 1), st);
+}
+
+s2w_status s2w_check(const s2w_plan* P) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(P->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  int word = 0;
+  e = cudaMemcpy(&word, P->err_word, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error word read");
+  if (word != 0) {
+    cudaMemset(P->err_word, 0, sizeof(int));
+    return fail((s2w_status)word, "device error word set");
+  }
+  return S2W_OK;
+}
+
+s2w_status s2w_trace_enable(s2w_plan* P, int on, int capacity) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  if (on && capacity < 1) return fail(S2W_EINVAL, "capacity must be >= 1");
+  P->trace_on = false;
+  if (on) {
+    const size_t want = 2 * (size_t)capacity;
+    while (P->trace_ev.size() < want) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate");
+      P->trace_ev.push_back(e);
+    }
+    P->trace_rec.clear();
+    P->trace_rec.reserve(capacity);
+    P->trace_on = true;
+  }
+  return S2W_OK;
+}
+
+s2w_status s2w_trace_reset(s2w_plan* P) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  P->trace_rec.clear();
+  return S2W_OK;
+}
+
+s2w_status s2w_trace_read(const s2w_plan* P, int kind, int64_t* launches, double* ms, double* flops) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  if (kind < 0 || kind >= K_NKINDS) return fail(S2W_EINVAL, "kernel kind out of range");
+  int64_t n = 0;
+  double t = 0.0, f = 0.0;
+  for (size_t i = 0; i < P->trace_rec.size(); ++i) {
+    if (P->trace_rec[i].kind != kind) continue;
+    cudaError_t e = cudaEventSynchronize(P->trace_ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float dt = 0.0f;
+    e = cudaEventElapsedTime(&dt, P->trace_ev[2 * i], P->trace_ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    ++n;
+    t += dt;
+    f += P->trace_rec[i].flops;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  return S2W_OK;
+}
+
+const char* s2w_kernel_name(int kind) { return (kind >= 0 && kind < K_NKINDS) ? kKindNames[kind] : ""; }
+
+}  // extern "C"

@@ -1,0 +1,606 @@
+// Float64 kernels of the hot path (sm_103a):
+//  * k_dft_fwd / k_dft_inv   azimuthal (alpha/phi, length 2L-1) and gamma (length 2N-1)
+//                            DFTs between pixel rings and m-columns (Sec. 5.2, Eq. 48);
+//  * k_wig_inv               inverse contraction over l against d^l_mn(beta), the
+//                            Wigner-d three-term recursion in l fused into the loop, with
+//                            the harmonic products (Eq. 27 / Eq. 29) fused as multipliers;
+//  * k_wig_fwd               forward contraction: colatitude quadrature matrix applied in
+//                            shared memory, then the recursion-generated d tile contracted
+//                            against the weighted columns, products fused in the epilogue.
+#include <math.h>
+
+#include "s2w_internal.h"
+
+namespace s2w {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// ------------------------------------------------------------------------- DFTs
+// y[k] = sum_j x[j] w^(SIGN j k), w = exp(2 pi i/n), n = n1 n2 (Cooley-Tukey split
+// j = n2 j1 + j2, k = k1 + n1 k2).  Stage 1 leaves the twiddled length-n1 transforms in
+// tmp[k1 n2 + j2]; stage 2 finishes the length-n2 transforms for requested outputs.
+template <int SIGN>
+__device__ __forceinline__ double2 twid(const double2* tw, int e) {
+  double2 t = tw[e];
+  if (SIGN < 0) t.y = -t.y;
+  return t;
+}
+
+template <int SIGN>
+__device__ void dft_stage1(const double2* x, double2* tmp, const double2* tw, int n, int n1, int n2) {
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int k1 = idx / n2, j2 = idx - k1 * n2;
+    const int step = (n2 * k1) % n;
+    double re = 0.0, im = 0.0;
+    int e = 0;
+    for (int j1 = 0; j1 < n1; ++j1) {
+      const double2 xv = x[n2 * j1 + j2];
+      const double2 t = twid<SIGN>(tw, e);
+      re = fma(xv.x, t.x, fma(-xv.y, t.y, re));
+      im = fma(xv.x, t.y, fma(xv.y, t.x, im));
+      e += step;
+      if (e >= n) e -= n;
+    }
+    const double2 t = twid<SIGN>(tw, (j2 * k1) % n);
+    tmp[k1 * n2 + j2] = make_double2(fma(re, t.x, -im * t.y), fma(re, t.y, im * t.x));
+  }
+}
+
+// one output of stage 2
+template <int SIGN, bool REAL_ONLY>
+__device__ __forceinline__ double2 dft_stage2_one(const double2* tmp, const double2* tw, int n, int n1,
+                                                  int n2, int k) {
+  const int k1 = k % n1, k2 = k / n1;
+  const int step = (n1 * k2) % n;
+  const double2* row = tmp + k1 * n2;
+  double re = 0.0, im = 0.0;
+  int e = 0;
+  for (int j2 = 0; j2 < n2; ++j2) {
+    const double2 v = row[j2];
+    const double2 t = twid<SIGN>(tw, e);
+    re = fma(v.x, t.x, fma(-v.y, t.y, re));
+    if (!REAL_ONLY) im = fma(v.x, t.y, fma(v.y, t.x, im));
+    e += step;
+    if (e >= n) e -= n;
+  }
+  return make_double2(re, im);
+}
+
+struct DftArgs {
+  const void* pix_in;
+  void* pix_out;
+  int64_t pix_sb;       // elements between maps
+  double2* G;           // [B][nact][L][Mc]
+  int B, nact, Ng, L, Mc, mlo, n, n1, n2;
+  const double2* tw;
+  const double2* gph;   // [nact][Ng] exp(+i n gamma_g)
+  double scale;
+};
+
+// Pixels [b][g][t][a] -> columns G[b][ni][t][mi].  One block per (ring t, map b).
+template <bool REAL>
+__global__ void k_dft_fwd(DftArgs a) {
+  extern __shared__ double2 sm2[];
+  const int n = a.n, t = blockIdx.x, b = blockIdx.y;
+  double2* tw = sm2;             // [n]
+  double2* x = tw + n;           // [n]
+  double2* tmp = x + n;          // [n]
+  double2* H = tmp + n;          // [Ng][Mc]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
+  const int64_t ring = (int64_t)a.L * n;
+  for (int g = 0; g < a.Ng; ++g) {
+    __syncthreads();
+    const int64_t base = (int64_t)b * a.pix_sb + (int64_t)g * ring + (int64_t)t * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (REAL) x[i] = make_double2(((const double*)a.pix_in)[base + i], 0.0);
+      else x[i] = ((const double2*)a.pix_in)[base + i];
+    }
+    __syncthreads();
+    dft_stage1<-1>(x, tmp, tw, n, a.n1, a.n2);
+    __syncthreads();
+    for (int mi = threadIdx.x; mi < a.Mc; mi += blockDim.x) {
+      int k = a.mlo + mi;
+      if (k < 0) k += n;
+      H[g * a.Mc + mi] = dft_stage2_one<-1, false>(tmp, tw, n, a.n1, a.n2, k);
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < a.nact * a.Mc; idx += blockDim.x) {
+    const int ni = idx / a.Mc, mi = idx - ni * a.Mc;
+    double re = 0.0, im = 0.0;
+    for (int g = 0; g < a.Ng; ++g) {
+      const double2 h = H[g * a.Mc + mi];
+      const double2 p = a.gph[ni * a.Ng + g];   // conj for the forward sum
+      re = fma(h.x, p.x, fma(h.y, p.y, re));
+      im = fma(h.y, p.x, fma(-h.x, p.y, im));
+    }
+    a.G[(((int64_t)b * a.nact + ni) * a.L + t) * a.Mc + mi] = make_double2(re * a.scale, im * a.scale);
+  }
+}
+
+// Columns G[b][ni][t][mi] -> pixels [b][g][t][a].  One block per (ring t, map b).
+template <bool REAL>
+__global__ void k_dft_inv(DftArgs a) {
+  extern __shared__ double2 sm2[];
+  const int n = a.n, t = blockIdx.x, b = blockIdx.y;
+  double2* tw = sm2;
+  double2* x = tw + n;
+  double2* tmp = x + n;
+  double2* Gs = tmp + n;         // [nact][Mc]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
+  for (int idx = threadIdx.x; idx < a.nact * a.Mc; idx += blockDim.x) {
+    const int ni = idx / a.Mc, mi = idx - ni * a.Mc;
+    Gs[idx] = a.G[(((int64_t)b * a.nact + ni) * a.L + t) * a.Mc + mi];
+  }
+  const int64_t ring = (int64_t)a.L * n;
+  for (int g = 0; g < a.Ng; ++g) {
+    __syncthreads();
+    for (int mi = threadIdx.x; mi < a.Mc; mi += blockDim.x) {
+      double re = 0.0, im = 0.0;
+      for (int ni = 0; ni < a.nact; ++ni) {
+        const double2 v = Gs[ni * a.Mc + mi];
+        const double2 p = a.gph[ni * a.Ng + g];
+        re = fma(v.x, p.x, fma(-v.y, p.y, re));
+        im = fma(v.x, p.y, fma(v.y, p.x, im));
+      }
+      const int m = a.mlo + mi;
+      if (REAL) {
+        x[m] = make_double2(re, im);
+        if (m > 0) x[n - m] = make_double2(re, -im);
+      } else {
+        x[m < 0 ? m + n : m] = make_double2(re, im);
+      }
+    }
+    __syncthreads();
+    dft_stage1<1>(x, tmp, tw, n, a.n1, a.n2);
+    __syncthreads();
+    const int64_t base = (int64_t)b * a.pix_sb + (int64_t)g * ring + (int64_t)t * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      if (REAL) {
+        ((double*)a.pix_out)[base + k] = dft_stage2_one<1, true>(tmp, tw, n, a.n1, a.n2, k).x;
+      } else {
+        ((double2*)a.pix_out)[base + k] = dft_stage2_one<1, false>(tmp, tw, n, a.n1, a.n2, k);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- Wigner-d recursion
+struct RecTables {
+  const double* wpole;   // -2 sin^2(beta/2) (northern half) or 2 cos^2(beta/2) (southern half)
+  const double* cpow_m;
+  const int* cpow_e;
+  const double* spow_m;
+  const int* spow_e;
+  const double* sqrtC;
+  int n;  // row stride (2L-1)
+};
+
+// Values below 2^-100 of the true d^l_mn never reach the sums; while a column's value
+// is smaller than that it is carried scaled by 2^(600 q), q > 0, and skipped.
+constexpr int kSkipExp = -100;
+constexpr int kStepExp = 600;
+constexpr double kRescaleAt = 3.273390607896142e+150;   // 2^500
+constexpr double kRescaleBy = 2.409919865102884e-181;   // 2^-600
+
+// d^{l0}_{mn}(beta_b) at l0 = max(|m|, |n|) from the closed form
+//   d^l_{l n} = sqrt(binom(2l, l+n)) cos^{l+n}(b/2) (-sin(b/2))^{l-n}
+// and the symmetries d_{mn} = (-1)^{m-n} d_{nm} = d_{-n,-m}.
+__device__ __forceinline__ void wigner_seed(const RecTables& T, int b, int l0, int m, int n, double& v,
+                                            int& q) {
+  int kb, ac, as;
+  double sign = 1.0;
+  if (m == l0) {
+    kb = l0 + n; ac = l0 + n; as = l0 - n;
+    if ((l0 - n) & 1) sign = -1.0;
+  } else if (m == -l0) {
+    kb = l0 - n; ac = l0 - n; as = l0 + n;
+  } else if (n == l0) {
+    kb = l0 + m; ac = l0 + m; as = l0 - m;
+  } else {
+    kb = l0 - m; ac = l0 - m; as = l0 + m;
+    if ((l0 + m) & 1) sign = -1.0;
+  }
+  const int64_t row = (int64_t)b * T.n;
+  const double prod = sign * T.sqrtC[(int64_t)l0 * T.n + kb] * T.cpow_m[row + ac] * T.spow_m[row + as];
+  q = 0;
+  if (prod == 0.0) {
+    v = 0.0;
+    return;
+  }
+  const int E = T.cpow_e[row + ac] + T.spow_e[row + as];
+  const int tot = E + ilogb(prod);
+  if (tot >= kSkipExp) {
+    v = scalbn(prod, E);
+  } else {
+    q = (kSkipExp - tot + kStepExp - 1) / kStepExp;
+    v = scalbn(prod, E + kStepExp * q);
+  }
+}
+
+// Coefficients of the three-term recursion in l (Varshalovich),
+//   d^{l+1} = A (cos b - B) d^l - C d^{l-1},
+//   A = (l+1)(2l+1)/sqrt(((l+1)^2-m^2)((l+1)^2-n^2)),  B = m n/(l(l+1)),
+//   C = A sqrt((l^2-m^2)(l^2-n^2))/(l(2l+1))            (B = C = 0 at l = 0).
+// Near the poles cos b and B are both close to +-1, so A (cos b - B) is formed as
+//   north: A (1 - B) - A (1 - cos b),   south: A (1 + cos b) - A (1 + B),
+// with 1 -+ B = (l(l+1) -+ m n)/(l(l+1)) from exact integers and 1 -+ cos b = 2 sin^2, 2 cos^2
+// of the half angle (the per-ring weight `wpole`).  Kn = A (1 - B), Ks = -A (1 + B).
+__device__ __forceinline__ void rec_coeffs(int l, int m, int n, double& A, double& Kn, double& Ks, double& C) {
+  const double l1 = l + 1.0, dl = l;
+  const double den = sqrt((l1 * l1 - (double)m * m) * (l1 * l1 - (double)n * n));
+  A = l1 * (2.0 * dl + 1.0) / den;
+  if (l == 0) {
+    Kn = A;
+    Ks = -A;
+    C = 0.0;
+  } else {
+    const double ll = dl * l1, mn = (double)m * (double)n;   // exact integers in float64
+    Kn = A * ((ll - mn) / ll);
+    Ks = -A * ((ll + mn) / ll);
+    C = A * sqrt((dl * dl - (double)m * m) * (dl * dl - (double)n * n)) / (dl * (2.0 * dl + 1.0));
+  }
+}
+
+struct WigInvArgs {
+  const double2* coef;
+  int64_t s_b, s_n, s_l;
+  int mlo_in;
+  const double2* mult;   // [L][nact]
+  const int* nvals;
+  int nact;
+  double2* G;            // [B][nact][L][Mc]
+  int B, L, Mc, mlo;
+  RecTables T;
+};
+
+constexpr int kInvThreads = 128;
+constexpr int kInvLT = 32;
+
+template <int MB>
+__global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
+  __shared__ double2 Fs[kInvLT * MB];
+  __shared__ double cA[kInvLT], cKn[kInvLT], cKs[kInvLT], cC[kInvLT];
+  const int mi = blockIdx.x, ni = blockIdx.y;
+  const int m = a.mlo + mi, nn = a.nvals[ni];
+  const int L = a.L;
+  const int b = blockIdx.z * blockDim.x + threadIdx.x;
+  const int l0 = max(abs(m), abs(nn));
+  const double wb = (b < L) ? a.T.wpole[b] : 0.0;
+  const double* cK = (2 * (2 * b + 1) < a.T.n) ? cKn : cKs;
+  for (int map0 = 0; map0 < a.B; map0 += MB) {
+    double2 acc[MB];
+#pragma unroll
+    for (int k = 0; k < MB; ++k) acc[k] = make_double2(0.0, 0.0);
+    double v = 0.0, vp = 0.0;
+    int q = 0;
+    if (b < L && l0 < L) wigner_seed(a.T, b, l0, m, nn, v, q);
+    for (int ls = l0; ls < L; ls += kInvLT) {
+      const int cnt = min(kInvLT, L - ls);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < cnt * MB; idx += blockDim.x) {
+        const int i = idx / MB, mp = idx - i * MB, l = ls + i, bm = map0 + mp;
+        double2 f = make_double2(0.0, 0.0);
+        if (bm < a.B)
+          f = cmul(a.coef[(int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_in)],
+                   a.mult[(int64_t)l * a.nact + ni]);
+        Fs[idx] = f;
+      }
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) rec_coeffs(ls + i, m, nn, cA[i], cKn[i], cKs[i], cC[i]);
+      __syncthreads();
+      if (b < L) {
+        for (int i = 0; i < cnt; ++i) {
+          if (q == 0) {
+#pragma unroll
+            for (int k = 0; k < MB; ++k) {
+              const double2 f = Fs[i * MB + k];
+              acc[k].x = fma(f.x, v, acc[k].x);
+              acc[k].y = fma(f.y, v, acc[k].y);
+            }
+          }
+          const double x = fma(cA[i], wb, cK[i]);
+          const double vn = fma(x, v, -cC[i] * vp);
+          vp = v;
+          v = vn;
+          if (q > 0 && fabs(v) > kRescaleAt) {
+            v *= kRescaleBy;
+            vp *= kRescaleBy;
+            --q;
+          }
+        }
+      }
+    }
+    if (b < L) {
+#pragma unroll
+      for (int k = 0; k < MB; ++k) {
+        const int bm = map0 + k;
+        if (bm < a.B) a.G[(((int64_t)bm * a.nact + ni) * L + b) * a.Mc + mi] = acc[k];
+      }
+    }
+  }
+}
+
+struct WigFwdArgs {
+  const double2* G;      // [B][nact][L][Mc]
+  int B, L, Mc, mlo;
+  const int* nvals;
+  int nact;
+  const double2* mult;   // [L][nact]
+  double2* out;
+  int64_t s_b, s_n, s_l;
+  int mlo_out;
+  const double* MT;      // [2][L][L]
+  RecTables T;
+};
+
+template <int MB, int LT>
+__global__ void k_wig_fwd(WigFwdArgs a) {
+  extern __shared__ double smd[];
+  const int L = a.L;
+  double2* Gs = (double2*)smd;                 // [L][MB]
+  double* Ds = (double*)(Gs + (size_t)L * MB); // [LT][L]
+  double* cA = Ds + (size_t)LT * L;
+  double* cKn = cA + LT;
+  double* cKs = cKn + LT;
+  double* cC = cKs + LT;
+  const int mi = blockIdx.x, ni = blockIdx.y;
+  const int m = a.mlo + mi, nn = a.nvals[ni];
+  const int t = threadIdx.x;
+  const int l0 = max(abs(m), abs(nn));
+  if (l0 >= L) return;
+  const int par = (m + nn) & 1;
+  const double* MT = a.MT + (size_t)par * L * L;
+  const double wb = (t < L) ? a.T.wpole[t] : 0.0;
+  const double* cK = (2 * (2 * t + 1) < a.T.n) ? cKn : cKs;
+  for (int map0 = 0; map0 < a.B; map0 += MB) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < L * MB; idx += blockDim.x) {
+      const int tt = idx / MB, mp = idx - tt * MB, bm = map0 + mp;
+      Gs[idx] = (bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * L + tt) * a.Mc + mi] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // colatitude quadrature: Gs <- M^{par} Gs
+    {
+      double2 acc[MB];
+#pragma unroll
+      for (int k = 0; k < MB; ++k) acc[k] = make_double2(0.0, 0.0);
+      if (t < L) {
+        for (int tp = 0; tp < L; ++tp) {
+          const double w = MT[(size_t)tp * L + t];
+#pragma unroll
+          for (int k = 0; k < MB; ++k) {
+            const double2 gv = Gs[tp * MB + k];
+            acc[k].x = fma(w, gv.x, acc[k].x);
+            acc[k].y = fma(w, gv.y, acc[k].y);
+          }
+        }
+      }
+      __syncthreads();
+      if (t < L) {
+#pragma unroll
+        for (int k = 0; k < MB; ++k) Gs[t * MB + k] = acc[k];
+      }
+    }
+    double v = 0.0, vp = 0.0;
+    int q = 0;
+    if (t < L) wigner_seed(a.T, t, l0, m, nn, v, q);
+    for (int ls = l0; ls < L; ls += LT) {
+      const int cnt = min(LT, L - ls);
+      __syncthreads();
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) rec_coeffs(ls + i, m, nn, cA[i], cKn[i], cKs[i], cC[i]);
+      __syncthreads();
+      if (t < L) {
+        for (int i = 0; i < cnt; ++i) {
+          Ds[i * L + t] = (q == 0) ? v : 0.0;
+          const double x = fma(cA[i], wb, cK[i]);
+          const double vn = fma(x, v, -cC[i] * vp);
+          vp = v;
+          v = vn;
+          if (q > 0 && fabs(v) > kRescaleAt) {
+            v *= kRescaleBy;
+            vp *= kRescaleBy;
+            --q;
+          }
+        }
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < cnt * MB; idx += blockDim.x) {
+        const int i = idx / MB, mp = idx - i * MB, bm = map0 + mp, l = ls + i;
+        const double* drow = Ds + (size_t)i * L;
+        double re = 0.0, im = 0.0;
+        for (int bb = 0; bb < L; ++bb) {
+          const double d = drow[bb];
+          const double2 gv = Gs[bb * MB + mp];
+          re = fma(d, gv.x, re);
+          im = fma(d, gv.y, im);
+        }
+        if (bm < a.B) {
+          const double2 r = cmul(make_double2(re, im), a.mult[(int64_t)l * a.nact + ni]);
+          double2* o = a.out + (int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_out);
+          atomicAdd(&o->x, r.x);
+          atomicAdd(&o->y, r.y);
+        }
+      }
+    }
+  }
+}
+
+RecTables rec_tables(const GridTables& g) {
+  RecTables T;
+  T.wpole = g.wpole;
+  T.cpow_m = g.cpow_m;
+  T.cpow_e = g.cpow_e;
+  T.spow_m = g.spow_m;
+  T.spow_e = g.spow_e;
+  T.sqrtC = g.sqrtC;
+  T.n = g.n;
+  return T;
+}
+
+int pick_mb(int B, int cap) {
+  int mb = 1;
+  while (mb < B && mb < cap) mb *= 2;
+  return mb;
+}
+
+template <int MB>
+cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, cudaStream_t st) {
+  dim3 grid(a.Mc, nact, (a.L + kInvThreads - 1) / kInvThreads);
+  k_wig_inv<MB><<<grid, kInvThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MB, int LT>
+cudaError_t launch_fwd_mb(const WigFwdArgs& a, int nact, cudaStream_t st) {
+  const int threads = ((a.L + 31) / 32) * 32;
+  const size_t smem = (size_t)a.L * MB * sizeof(double2) + (size_t)LT * a.L * sizeof(double) + 4 * LT * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_wig_fwd<MB, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.Mc, nact);
+  k_wig_fwd<MB, LT><<<grid, threads < 32 ? 32 : threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st) {
+  return cudaMemsetAsync(p, 0, (size_t)bytes, st);
+}
+
+static DftArgs dft_args(const GridTables& g, const TransformSpec& t, ColumnArgs c) {
+  DftArgs a;
+  a.G = c.G;
+  a.B = c.B;
+  a.nact = c.nact;
+  a.Ng = 2 * t.N - 1;
+  a.L = c.L;
+  a.Mc = c.Mc;
+  a.mlo = c.mlo;
+  a.n = g.n;
+  a.n1 = g.n1;
+  a.n2 = g.n2;
+  a.tw = g.tw;
+  a.gph = t.gphase;
+  a.scale = 0.0;
+  return a;
+}
+
+cudaError_t launch_dft_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
+                               int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st) {
+  (void)P;
+  DftArgs a = dft_args(g, t, c);
+  a.pix_in = pix;
+  a.pix_out = nullptr;
+  a.pix_sb = pix_sb;
+  a.scale = (2.0 * 3.14159265358979323846 / g.n) * t.gscale;
+  const size_t smem = (size_t)(3 * g.n + a.Ng * c.Mc) * sizeof(double2);
+  dim3 grid(c.L, c.B);
+  cudaError_t e;
+  if (real) {
+    e = cudaFuncSetAttribute(k_dft_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_dft_fwd<true><<<grid, 256, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_dft_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_dft_fwd<false><<<grid, 256, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                               void* pix, int64_t pix_sb, bool real, cudaStream_t st) {
+  (void)P;
+  DftArgs a = dft_args(g, t, c);
+  a.pix_in = nullptr;
+  a.pix_out = pix;
+  a.pix_sb = pix_sb;
+  const size_t smem = (size_t)(3 * g.n + c.nact * c.Mc) * sizeof(double2);
+  dim3 grid(c.L, c.B);
+  cudaError_t e;
+  if (real) {
+    e = cudaFuncSetAttribute(k_dft_inv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_dft_inv<true><<<grid, 256, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_dft_inv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_dft_inv<false><<<grid, 256, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
+                                  ColumnArgs out, cudaStream_t st) {
+  (void)P;
+  WigInvArgs a;
+  a.coef = in.coef;
+  a.s_b = in.s_b;
+  a.s_n = in.s_n;
+  a.s_l = in.s_l;
+  a.mlo_in = in.mlo;
+  a.mult = t.mult_inv;
+  a.nvals = t.nvals;
+  a.nact = t.nact;
+  a.G = out.G;
+  a.B = out.B;
+  a.L = out.L;
+  a.Mc = out.Mc;
+  a.mlo = out.mlo;
+  a.T = rec_tables(g);
+  switch (pick_mb(out.B, 16)) {
+    case 1: return launch_inv_mb<1>(a, t.nact, st);
+    case 2: return launch_inv_mb<2>(a, t.nact, st);
+    case 4: return launch_inv_mb<4>(a, t.nact, st);
+    case 8: return launch_inv_mb<8>(a, t.nact, st);
+    default: return launch_inv_mb<16>(a, t.nact, st);
+  }
+}
+
+cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
+                                  CoefArgs out, cudaStream_t st) {
+  (void)P;
+  WigFwdArgs a;
+  a.G = in.G;
+  a.B = in.B;
+  a.L = in.L;
+  a.Mc = in.Mc;
+  a.mlo = in.mlo;
+  a.nvals = t.nvals;
+  a.nact = t.nact;
+  a.mult = t.mult_fwd;
+  a.out = const_cast<double2*>(out.coef);
+  a.s_b = out.s_b;
+  a.s_n = out.s_n;
+  a.s_l = out.s_l;
+  a.mlo_out = out.mlo;
+  a.MT = g.MT;
+  a.T = rec_tables(g);
+  if (in.L <= 256) {
+    switch (pick_mb(in.B, 16)) {
+      case 1: return launch_fwd_mb<1, 32>(a, t.nact, st);
+      case 2: return launch_fwd_mb<2, 32>(a, t.nact, st);
+      case 4: return launch_fwd_mb<4, 32>(a, t.nact, st);
+      case 8: return launch_fwd_mb<8, 32>(a, t.nact, st);
+      default: return launch_fwd_mb<16, 32>(a, t.nact, st);
+    }
+  } else if (in.L <= 512) {
+    switch (pick_mb(in.B, 8)) {
+      case 1: return launch_fwd_mb<1, 32>(a, t.nact, st);
+      case 2: return launch_fwd_mb<2, 32>(a, t.nact, st);
+      case 4: return launch_fwd_mb<4, 32>(a, t.nact, st);
+      default: return launch_fwd_mb<8, 32>(a, t.nact, st);
+    }
+  } else {
+    switch (pick_mb(in.B, 4)) {
+      case 1: return launch_fwd_mb<1, 16>(a, t.nact, st);
+      case 2: return launch_fwd_mb<2, 16>(a, t.nact, st);
+      default: return launch_fwd_mb<4, 16>(a, t.nact, st);
+    }
+  }
+}
+
+}  // namespace s2w

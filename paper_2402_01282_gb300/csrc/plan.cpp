@@ -1,0 +1,424 @@
+// Host-side construction of a transform plan: parameter validation, the wavelet
+// dictionary (App. A), multiresolution band-limits (Sec. 3.3), and the float64
+// tables the kernels read (MW grids, Wigner-d seed powers, the colatitude
+// quadrature matrices and DFT twiddles).  Everything here runs once per plan.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "s2w_internal.h"
+
+namespace s2w {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+using cplx = std::complex<double>;
+
+// ---------------------------------------------------------------- tiling (App. A)
+
+// 20-point Gauss-Legendre rule on [-1, 1] by Newton iteration on P_20.
+struct GaussLegendre {
+  static constexpr int n = 20;
+  double x[n], w[n];
+  GaussLegendre() {
+    for (int i = 0; i < n; ++i) {
+      double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        double dp = n * (z * p1 - p0) / (z * z - 1.0);
+        double dz = p1 / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-17) break;
+      }
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+};
+
+// Smooth bump s(t) = exp(-1/(1-t^2)) (Eq. A3) and its dilation s_lambda (Eq. A2).
+double bump(double t) { return (t <= -1.0 || t >= 1.0) ? 0.0 : std::exp(-1.0 / (1.0 - t * t)); }
+
+struct Tiling {
+  double lam;
+  double norm;
+  GaussLegendre gl;
+  explicit Tiling(double lam_) : lam(lam_) { norm = integral(1.0 / lam); }
+  double integrand(double u) const {
+    double s = bump(2.0 * lam / (lam - 1.0) * (u - 1.0 / lam) - 1.0);
+    return s * s / u;
+  }
+  // int_a^b s_lambda(u)^2/u du over [a, b] clipped to the support [1/lambda, 1],
+  // composite Gauss-Legendre (64 panels x 20 nodes).
+  double integral(double a, double b = 1.0) const {
+    a = std::max(a, 1.0 / lam);
+    b = std::min(b, 1.0);
+    if (a >= b) return 0.0;
+    const int panels = 64;
+    double h = (b - a) / panels, tot = 0.0;
+    for (int p = 0; p < panels; ++p) {
+      double lo = a + p * h, mid = lo + 0.5 * h, acc = 0.0;
+      for (int i = 0; i < GaussLegendre::n; ++i) acc += gl.w[i] * integrand(mid + 0.5 * h * gl.x[i]);
+      tot += 0.5 * h * acc;
+    }
+    return tot;
+  }
+  // k_lambda(t) (Eq. A4).
+  double k(double t) const {
+    if (t <= 1.0 / lam) return 1.0;
+    if (t >= 1.0) return 0.0;
+    return integral(t) / norm;
+  }
+  // kappa_lambda(t) = sqrt(k(t/lambda) - k(t)) (Eq. A5).  By Eq. A4 the difference is the
+  // single integral of s_lambda^2/u over [t/lambda, t]; evaluating it that way keeps full
+  // relative precision at the support edges, where two values of k near 1 would cancel.
+  double kappa(double t) const {
+    double d = integral(t / lam, t) / norm;
+    return d > 0.0 ? std::sqrt(d) : 0.0;
+  }
+};
+
+// ceil(lambda^e) robust to rounding of exact integer powers.
+int ceil_pow(double lam, int e) {
+  double v = std::pow(lam, e);
+  double r = std::nearbyint(v);
+  if (std::fabs(v - r) < 1e-9 * std::max(1.0, v)) return (int)r;
+  return (int)std::ceil(v);
+}
+
+// Azimuthal tiling zeta_lm (Eq. A6).
+cplx zeta(int l, int m, int N) {
+  bool mu = ((N + m) % 2 + 2) % 2 == 1;
+  int q = std::min(N - 1, l - (((N + l) % 2 == 0) ? 1 : 0));
+  if (!mu || q < 0 || std::abs(m) > q || ((q - m) % 2) != 0) return 0.0;
+  int k = (q - m) / 2;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r *= double(q - k + i) / double(i);
+  r = std::ldexp(r, -q);
+  double v = std::sqrt(r);
+  return ((N - 1) % 2 == 0) ? cplx(v, 0.0) : cplx(0.0, v);
+}
+
+// ---------------------------------------------------------------- grids
+
+// exp(-i p theta_u), theta_u = pi (2u+1)/n, with exact integer argument reduction.
+cplx phase_theta(long p, long u, long n) {
+  long num = ((p * (2 * u + 1)) % (2 * n) + 2 * n) % (2 * n);
+  double a = kPi * double(num) / double(n);
+  return cplx(std::cos(a), -std::sin(a));
+}
+
+double sin_weight_re(long q) { return (q % 2 == 0) ? 2.0 / (1.0 - double(q) * double(q)) : 0.0; }
+double sin_weight_im(long q) { return q == 1 ? 0.5 * kPi : (q == -1 ? -0.5 * kPi : 0.0); }
+
+// Colatitude quadrature matrix for parity sigma (= (-1)^(m+n)): Mq[t][t'] such that
+// int_0^pi G(theta) d(theta) sin(theta) d theta = sum_t (Mq G)_t d(theta_t) for every
+// column G and Wigner function d of that parity band-limited at L (MW sampling).
+// Built column by column from the extend / DFT / sin-weight convolution / inverse
+// DFT / fold steps applied to unit impulses.
+void quad_matrix(int L, int sigma, std::vector<double>& M /* [t][t'] */) {
+  const long n = 2 * L - 1;
+  M.assign((size_t)L * L, 0.0);
+  std::vector<cplx> X(n), H(n), g(n);
+  // w(p + q) for p, q in [-(L-1), L-1]
+  for (int tp = 0; tp < L; ++tp) {
+    // Fourier coefficients of the parity-extended impulse at theta_tp.
+    for (long p = -(L - 1); p <= L - 1; ++p) {
+      cplx v = phase_theta(p, tp, n);
+      if (tp < L - 1) v += double(sigma) * phase_theta(p, n - 1 - tp, n);
+      X[p + L - 1] = v / double(n);
+    }
+    for (long q = -(L - 1); q <= L - 1; ++q) {
+      cplx acc = 0.0;
+      for (long p = -(L - 1); p <= L - 1; ++p) {
+        long k = p + q;
+        double wr = sin_weight_re(k), wi = sin_weight_im(k);
+        if (wr == 0.0 && wi == 0.0) continue;
+        acc += X[p + L - 1] * cplx(wr, wi);
+      }
+      H[q + L - 1] = acc;
+    }
+    for (long u = 0; u < n; ++u) {
+      cplx acc = 0.0;
+      for (long q = -(L - 1); q <= L - 1; ++q) acc += H[q + L - 1] * phase_theta(q, u, n);
+      g[u] = acc / double(n);
+    }
+    for (int t = 0; t < L; ++t) {
+      cplx v = g[t];
+      if (t < L - 1) v += double(sigma) * g[n - 1 - t];
+      M[(size_t)t * L + tp] = v.real();
+    }
+  }
+}
+
+template <class T>
+s2w_status upload(s2w_plan* P, const std::vector<T>& h, T** d, cudaStream_t st, std::string& err) {
+  *d = nullptr;
+  if (h.empty()) return S2W_OK;
+  void* p = nullptr;
+  if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "cudaMalloc failed for a plan table";
+    return S2W_ENOMEM;
+  }
+  P->owned.push_back(p);
+  if (cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    err = "cudaMemcpyAsync failed while uploading a plan table";
+    return S2W_ECUDA;
+  }
+  *d = static_cast<T*>(p);
+  return S2W_OK;
+}
+
+#define S2W_TRY(x)                   \
+  do {                               \
+    s2w_status _s = (x);             \
+    if (_s != S2W_OK) return _s;     \
+  } while (0)
+
+void factorise(int n, int& n1, int& n2) {
+  n1 = 1;
+  n2 = n;
+  for (int a = 2; a * a <= n; ++a)
+    if (n % a == 0) {
+      n1 = a;
+      n2 = n / a;
+    }
+}
+
+s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::string& err) {
+  g.L = L;
+  g.n = 2 * L - 1;
+  factorise(g.n, g.n1, g.n2);
+  const int n = g.n;
+  std::vector<double> wpole(L), cm((size_t)L * n), sm((size_t)L * n), sc((size_t)L * n, 0.0);
+  std::vector<int> ce((size_t)L * n), se((size_t)L * n);
+  for (int b = 0; b < L; ++b) {
+    // half angle beta_b/2 = pi num/(2n); the smaller of sin and cos is evaluated through an
+    // exact complementary argument so both keep full relative precision near the poles.
+    const long num = 2 * b + 1, cnum = n - num;   // pi/2 - beta_b/2 = pi cnum/(2n)
+    double ch, sh;
+    if (2 * num <= n) {
+      sh = std::sin(0.5 * kPi * double(num) / double(n));
+      ch = std::cos(0.5 * kPi * double(num) / double(n));
+    } else {
+      ch = (cnum == 0) ? 0.0 : std::sin(0.5 * kPi * double(cnum) / double(n));
+      sh = (cnum == 0) ? 1.0 : std::cos(0.5 * kPi * double(cnum) / double(n));
+    }
+    // recursion weight: -(1 - cos beta) = -2 sin^2(beta/2) on the northern half,
+    // (1 + cos beta) = 2 cos^2(beta/2) on the southern half (see rec_coeffs).
+    wpole[b] = (2 * num < n) ? -2.0 * sh * sh : 2.0 * ch * ch;
+    // powers as (mantissa in [0.5,1), exponent); zero base gives exact zeros.
+    double vm = 0.5, sv = 0.5;
+    int ve = 1, svx = 1;
+    for (int a = 0; a < n; ++a) {
+      cm[(size_t)b * n + a] = vm;
+      ce[(size_t)b * n + a] = ve;
+      sm[(size_t)b * n + a] = sv;
+      se[(size_t)b * n + a] = svx;
+      int d;
+      vm = std::frexp(vm * ch, &d);
+      ve = (vm == 0.0) ? 0 : ve + d;
+      sv = std::frexp(sv * sh, &d);
+      svx = (sv == 0.0) ? 0 : svx + d;
+    }
+  }
+  for (int l = 0; l < L; ++l) {
+    double v = 1.0;
+    sc[(size_t)l * n] = 1.0;
+    for (int k = 1; k <= 2 * l; ++k) {
+      v *= std::sqrt(double(2 * l - k + 1) / double(k));
+      sc[(size_t)l * n + k] = v;
+    }
+  }
+  std::vector<double> MT((size_t)2 * L * L), M;
+  for (int par = 0; par < 2; ++par) {
+    quad_matrix(L, par == 0 ? 1 : -1, M);
+    for (int t = 0; t < L; ++t)
+      for (int tp = 0; tp < L; ++tp) MT[(size_t)par * L * L + (size_t)tp * L + t] = M[(size_t)t * L + tp];
+  }
+  std::vector<double2> tw(n);
+  for (int e = 0; e < n; ++e) {
+    double a = 2.0 * kPi * double(e) / double(n);
+    tw[e] = make_double2(std::cos(a), std::sin(a));
+  }
+  S2W_TRY(upload(P, wpole, &g.wpole, st, err));
+  S2W_TRY(upload(P, cm, &g.cpow_m, st, err));
+  S2W_TRY(upload(P, ce, &g.cpow_e, st, err));
+  S2W_TRY(upload(P, sm, &g.spow_m, st, err));
+  S2W_TRY(upload(P, se, &g.spow_e, st, err));
+  S2W_TRY(upload(P, sc, &g.sqrtC, st, err));
+  S2W_TRY(upload(P, MT, &g.MT, st, err));
+  S2W_TRY(upload(P, tw, &g.tw, st, err));
+  return S2W_OK;
+}
+
+s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int N, int grid,
+                      const std::vector<int>& nvals, const std::vector<cplx>& minv,
+                      const std::vector<cplx>& mfwd, std::string& err) {
+  t.L = L;
+  t.N = N;
+  t.grid = grid;
+  t.nact = (int)nvals.size();
+  t.nvals_h = nvals;
+  std::vector<double2> a(minv.size()), b(mfwd.size()), ph((size_t)t.nact * (2 * N - 1));
+  for (size_t i = 0; i < minv.size(); ++i) a[i] = make_double2(minv[i].real(), minv[i].imag());
+  for (size_t i = 0; i < mfwd.size(); ++i) b[i] = make_double2(mfwd[i].real(), mfwd[i].imag());
+  const long ng = 2 * N - 1;
+  for (int i = 0; i < t.nact; ++i)
+    for (long gi = 0; gi < ng; ++gi) {
+      long num = ((long)nvals[i] * gi % ng + ng) % ng;
+      double ang = 2.0 * kPi * double(num) / double(ng);
+      ph[(size_t)i * ng + gi] = make_double2(std::cos(ang), std::sin(ang));
+    }
+  t.gscale = 1.0;
+  S2W_TRY(upload(P, nvals, &t.nvals, st, err));
+  S2W_TRY(upload(P, a, &t.mult_inv, st, err));
+  S2W_TRY(upload(P, b, &t.mult_fwd, st, err));
+  S2W_TRY(upload(P, ph, &t.gphase, st, err));
+  return S2W_OK;
+}
+
+}  // namespace
+
+s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::string& err) {
+  if (p.L < 2 || p.L > 1024) { err = "L must satisfy 2 <= L <= 1024"; return S2W_EINVAL; }
+  if (p.N < 1 || p.N > p.L) { err = "N must satisfy 1 <= N <= L"; return S2W_EINVAL; }
+  if (!(p.lambda > 1.0) || !std::isfinite(p.lambda)) { err = "lambda must be > 1"; return S2W_EINVAL; }
+  if (std::abs(p.spin) >= p.L) { err = "|spin| must be < L"; return S2W_EINVAL; }
+  if (p.batch < 1) { err = "batch must be >= 1"; return S2W_EINVAL; }
+  if (p.reality && p.spin != 0) { err = "reality requires spin 0"; return S2W_EINVAL; }
+  if (p.precision != S2W_FP64) { err = "only S2W_FP64 precision is implemented"; return S2W_EUNSUPPORTED; }
+  if (p.precompute != 0) { err = "precompute mode is not implemented"; return S2W_EUNSUPPORTED; }
+  int J = 0;
+  while (ceil_pow(p.lambda, J) < p.L) ++J;
+  if (p.J0 < 0 || p.J0 > J) { err = "J0 must satisfy 0 <= J0 <= J"; return S2W_EINVAL; }
+
+  P->p = p;
+  P->real = p.reality != 0;
+  P->Mc = P->real ? p.L : 2 * p.L - 1;
+  P->mlo = P->real ? 0 : -(p.L - 1);
+  P->J = J;
+  P->L_phi = std::min(ceil_pow(p.lambda, p.J0), p.L);
+  P->nscales = J - p.J0 + 1;
+  for (int j = p.J0; j <= J; ++j) {
+    int Lj = std::min(ceil_pow(p.lambda, j + 1), p.L);
+    P->scale_j.push_back(j);
+    P->Lj.push_back(Lj);
+    P->Nj.push_back(std::min(p.N, Lj));
+  }
+  P->map_elems = (int64_t)p.L * (2 * p.L - 1);
+  P->scal_elems = (int64_t)P->L_phi * (2 * P->L_phi - 1);
+  P->wav_off.assign(1, 0);
+  for (int s = 0; s < P->nscales; ++s)
+    P->wav_off.push_back(P->wav_off.back() + (int64_t)(2 * P->Nj[s] - 1) * P->Lj[s] * (2 * P->Lj[s] - 1));
+  P->wav_elems = P->wav_off.back();
+
+  // grids for every distinct band-limit
+  std::map<int, int> gidx;
+  auto grid_for = [&](int L) -> int {
+    auto it = gidx.find(L);
+    if (it != gidx.end()) return it->second;
+    int id = (int)P->grids.size();
+    P->grids.emplace_back();
+    gidx[L] = id;
+    return id;
+  };
+  grid_for(p.L);
+  grid_for(P->L_phi);
+  for (int s = 0; s < P->nscales; ++s) grid_for(P->Lj[s]);
+  for (auto& kv : gidx) S2W_TRY(build_grid(P, kv.first, st, P->grids[kv.second], err));
+
+  Tiling tile(p.lambda);
+  const int L = p.L, s = p.spin;
+  // spin SHT at L: d^l_{m,-s}, multiplier (-1)^s sqrt((2l+1)/(4 pi)) (MW convention)
+  {
+    std::vector<cplx> mi(L), mf(L);
+    for (int l = 0; l < L; ++l) {
+      double v = (l >= std::abs(s)) ? ((s % 2 == 0) ? 1.0 : -1.0) * std::sqrt((2.0 * l + 1.0) / (4.0 * kPi)) : 0.0;
+      mi[l] = mf[l] = v;
+    }
+    S2W_TRY(build_spec(P, st, P->sht, L, 1, gidx[L], {-s}, mi, mf, err));
+  }
+  // scaling function at L_phi: Phi_l0 = sqrt((2l+1)/(4 pi)) sqrt(k(l / lambda^J0)); the
+  // scaling map is a spin-0 function, so its harmonic multiplier is Phi_l0 (Eq. 29, Eq. 41).
+  {
+    const int LP = P->L_phi;
+    std::vector<cplx> m(LP);
+    double scale = std::pow(p.lambda, p.J0);
+    for (int l = 0; l < LP; ++l)
+      m[l] = (l >= std::abs(s)) ? std::sqrt((2.0 * l + 1.0) / (4.0 * kPi)) * std::sqrt(tile.k(l / scale)) : 0.0;
+    S2W_TRY(build_spec(P, st, P->scal_t, LP, 1, gidx[LP], {0}, m, m, err));
+  }
+  P->wav_t.resize(P->nscales);
+  P->raw_t.resize(P->nscales);
+  for (int sc = 0; sc < P->nscales; ++sc) {
+    const int j = P->scale_j[sc], Lj = P->Lj[sc], Nj = P->Nj[sc];
+    const double lj = std::pow(p.lambda, j);
+    std::vector<int> act, all;
+    for (int n = -(Nj - 1); n <= Nj - 1; ++n) {
+      all.push_back(n);
+      if (((p.N + n) % 2 + 2) % 2 == 1) act.push_back(n);
+    }
+    // Psi^j_ln = sqrt((2l+1)/(8 pi^2)) kappa(l / lambda^j) zeta_ln (Eq. A9)
+    std::vector<cplx> mi((size_t)Lj * act.size()), mf((size_t)Lj * act.size());
+    for (int l = 0; l < Lj; ++l) {
+      double kap = (l >= std::abs(s)) ? tile.kappa(l / lj) : 0.0;
+      for (size_t i = 0; i < act.size(); ++i) {
+        cplx psi = std::sqrt((2.0 * l + 1.0) / (8.0 * kPi * kPi)) * kap * zeta(l, act[i], p.N);
+        mi[(size_t)l * act.size() + i] = std::conj(psi);
+        mf[(size_t)l * act.size() + i] = psi;
+      }
+    }
+    S2W_TRY(build_spec(P, st, P->wav_t[sc], Lj, Nj, gidx[Lj], act, mi, mf, err));
+    P->wav_t[sc].gscale = 2.0 * kPi / (2.0 * Nj - 1.0);
+    std::vector<cplx> ri((size_t)Lj * all.size()), rf((size_t)Lj * all.size(), 1.0);
+    for (int l = 0; l < Lj; ++l)
+      for (size_t i = 0; i < all.size(); ++i) ri[(size_t)l * all.size() + i] = (2.0 * l + 1.0) / (8.0 * kPi * kPi);
+    S2W_TRY(build_spec(P, st, P->raw_t[sc], Lj, Nj, gidx[Lj], all, ri, rf, err));
+    P->raw_t[sc].gscale = 2.0 * kPi / (2.0 * Nj - 1.0);
+  }
+
+  // workspaces
+  const int64_t B = p.batch;
+  int64_t gmax = B * (int64_t)L * P->Mc;
+  for (int sc = 0; sc < P->nscales; ++sc) {
+    int64_t Mcj = P->real ? P->Lj[sc] : 2 * P->Lj[sc] - 1;
+    gmax = std::max(gmax, B * (2 * P->Nj[sc] - 1) * (int64_t)P->Lj[sc] * Mcj);
+  }
+  P->g_ws_elems = gmax;
+  void* q = nullptr;
+  if (cudaMalloc(&q, gmax * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); err = "workspace allocation failed"; return S2W_ENOMEM; }
+  P->owned.push_back(q);
+  P->g_ws = (double2*)q;
+  if (cudaMalloc(&q, B * (int64_t)L * P->Mc * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); err = "workspace allocation failed"; return S2W_ENOMEM; }
+  P->owned.push_back(q);
+  P->flm_ws = (double2*)q;
+  if (cudaMalloc(&q, sizeof(int)) != cudaSuccess) { cudaGetLastError(); err = "workspace allocation failed"; return S2W_ENOMEM; }
+  P->owned.push_back(q);
+  P->err_word = (int*)q;
+  if (cudaMemsetAsync(P->err_word, 0, sizeof(int), st) != cudaSuccess) { err = "memset failed"; return S2W_ECUDA; }
+  if (cudaStreamSynchronize(st) != cudaSuccess) { err = "plan upload failed"; return S2W_ECUDA; }
+  return S2W_OK;
+}
+
+void free_plan(s2w_plan* P) {
+  for (void* q : P->owned) cudaFree(q);
+  P->owned.clear();
+}
+
+}  // namespace s2w

@@ -1,0 +1,115 @@
+// Internal structures shared by the host plan builder and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/s2w.h"
+
+namespace s2w {
+
+// Tables for one MW band-limit L (shared by every transform run at that L).
+// Device pointers; rows are padded to the row lengths given.
+struct GridTables {
+  int L = 0;            // band-limit (L beta/theta rings, n = 2L-1 azimuthal samples)
+  int n = 0;            // 2L-1
+  int n1 = 1, n2 = 1;   // DFT factorisation n = n1 * n2 (n1 = 1 for primes)
+  double* wpole = nullptr;     // [L] -2 sin^2(beta_b/2) (beta < pi/2) or 2 cos^2(beta_b/2) (beta >= pi/2)
+  double* cpow_m = nullptr;    // [L][n] mantissa of cos(beta_b/2)^a, a = 0..n-1
+  int* cpow_e = nullptr;       // [L][n] binary exponent
+  double* spow_m = nullptr;    // [L][n] sin(beta_b/2)^a
+  int* spow_e = nullptr;
+  double* sqrtC = nullptr;     // [L][n] sqrt(binom(2l, k)), k = 0..2l
+  double* MT = nullptr;        // [2][L][L] quadrature matrices, transposed: MT[par][t'][t]
+  double2* tw = nullptr;       // [n] exp(+2 pi i e / n)
+};
+
+// One Wigner / SHT transform instance: band-limit, the n values it carries and the
+// per-(l, n) multipliers that fuse the harmonic products into the contraction.
+struct TransformSpec {
+  int L = 0, N = 0;          // band-limits (N = 1 for the SHT)
+  int grid = -1;             // index into Plan::grids
+  int nact = 0;              // number of n values carried
+  int* nvals = nullptr;      // device [nact]
+  std::vector<int> nvals_h;
+  double2* mult_inv = nullptr;  // [L][nact] multiplier applied before the inverse contraction
+  double2* mult_fwd = nullptr;  // [L][nact] multiplier applied after the forward contraction
+  double2* gphase = nullptr;    // [nact][2N-1] exp(+i n gamma_g)
+  double gscale = 1.0;          // gamma quadrature factor 2 pi/(2N-1) (1 for the SHT)
+};
+
+struct s2w_plan_impl;
+
+}  // namespace s2w
+
+struct s2w_plan {
+  s2w_params p{};
+  int Mc = 0, mlo = 0;                 // m storage at L
+  bool real = false;
+  int nscales = 0, J = 0, L_phi = 1;
+  std::vector<int> scale_j, Lj, Nj;
+  std::vector<int64_t> wav_off;        // per map, elements
+  int64_t map_elems = 0, wav_elems = 0, scal_elems = 0;
+
+  std::vector<s2w::GridTables> grids;  // one per distinct band-limit
+  s2w::TransformSpec sht;              // spin SHT at L (n = -spin)
+  s2w::TransformSpec scal_t;           // scaling function synthesis at L_phi (n = 0)
+  std::vector<s2w::TransformSpec> wav_t;   // wavelet scales (active n only, Psi multipliers)
+  std::vector<s2w::TransformSpec> raw_t;   // raw Wigner transforms per scale (all n)
+
+  double2* flm_ws = nullptr;           // [batch][L][Mc] harmonic workspace
+  double2* g_ws = nullptr;             // largest [batch][nact or 2N-1][L_j][Mc_j] column buffer
+  int64_t g_ws_elems = 0;
+  int* err_word = nullptr;             // device error word
+  cudaStream_t last_stream = nullptr;
+  std::vector<void*> owned;            // every device allocation, freed on destroy
+
+  // tracing
+  bool trace_on = false;
+  std::vector<cudaEvent_t> trace_ev;   // pool, two per recorded launch
+  struct TraceRec { int kind; double flops; };
+  std::vector<TraceRec> trace_rec;
+};
+
+namespace s2w {
+
+// Host-side plan construction (plan.cpp).
+s2w_status build_plan(const s2w_params& p, cudaStream_t stream, s2w_plan* plan, std::string& err);
+void free_plan(s2w_plan* plan);
+
+// Kernel launchers (kernels_fp64.cu).  All asynchronous on `st`.
+struct ColumnArgs {
+  // A column buffer G[b][nact][L][Mc] (complex) on the MW SO(3)/S2 grid at L.
+  double2* G;
+  int B, nact, L, Mc, mlo;
+};
+
+// Pixel -> columns: azimuthal DFT (length 2L-1) and gamma DFT (length 2N-1), scaled by
+// (2pi/(2L-1)) (2pi/(2N-1)).  Pixel layout [b][2N-1][L][2L-1]; for the SHT N = 1.
+// pix_sb = elements between consecutive maps of the pixel array.
+cudaError_t launch_dft_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
+                               const void* pix, int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st);
+// Columns -> pixels: inverse gamma and alpha DFTs (no scaling).
+cudaError_t launch_dft_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
+                               ColumnArgs c, void* pix, int64_t pix_sb, bool real, cudaStream_t st);
+
+// Coefficient source for the inverse contraction: element (b, n_idx, l, m) is
+// coef[b*s_b + n_idx*s_n + l*s_l + (m - mlo)] (s_n = 0 to share one f_lm across n).
+struct CoefArgs {
+  const double2* coef;   // written through (const_cast) when used as an output
+  int64_t s_b, s_n, s_l;
+  int mlo;
+};
+// G[b][n][beta][m] = sum_l coef(b,n,l,m) * mult_inv[l][n] * d^l_{m n}(beta)
+cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
+                                  CoefArgs in, ColumnArgs out, cudaStream_t st);
+// out(b,n,l,m) += mult_fwd[l][n] * sum_beta (M^{par(m+n)} G)[beta] d^l_{m n}(beta)
+cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
+                                  ColumnArgs in, CoefArgs out, cudaStream_t st);
+
+cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st);
+
+}  // namespace s2w
