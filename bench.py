@@ -115,6 +115,27 @@ def cpu_baseline_sample():
     return dt, err
 
 
+PRECISIONS = {"fp64": 0, "fp64_native": 3}
+PRECISION_DOC = {
+    "fp64": "float64 accuracy: Wigner-d recursion and l-contractions in float64, DFTs and "
+            "colatitude quadrature in compensated float32 pairs",
+    "fp64_native": "plain float64: every step in native float64",
+}
+
+
+def time_steps(torch, plan, f, wav, scal, f2, flush, stream, steps):
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        plan.forward(f, wav, scal)
+        plan.inverse(wav, scal, f2)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -125,7 +146,7 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    plan = s2w.Plan(L, N, LAM, J0, reality=True, batch=B)
+    plan = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[args.precision])
     flm, f = make_inputs(torch, plan, rank)
     wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -142,26 +163,17 @@ def run_ours(args, world, rank, local):
     sampler = ClockSampler(str(gpu_id)) if rank == 0 else None
     plan.trace(True, capacity=64 * (args.steps + 1))
     plan.trace_reset()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        plan.forward(f, wav, scal)
-        plan.inverse(wav, scal, f2)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    step_ms = time_steps(torch, plan, f, wav, scal, f2, flush, stream, args.steps)
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
     plan.check()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     trace = plan.trace_read()
     plan.trace(False)
@@ -201,6 +213,22 @@ def run_ours(args, world, rank, local):
         e2e_ms = float(t.item())
     e2e_err = float(np.abs(out_host.numpy() - f_host.numpy()).max() / np.abs(f_host.numpy()).max())
 
+    # the plain float64 path on the same inputs, for comparison (not the headline)
+    other = {}
+    if args.precision != "fp64_native" and not args.no_compare:
+        nat = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS["fp64_native"])
+        for _ in range(2):
+            nat.forward(f, wav, scal)
+            nat.inverse(wav, scal, f2)
+        ms = time_steps(torch, nat, f, wav, scal, f2, flush, stream, max(2, args.steps // 2))
+        nat.check()
+        flm3 = plan.empty_flm()
+        plan.sht_forward(f2, flm3)
+        other["fp64_native"] = {"value": B * len(ms) / (sum(ms) * 1e-3), "ms_per_step": sum(ms) / len(ms),
+                                "max_rel_err": float(np.abs(flm3.cpu().numpy() - flm).max() / np.abs(flm).max()),
+                                "precision": PRECISION_DOC["fp64_native"]}
+        nat.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -220,9 +248,11 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded band-limited maps, the paper's random-signal protocol)",
         "config": {"workload": WORKLOAD, "L": L, "N": N, "lambda": LAM, "J0": J0, "spin": 0,
-                   "maps_per_gpu": B, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "maps_per_gpu": B, "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MB write)"},
+        "precision_detail": PRECISION_DOC[args.precision],
         "max_rel_err": err,
+        "other_modes": other,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
@@ -278,6 +308,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the plain float64 path")
+    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":

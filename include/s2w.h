@@ -55,7 +55,12 @@ typedef enum {
   S2W_ENONFINITE = 6     /* a kernel detected a non-finite input */
 } s2w_status;
 
-typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2 } s2w_precision;
+/* S2W_FP64         float64 accuracy (1e-11 target): Wigner-d recursion and l-contractions in
+ *                  float64; DFTs in compensated float32 pairs (error-free transformations).
+ * S2W_FP64_NATIVE  every step in native float64: the plain float64 path, kept as the
+ *                  baseline the other modes are compared with.
+ * S2W_FP32_SPLIT, S2W_BF16  reduced-precision modes (not implemented in this build). */
+typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3 } s2w_precision;
 
 /* Problem statement of the sphere transform (Algorithm 1; Sec. 3.3; App. A).
  *   L        angular band-limit, harmonic degrees l < L            (2 <= L <= 1024)
@@ -64,7 +69,7 @@ typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2 } s2w_precision;
  *   spin     spin of the signal, |spin| < L
  *   reality  1 for real spin-0 signals (real pixel arrays, m >= 0 stored)
  *   batch    number of maps transformed per call                   (>= 1)
- *   precision  s2w_precision; only S2W_FP64 is implemented in this build
+ *   precision  s2w_precision (S2W_FP64 or S2W_FP64_NATIVE in this build)
  *   precompute 0 (Wigner-d functions by recursion inside the kernels)
  *   lambda   dilation factor lambda > 1 (Eq. A2); scale j uses band-limit
  *            L_j = min(ceil(lambda^(j+1)), L) and N_j = min(N, L_j), j = J0..J with J

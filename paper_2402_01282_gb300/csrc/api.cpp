@@ -110,7 +110,9 @@ s2w_status fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, i
   ColumnArgs c = cols(P, t.nact, t.L);
   {
     TraceScope ts(P, st, K_DFT_FWD, P->trace_on ? dft_flops(P, t) : 0.0);
-    S2W_CUDA(launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st), "azimuthal DFT (forward)");
+    S2W_CUDA(P->native64 ? launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st)
+                         : launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st),
+             "azimuthal DFT (forward)");
   }
   {
     TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
@@ -130,7 +132,9 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
   }
   {
     TraceScope ts(P, st, K_DFT_INV, P->trace_on ? dft_flops(P, t) : 0.0);
-    S2W_CUDA(launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st), "azimuthal DFT (inverse)");
+    S2W_CUDA(P->native64 ? launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st)
+                         : launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st),
+             "azimuthal DFT (inverse)");
   }
   return S2W_OK;
 }

@@ -9,6 +9,7 @@
 //                            against the weighted columns, products fused in the epilogue.
 #include <math.h>
 
+#include "comp32.cuh"
 #include "s2w_internal.h"
 
 namespace s2w {
@@ -333,10 +334,13 @@ struct WigFwdArgs {
   int64_t s_b, s_n, s_l;
   int mlo_out;
   const double* MT;      // [2][L][L]
+  const float2* MT2;     // the same as float pairs (compensated quadrature)
   RecTables T;
 };
 
-template <int MB, int LT>
+// C32: the quadrature M^{par} G runs in compensated float32 pairs (see comp32.cuh) instead of
+// native float64; the recursion and the l-contraction are float64 either way.
+template <int MB, int LT, bool C32>
 __global__ void k_wig_fwd(WigFwdArgs a) {
   extern __shared__ double smd[];
   const int L = a.L;
@@ -359,11 +363,35 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < L * MB; idx += blockDim.x) {
       const int tt = idx / MB, mp = idx - tt * MB, bm = map0 + mp;
-      Gs[idx] = (bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * L + tt) * a.Mc + mi] : make_double2(0.0, 0.0);
+      const double2 gv = (bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * L + tt) * a.Mc + mi] : make_double2(0.0, 0.0);
+      if (C32) reinterpret_cast<float4*>(Gs)[idx] = split(gv);
+      else Gs[idx] = gv;
     }
     __syncthreads();
     // colatitude quadrature: Gs <- M^{par} Gs
-    {
+    if (C32) {
+      const float2* MT2 = a.MT2 + (size_t)par * L * L;
+      const float4* G4 = reinterpret_cast<const float4*>(Gs);
+      Acc ar[MB], ai[MB];
+#pragma unroll
+      for (int k = 0; k < MB; ++k) ar[k] = ai[k] = Acc{0.f, 0.f};
+      if (t < L) {
+        for (int tp = 0; tp < L; ++tp) {
+          const float2 w = MT2[(size_t)tp * L + t];
+#pragma unroll
+          for (int k = 0; k < MB; ++k) {
+            const float4 gv = G4[tp * MB + k];
+            acc_add(ar[k], gv.x, gv.y, w.x, w.y);
+            acc_add(ai[k], gv.z, gv.w, w.x, w.y);
+          }
+        }
+      }
+      __syncthreads();
+      if (t < L) {
+#pragma unroll
+        for (int k = 0; k < MB; ++k) Gs[t * MB + k] = make_double2(to_double(ar[k]), to_double(ai[k]));
+      }
+    } else {
       double2 acc[MB];
 #pragma unroll
       for (int k = 0; k < MB; ++k) acc[k] = make_double2(0.0, 0.0);
@@ -453,15 +481,20 @@ cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int MB, int LT>
-cudaError_t launch_fwd_mb(const WigFwdArgs& a, int nact, cudaStream_t st) {
+template <int MB, int LT, bool C32>
+cudaError_t launch_fwd_k(const WigFwdArgs& a, int nact, cudaStream_t st) {
   const int threads = ((a.L + 31) / 32) * 32;
   const size_t smem = (size_t)a.L * MB * sizeof(double2) + (size_t)LT * a.L * sizeof(double) + 4 * LT * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_wig_fwd<MB, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_wig_fwd<MB, LT, C32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.Mc, nact);
-  k_wig_fwd<MB, LT><<<grid, threads < 32 ? 32 : threads, smem, st>>>(a);
+  k_wig_fwd<MB, LT, C32><<<grid, threads < 32 ? 32 : threads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int MB, int LT>
+cudaError_t launch_fwd_mb(const WigFwdArgs& a, int nact, bool c32, cudaStream_t st) {
+  return c32 ? launch_fwd_k<MB, LT, true>(a, nact, st) : launch_fwd_k<MB, LT, false>(a, nact, st);
 }
 
 }  // namespace
@@ -562,7 +595,6 @@ cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const 
 
 cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
                                   CoefArgs out, cudaStream_t st) {
-  (void)P;
   WigFwdArgs a;
   a.G = in.G;
   a.B = in.B;
@@ -578,27 +610,29 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
   a.s_l = out.s_l;
   a.mlo_out = out.mlo;
   a.MT = g.MT;
+  a.MT2 = g.MT2;
   a.T = rec_tables(g);
+  const bool c32 = !P->native64;
   if (in.L <= 256) {
     switch (pick_mb(in.B, 16)) {
-      case 1: return launch_fwd_mb<1, 32>(a, t.nact, st);
-      case 2: return launch_fwd_mb<2, 32>(a, t.nact, st);
-      case 4: return launch_fwd_mb<4, 32>(a, t.nact, st);
-      case 8: return launch_fwd_mb<8, 32>(a, t.nact, st);
-      default: return launch_fwd_mb<16, 32>(a, t.nact, st);
+      case 1: return launch_fwd_mb<1, 32>(a, t.nact, c32, st);
+      case 2: return launch_fwd_mb<2, 32>(a, t.nact, c32, st);
+      case 4: return launch_fwd_mb<4, 32>(a, t.nact, c32, st);
+      case 8: return launch_fwd_mb<8, 32>(a, t.nact, c32, st);
+      default: return launch_fwd_mb<16, 32>(a, t.nact, c32, st);
     }
   } else if (in.L <= 512) {
     switch (pick_mb(in.B, 8)) {
-      case 1: return launch_fwd_mb<1, 32>(a, t.nact, st);
-      case 2: return launch_fwd_mb<2, 32>(a, t.nact, st);
-      case 4: return launch_fwd_mb<4, 32>(a, t.nact, st);
-      default: return launch_fwd_mb<8, 32>(a, t.nact, st);
+      case 1: return launch_fwd_mb<1, 32>(a, t.nact, c32, st);
+      case 2: return launch_fwd_mb<2, 32>(a, t.nact, c32, st);
+      case 4: return launch_fwd_mb<4, 32>(a, t.nact, c32, st);
+      default: return launch_fwd_mb<8, 32>(a, t.nact, c32, st);
     }
   } else {
     switch (pick_mb(in.B, 4)) {
-      case 1: return launch_fwd_mb<1, 16>(a, t.nact, st);
-      case 2: return launch_fwd_mb<2, 16>(a, t.nact, st);
-      default: return launch_fwd_mb<4, 16>(a, t.nact, st);
+      case 1: return launch_fwd_mb<1, 16>(a, t.nact, c32, st);
+      case 2: return launch_fwd_mb<2, 16>(a, t.nact, c32, st);
+      default: return launch_fwd_mb<4, 16>(a, t.nact, c32, st);
     }
   }
 }

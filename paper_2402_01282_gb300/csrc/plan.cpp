@@ -190,6 +190,12 @@ s2w_status upload(s2w_plan* P, const std::vector<T>& h, T** d, cudaStream_t st, 
     if (_s != S2W_OK) return _s;     \
   } while (0)
 
+// float64 complex -> (re_hi, re_lo, im_hi, im_lo) float pair representation
+float4 split4(double2 v) {
+  float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 void factorise(int n, int& n1, int& n2) {
   n1 = 1;
   n2 = n;
@@ -252,9 +258,11 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
       for (int tp = 0; tp < L; ++tp) MT[(size_t)par * L * L + (size_t)tp * L + t] = M[(size_t)t * L + tp];
   }
   std::vector<double2> tw(n);
+  std::vector<float4> tw4(n);
   for (int e = 0; e < n; ++e) {
     double a = 2.0 * kPi * double(e) / double(n);
     tw[e] = make_double2(std::cos(a), std::sin(a));
+    tw4[e] = split4(tw[e]);
   }
   S2W_TRY(upload(P, wpole, &g.wpole, st, err));
   S2W_TRY(upload(P, cm, &g.cpow_m, st, err));
@@ -262,8 +270,15 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
   S2W_TRY(upload(P, sm, &g.spow_m, st, err));
   S2W_TRY(upload(P, se, &g.spow_e, st, err));
   S2W_TRY(upload(P, sc, &g.sqrtC, st, err));
+  std::vector<float2> MT2(MT.size());
+  for (size_t i = 0; i < MT.size(); ++i) {
+    float h = (float)MT[i];
+    MT2[i] = make_float2(h, (float)(MT[i] - (double)h));
+  }
   S2W_TRY(upload(P, MT, &g.MT, st, err));
+  S2W_TRY(upload(P, MT2, &g.MT2, st, err));
   S2W_TRY(upload(P, tw, &g.tw, st, err));
+  S2W_TRY(upload(P, tw4, &g.tw4, st, err));
   return S2W_OK;
 }
 
@@ -276,6 +291,7 @@ s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int
   t.nact = (int)nvals.size();
   t.nvals_h = nvals;
   std::vector<double2> a(minv.size()), b(mfwd.size()), ph((size_t)t.nact * (2 * N - 1));
+  std::vector<float4> ph4(ph.size());
   for (size_t i = 0; i < minv.size(); ++i) a[i] = make_double2(minv[i].real(), minv[i].imag());
   for (size_t i = 0; i < mfwd.size(); ++i) b[i] = make_double2(mfwd[i].real(), mfwd[i].imag());
   const long ng = 2 * N - 1;
@@ -284,12 +300,14 @@ s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int
       long num = ((long)nvals[i] * gi % ng + ng) % ng;
       double ang = 2.0 * kPi * double(num) / double(ng);
       ph[(size_t)i * ng + gi] = make_double2(std::cos(ang), std::sin(ang));
+      ph4[(size_t)i * ng + gi] = split4(ph[(size_t)i * ng + gi]);
     }
   t.gscale = 1.0;
   S2W_TRY(upload(P, nvals, &t.nvals, st, err));
   S2W_TRY(upload(P, a, &t.mult_inv, st, err));
   S2W_TRY(upload(P, b, &t.mult_fwd, st, err));
   S2W_TRY(upload(P, ph, &t.gphase, st, err));
+  S2W_TRY(upload(P, ph4, &t.gphase4, st, err));
   return S2W_OK;
 }
 
@@ -302,13 +320,17 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   if (std::abs(p.spin) >= p.L) { err = "|spin| must be < L"; return S2W_EINVAL; }
   if (p.batch < 1) { err = "batch must be >= 1"; return S2W_EINVAL; }
   if (p.reality && p.spin != 0) { err = "reality requires spin 0"; return S2W_EINVAL; }
-  if (p.precision != S2W_FP64) { err = "only S2W_FP64 precision is implemented"; return S2W_EUNSUPPORTED; }
+  if (p.precision != S2W_FP64 && p.precision != S2W_FP64_NATIVE) {
+    err = "precision mode not implemented in this build";
+    return S2W_EUNSUPPORTED;
+  }
   if (p.precompute != 0) { err = "precompute mode is not implemented"; return S2W_EUNSUPPORTED; }
   int J = 0;
   while (ceil_pow(p.lambda, J) < p.L) ++J;
   if (p.J0 < 0 || p.J0 > J) { err = "J0 must satisfy 0 <= J0 <= J"; return S2W_EINVAL; }
 
   P->p = p;
+  P->native64 = p.precision == S2W_FP64_NATIVE;
   P->real = p.reality != 0;
   P->Mc = P->real ? p.L : 2 * p.L - 1;
   P->mlo = P->real ? 0 : -(p.L - 1);

@@ -24,7 +24,9 @@ struct GridTables {
   int* spow_e = nullptr;
   double* sqrtC = nullptr;     // [L][n] sqrt(binom(2l, k)), k = 0..2l
   double* MT = nullptr;        // [2][L][L] quadrature matrices, transposed: MT[par][t'][t]
+  float2* MT2 = nullptr;       // the same as float pairs (hi, lo)
   double2* tw = nullptr;       // [n] exp(+2 pi i e / n)
+  float4* tw4 = nullptr;       // [n] the same as float pairs (re_hi, re_lo, im_hi, im_lo)
 };
 
 // One Wigner / SHT transform instance: band-limit, the n values it carries and the
@@ -38,6 +40,7 @@ struct TransformSpec {
   double2* mult_inv = nullptr;  // [L][nact] multiplier applied before the inverse contraction
   double2* mult_fwd = nullptr;  // [L][nact] multiplier applied after the forward contraction
   double2* gphase = nullptr;    // [nact][2N-1] exp(+i n gamma_g)
+  float4* gphase4 = nullptr;    // the same as float pairs
   double gscale = 1.0;          // gamma quadrature factor 2 pi/(2N-1) (1 for the SHT)
 };
 
@@ -47,6 +50,7 @@ struct s2w_plan_impl;
 
 struct s2w_plan {
   s2w_params p{};
+  bool native64 = false;               // every step in native float64 (S2W_FP64_NATIVE)
   int Mc = 0, mlo = 0;                 // m storage at L
   bool real = false;
   int nscales = 0, J = 0, L_phi = 1;
@@ -111,5 +115,11 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
                                   ColumnArgs in, CoefArgs out, cudaStream_t st);
 
 cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st);
+
+// Compensated-float32 versions of the two DFT launchers (kernels_dft_c32.cu); same contract.
+cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, const void* pix, int64_t pix_sb,
+                                bool real, ColumnArgs c, cudaStream_t st);
+cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, ColumnArgs c, void* pix,
+                                int64_t pix_sb, bool real, cudaStream_t st);
 
 }  // namespace s2w

@@ -12,6 +12,7 @@ from oracle import filters, harmonic, wavelet
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
+MODES = [0, 3]          # S2W_FP64 (compensated-float32 DFT and quadrature), S2W_FP64_NATIVE
 
 
 def rel(a, b):
@@ -30,10 +31,11 @@ def internal_flm(flm_full, L, real):
     return flm_full[:, L - 1:] if real else flm_full
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("L,spin,real,B", [(2, 0, True, 1), (8, 0, True, 3), (17, 0, False, 2), (33, 0, True, 2),
                                            (16, 1, False, 1), (11, 2, False, 3), (64, 0, True, 1)])
-def test_sht_parity(lib, L, spin, real, B):
-    plan = lib.Plan(L, min(2, L), 2.0, 0, spin=spin, reality=real, batch=B)
+def test_sht_parity(lib, L, spin, real, B, mode):
+    plan = lib.Plan(L, min(2, L), 2.0, 0, spin=spin, reality=real, batch=B, precision=mode)
     rng = synth.rng_for(500, L)
     # arbitrary samples: pins the exact MW forward operator, not only its band-limited action
     f = synth.pixels_random((B, L, 2 * L - 1), rng, complex_=not real)
@@ -54,9 +56,10 @@ def test_sht_parity(lib, L, spin, real, B):
     plan.check()
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("L,N,real,B", [(33, 4, True, 2), (20, 3, False, 1), (9, 9, False, 2)])
-def test_wigner_parity(lib, L, N, real, B):
-    plan = lib.Plan(L, N, 2.0, 0, reality=real, batch=B)
+def test_wigner_parity(lib, L, N, real, B, mode):
+    plan = lib.Plan(L, N, 2.0, 0, reality=real, batch=B, precision=mode)
     rng = synth.rng_for(501, L)
     for s in range(plan.nscales):
         Lj, Nj = plan.Lj[s], plan.Nj[s]
@@ -90,8 +93,8 @@ def lib_empty(plan, s):
     return torch.empty((plan.batch, *plan.scale_shape(s)), dtype=plan.dtype, device="cuda")
 
 
-def _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg):
-    plan = lib.Plan(L, N, lam, J0, spin=spin, reality=real, batch=B)
+def _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg, mode=0):
+    plan = lib.Plan(L, N, lam, J0, spin=spin, reality=real, batch=B, precision=mode)
     flms = [synth.flm_random(L, synth.rng_for(cfg, b), spin=spin, reality=real) for b in range(B)]
     fs = [harmonic.sht_inverse(x, L, spin) for x in flms]
     if real:
@@ -105,14 +108,15 @@ def _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg):
     return plan, f, wav, scal, f2.cpu().numpy()
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("L,N,lam,J0,spin,real,B,cfg", [
     (32, 4, 2.0, 0, 0, True, 1, 1),          # the L=32, N=4 single-map workload
     (16, 3, 2.0, 1, 2, False, 2, 502),        # spin 2, complex
     (23, 5, 1.7, 1, 0, True, 3, 503),         # non-dyadic lambda, ragged sizes
     (10, 1, 2.0, 0, 0, True, 1, 504),         # axisymmetric N = 1
 ])
-def test_wavelet_parity(lib, L, N, lam, J0, spin, real, B, cfg):
-    plan, f, wav, scal, f2 = _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg)
+def test_wavelet_parity(lib, L, N, lam, J0, spin, real, B, cfg, mode):
+    plan, f, wav, scal, f2 = _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg, mode)
     wv = wav.cpu().numpy()
     sc = scal.cpu().numpy()
     for b in range(B):
@@ -145,17 +149,23 @@ def test_synthesis_on_arbitrary_coefficients(lib):
 
 def test_full_size_256(lib):
     """The L=256, N=8, lambda=2, J0=2 workload of 16 real maps in the launch configuration the
-    benchmark times: map 0 against the oracle on every output, and the round trip of all 16."""
+    benchmark times, in both float64 modes: map 0 against the oracle on every output, and the
+    round trip of all 16."""
     L, N, lam, J0, B = 256, 8, 2.0, 2, 16
-    plan, f, wav, scal, f2 = _wavelet_case(lib, L, N, lam, J0, 0, True, B, 2)
-    W_ref, Wp_ref = wavelet.analysis(f[0], L, N, lam, J0, 0, True)
-    wv = wav[0].cpu().numpy()
-    for s, w_ref in enumerate(W_ref):
-        got = wv[plan.wav_offsets[s]:plan.wav_offsets[s + 1]].reshape(plan.scale_shape(s))
-        assert rel(got, w_ref) < TOL, s
-    assert rel(scal[0].cpu().numpy(), Wp_ref) < TOL
-    for b in range(B):
-        assert rel(f2[b], f[b]) < TOL, b
+    ref = None
+    for mode in MODES:
+        plan, f, wav, scal, f2 = _wavelet_case(lib, L, N, lam, J0, 0, True, B, 2, mode)
+        if ref is None:
+            ref = wavelet.analysis(f[0], L, N, lam, J0, 0, True)
+        W_ref, Wp_ref = ref
+        wv = wav[0].cpu().numpy()
+        for s, w_ref in enumerate(W_ref):
+            got = wv[plan.wav_offsets[s]:plan.wav_offsets[s + 1]].reshape(plan.scale_shape(s))
+            assert rel(got, w_ref) < TOL, (mode, s)
+        assert rel(scal[0].cpu().numpy(), Wp_ref) < TOL
+        for b in range(B):
+            assert rel(f2[b], f[b]) < TOL, (mode, b)
+        plan.close()
 
 
 def test_full_size_steps_256(lib):
