@@ -46,3 +46,40 @@ __device__ __forceinline__ float4 split(double2 v) {
 }
 
 }  // namespace s2w
+
+namespace s2w {
+
+// float64 -> pair with integer operations only (no conversion on the float64 pipe):
+// hi = v truncated to 24 significant bits, lo = the remaining 29 mantissa bits truncated to
+// 24, so hi + lo = v to 2^-48 relative.  |v| < 2^-126 returns (0, 0) and lo is dropped once it
+// falls below the float range (|v| < ~2^-75): both are far below any term these kernels sum.
+__device__ __forceinline__ float2 split1_bits(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hi32 = (unsigned int)(u >> 32), lo32 = (unsigned int)u;
+  const int E = (int)((hi32 >> 20) & 0x7FFu) - 1023;
+  if (E < -126) return make_float2(0.f, 0.f);
+  const unsigned int sign = hi32 & 0x80000000u;
+  const unsigned int mant23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+  const float h = __uint_as_float(sign | ((unsigned int)(E + 127) << 23) | mant23);
+  const unsigned int r = lo32 & 0x1FFFFFFFu;
+  float l = 0.f;
+  if (r != 0u) {
+    const int lead = 31 - __clz((int)r);
+    const int field = E - 52 + lead + 127;
+    if (field > 0) {
+      const unsigned int m = (lead >= 23 ? (r >> (lead - 23)) : (r << (23 - lead))) & 0x7FFFFFu;
+      l = __uint_as_float(sign | ((unsigned int)field << 23) | m);
+    }
+  }
+  return make_float2(h, l);
+}
+
+}  // namespace s2w
+
+namespace s2w {
+// two accumulators (real, imaginary) -> (re_hi, re_lo, im_hi, im_lo)
+__device__ __forceinline__ float4 pack_pair(Acc re, Acc im) {
+  const float2 r = renorm(re), i = renorm(im);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+}  // namespace s2w

@@ -261,10 +261,14 @@ struct WigInvArgs {
 constexpr int kInvThreads = 128;
 constexpr int kInvLT = 32;
 
-template <int MB>
+// C32: the sum over l runs in compensated float32 pairs (comp32.cuh): coefficient tiles are
+// split into pairs once per block and each float64 recursion value d^l_mn(beta) is split with
+// integer operations, so the float64 pipe only carries the recursion itself.
+template <int MB, bool C32>
 __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
   __shared__ double2 Fs[kInvLT * MB];
   __shared__ double cA[kInvLT], cKn[kInvLT], cKs[kInvLT], cC[kInvLT];
+  float4* F4 = reinterpret_cast<float4*>(Fs);
   const int mi = blockIdx.x, ni = blockIdx.y;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int L = a.L;
@@ -273,9 +277,15 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
   const double wb = (b < L) ? a.T.wpole[b] : 0.0;
   const double* cK = (2 * (2 * b + 1) < a.T.n) ? cKn : cKs;
   for (int map0 = 0; map0 < a.B; map0 += MB) {
-    double2 acc[MB];
+    double2 acc[C32 ? 1 : MB];
+    Acc ar[C32 ? MB : 1], ai[C32 ? MB : 1];
+    if (C32) {
 #pragma unroll
-    for (int k = 0; k < MB; ++k) acc[k] = make_double2(0.0, 0.0);
+      for (int k = 0; k < MB; ++k) ar[k] = ai[k] = Acc{0.f, 0.f};
+    } else {
+#pragma unroll
+      for (int k = 0; k < (C32 ? 1 : MB); ++k) acc[k] = make_double2(0.0, 0.0);
+    }
     double v = 0.0, vp = 0.0;
     int q = 0;
     if (b < L && l0 < L) wigner_seed(a.T, b, l0, m, nn, v, q);
@@ -288,18 +298,29 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
         if (bm < a.B)
           f = cmul(a.coef[(int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_in)],
                    a.mult[(int64_t)l * a.nact + ni]);
-        Fs[idx] = f;
+        if (C32) F4[idx] = split(f);
+        else Fs[idx] = f;
       }
       for (int i = threadIdx.x; i < cnt; i += blockDim.x) rec_coeffs(ls + i, m, nn, cA[i], cKn[i], cKs[i], cC[i]);
       __syncthreads();
       if (b < L) {
         for (int i = 0; i < cnt; ++i) {
           if (q == 0) {
+            if (C32) {
+              const float2 d = split1_bits(v);
 #pragma unroll
-            for (int k = 0; k < MB; ++k) {
-              const double2 f = Fs[i * MB + k];
-              acc[k].x = fma(f.x, v, acc[k].x);
-              acc[k].y = fma(f.y, v, acc[k].y);
+              for (int k = 0; k < MB; ++k) {
+                const float4 f = F4[i * MB + k];
+                acc_add(ar[k], f.x, f.y, d.x, d.y);
+                acc_add(ai[k], f.z, f.w, d.x, d.y);
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < (C32 ? 1 : MB); ++k) {
+                const double2 f = Fs[i * MB + k];
+                acc[k].x = fma(f.x, v, acc[k].x);
+                acc[k].y = fma(f.y, v, acc[k].y);
+              }
             }
           }
           const double x = fma(cA[i], wb, cK[i]);
@@ -318,7 +339,12 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
 #pragma unroll
       for (int k = 0; k < MB; ++k) {
         const int bm = map0 + k;
-        if (bm < a.B) a.G[(((int64_t)bm * a.nact + ni) * L + b) * a.Mc + mi] = acc[k];
+        if (bm < a.B) {
+          double2 r;
+          if (C32) r = make_double2(to_double(ar[k]), to_double(ai[k]));
+          else r = acc[C32 ? 0 : k];
+          a.G[(((int64_t)bm * a.nact + ni) * L + b) * a.Mc + mi] = r;
+        }
       }
     }
   }
@@ -338,8 +364,10 @@ struct WigFwdArgs {
   RecTables T;
 };
 
-// C32: the quadrature M^{par} G runs in compensated float32 pairs (see comp32.cuh) instead of
-// native float64; the recursion and the l-contraction are float64 either way.
+// C32: the quadrature M^{par} G and the contraction over beta run in compensated float32
+// pairs (comp32.cuh); the weighted columns stay as pairs in shared memory and each recursion
+// value is split with integer operations.  Without C32 every step is native float64.  The
+// Wigner-d recursion is float64 either way.
 template <int MB, int LT, bool C32>
 __global__ void k_wig_fwd(WigFwdArgs a) {
   extern __shared__ double smd[];
@@ -388,8 +416,9 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
       }
       __syncthreads();
       if (t < L) {
+        float4* G4w = reinterpret_cast<float4*>(Gs);
 #pragma unroll
-        for (int k = 0; k < MB; ++k) Gs[t * MB + k] = make_double2(to_double(ar[k]), to_double(ai[k]));
+        for (int k = 0; k < MB; ++k) G4w[t * MB + k] = pack_pair(ar[k], ai[k]);
       }
     } else {
       double2 acc[MB];
@@ -422,7 +451,8 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
       __syncthreads();
       if (t < L) {
         for (int i = 0; i < cnt; ++i) {
-          Ds[i * L + t] = (q == 0) ? v : 0.0;
+          if (C32) reinterpret_cast<float2*>(Ds)[i * L + t] = (q == 0) ? split1_bits(v) : make_float2(0.f, 0.f);
+          else Ds[i * L + t] = (q == 0) ? v : 0.0;
           const double x = fma(cA[i], wb, cK[i]);
           const double vn = fma(x, v, -cC[i] * vp);
           vp = v;
@@ -437,13 +467,27 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
       __syncthreads();
       for (int idx = threadIdx.x; idx < cnt * MB; idx += blockDim.x) {
         const int i = idx / MB, mp = idx - i * MB, bm = map0 + mp, l = ls + i;
-        const double* drow = Ds + (size_t)i * L;
         double re = 0.0, im = 0.0;
-        for (int bb = 0; bb < L; ++bb) {
-          const double d = drow[bb];
-          const double2 gv = Gs[bb * MB + mp];
-          re = fma(d, gv.x, re);
-          im = fma(d, gv.y, im);
+        if (C32) {
+          const float2* drow = reinterpret_cast<const float2*>(Ds) + (size_t)i * L;
+          const float4* G4 = reinterpret_cast<const float4*>(Gs);
+          Acc ar{0.f, 0.f}, ai{0.f, 0.f};
+          for (int bb = 0; bb < L; ++bb) {
+            const float2 d = drow[bb];
+            const float4 gv = G4[bb * MB + mp];
+            acc_add(ar, gv.x, gv.y, d.x, d.y);
+            acc_add(ai, gv.z, gv.w, d.x, d.y);
+          }
+          re = to_double(ar);
+          im = to_double(ai);
+        } else {
+          const double* drow = Ds + (size_t)i * L;
+          for (int bb = 0; bb < L; ++bb) {
+            const double d = drow[bb];
+            const double2 gv = Gs[bb * MB + mp];
+            re = fma(d, gv.x, re);
+            im = fma(d, gv.y, im);
+          }
         }
         if (bm < a.B) {
           const double2 r = cmul(make_double2(re, im), a.mult[(int64_t)l * a.nact + ni]);
@@ -475,9 +519,10 @@ int pick_mb(int B, int cap) {
 }
 
 template <int MB>
-cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, cudaStream_t st) {
+cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, bool c32, cudaStream_t st) {
   dim3 grid(a.Mc, nact, (a.L + kInvThreads - 1) / kInvThreads);
-  k_wig_inv<MB><<<grid, kInvThreads, 0, st>>>(a);
+  if (c32) k_wig_inv<MB, true><<<grid, kInvThreads, 0, st>>>(a);
+  else k_wig_inv<MB, false><<<grid, kInvThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -568,7 +613,6 @@ cudaError_t launch_dft_inverse(const s2w_plan* P, const GridTables& g, const Tra
 
 cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
                                   ColumnArgs out, cudaStream_t st) {
-  (void)P;
   WigInvArgs a;
   a.coef = in.coef;
   a.s_b = in.s_b;
@@ -585,11 +629,11 @@ cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const 
   a.mlo = out.mlo;
   a.T = rec_tables(g);
   switch (pick_mb(out.B, 16)) {
-    case 1: return launch_inv_mb<1>(a, t.nact, st);
-    case 2: return launch_inv_mb<2>(a, t.nact, st);
-    case 4: return launch_inv_mb<4>(a, t.nact, st);
-    case 8: return launch_inv_mb<8>(a, t.nact, st);
-    default: return launch_inv_mb<16>(a, t.nact, st);
+    case 1: return launch_inv_mb<1>(a, t.nact, !P->native64, st);
+    case 2: return launch_inv_mb<2>(a, t.nact, !P->native64, st);
+    case 4: return launch_inv_mb<4>(a, t.nact, !P->native64, st);
+    case 8: return launch_inv_mb<8>(a, t.nact, !P->native64, st);
+    default: return launch_inv_mb<16>(a, t.nact, !P->native64, st);
   }
 }
 
