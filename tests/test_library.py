@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared_symbols():
     hdr = open(os.path.join(ROOT, "include", "s2w.h")).read()
-    return sorted(set(re.findall(r"\b(s2w_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"^(?:s2w_status|const char\s*\*)\s+(s2w_[a-z_0-9]+)\s*\(", hdr, re.M)))
 
 
 @pytest.fixture(scope="module")
