@@ -125,6 +125,19 @@ s2w_status s2w_wigner_forward(const s2w_plan* plan, int scale, const void* f, vo
 s2w_status s2w_wigner_inverse(const s2w_plan* plan, int scale, const void* flmn, void* f,
                               void* stream);
 
+/* The inverse spin SHT of s2w_sht_inverse, for callers that cannot allocate device memory
+ * when they need it (a host application that owns every device allocation and forbids new
+ * ones after start-up, or code running while a CUDA graph is captured, where cudaMalloc is not
+ * allowed) and cannot borrow the plan's workspace because another call on the same plan may be
+ * running.  The paper has no counterpart: it is a deployment variant of the Eq. 3 transform.
+ * Its m-column scratch is a fixed 16 MiB device array inside the library (held by every GPU
+ * that loads it, until exit): the call allocates nothing and returns S2W_EINVAL when
+ * batch * L * Mc exceeds 1,048,576 complex elements (e.g. 16 real maps at L = 256).  The first
+ * call on a device looks the array's device address up (make it before any stream capture).
+ * All calls share the array; calls whose work overlaps on the GPU race on it.  Same arguments,
+ * layouts and results as s2w_sht_inverse. */
+s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f, void* stream);
+
 /* Synchronises the plan's last stream, then reads and clears the device error word.
  * Returns S2W_OK, S2W_ECUDA (asynchronous CUDA error) or the recorded status. */
 s2w_status s2w_check(const s2w_plan* plan);

@@ -25,7 +25,7 @@ STATUS = {0: "S2W_OK", 1: "S2W_EINVAL", 2: "S2W_ENOMEM", 3: "S2W_ECUDA", 4: "S2W
 EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forward", "s2w_inverse",
            "s2w_sht_forward", "s2w_sht_inverse", "s2w_wigner_forward", "s2w_wigner_inverse",
            "s2w_check", "s2w_last_error", "s2w_version", "s2w_trace_enable", "s2w_trace_reset",
-           "s2w_trace_read", "s2w_kernel_name"]
+           "s2w_trace_read", "s2w_kernel_name", "s2w_sht_inverse_static"]
 KERNEL_KINDS = 4
 
 
@@ -57,6 +57,7 @@ def load(path: str = LIB_PATH):
     lib.s2w_inverse.argtypes = [vp, vp, vp, vp, vp]
     lib.s2w_sht_forward.argtypes = [vp, vp, vp, vp]
     lib.s2w_sht_inverse.argtypes = [vp, vp, vp, vp]
+    lib.s2w_sht_inverse_static.argtypes = [vp, vp, vp, vp]
     lib.s2w_wigner_forward.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.s2w_wigner_inverse.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.s2w_check.argtypes = [vp]
@@ -184,6 +185,11 @@ class Plan:
     def sht_inverse(self, flm, f, stream=None):
         _check(_lib.s2w_sht_inverse(self._h, _ptr(flm, False, "flm"), _ptr(f, self.real, "f"),
                                     _stream(stream)))
+
+    def sht_inverse_static(self, flm, f, stream=None):
+        """s2w_sht_inverse with its scratch in the library's fixed device array (allocates nothing)."""
+        _check(_lib.s2w_sht_inverse_static(self._h, _ptr(flm, False, "flm"), _ptr(f, self.real, "f"),
+                                           _stream(stream)))
 
     def wigner_forward(self, s: int, f, flmn, stream=None):
         _check(_lib.s2w_wigner_forward(self._h, s, _ptr(f, self.real, "f"), _ptr(flmn, False, "flmn"),

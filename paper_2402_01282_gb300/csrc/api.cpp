@@ -143,6 +143,11 @@ size_t pix_bytes(const s2w_plan* P) { return P->real ? sizeof(double) : sizeof(d
 
 }  // namespace
 
+namespace s2w {
+// Lets other translation units report through s2w_last_error().
+s2w_status record_error(s2w_status s, const std::string& msg) { return fail(s, msg); }
+}  // namespace s2w
+
 extern "C" {
 
 const char* s2w_last_error(void) { return g_last_error.c_str(); }

@@ -80,6 +80,9 @@ struct s2w_plan {
 
 namespace s2w {
 
+// Records a failure message for s2w_last_error() and returns s (api.cpp).
+s2w_status record_error(s2w_status s, const std::string& msg);
+
 // Host-side plan construction (plan.cpp).
 s2w_status build_plan(const s2w_params& p, cudaStream_t stream, s2w_plan* plan, std::string& err);
 void free_plan(s2w_plan* plan);
