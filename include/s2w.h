@@ -125,6 +125,39 @@ s2w_status s2w_wigner_forward(const s2w_plan* plan, int scale, const void* f, vo
 s2w_status s2w_wigner_inverse(const s2w_plan* plan, int scale, const void* flmn, void* f,
                               void* stream);
 
+/* ---- ball: Fourier-Laguerre radial transform and spherical-Laguerre transform ----------
+ * (Sec. 2.3, Eqs. 6-11.)  Radial basis K_p(r) = sqrt(p!/(p+2)!) e^{-r/(2 tau)} tau^{-3/2}
+ * L^(2)_p(r/tau) (Eq. 6), radial band-limit p < P.  The radial samples are the P generalised
+ * Gauss-Laguerre nodes r_i = tau x_i (roots of L^(2)_P) with weights omega_i such that the
+ * forward transform f_p = sum_i omega_i K_p(r_i) f(r_i) (Eq. 7) is exact for band-limited
+ * signals; the inverse is f(r_i) = sum_p K_p(r_i) f_p (Eq. 8).
+ * Layouts (b = batch index): radial samples of harmonic coefficients f_r [b][P node][L][Mc] and
+ * Fourier-Laguerre coefficients f_p [b][P][L][Mc], complex; ball pixels [b][P node][L][2L-1]
+ * (real when reality = 1, else complex).  The plan owns a workspace of batch*P*L*Mc complex. */
+typedef struct {
+  int L;          /* angular band-limit (2 <= L <= 1024) */
+  int P;          /* radial band-limit (2 <= P <= 256) */
+  int spin, reality, batch, precision;   /* as in s2w_params (precision S2W_FP64 or S2W_FP64_NATIVE) */
+  double tau;     /* Laguerre scale tau > 0 */
+} s2w_ball_params;
+
+typedef struct s2w_ball_plan s2w_ball_plan;
+
+/* Builds the radial quadrature and matrices in float64 on the host and an SHT plan for
+ * batch*P maps; blocks until uploads complete. */
+s2w_status s2w_ball_plan_create(const s2w_ball_params* params, void* stream, s2w_ball_plan** out);
+s2w_status s2w_ball_plan_destroy(s2w_ball_plan* plan);
+/* Copies the nodes r_i and weights omega_i (P doubles each, HOST pointers, may be NULL). */
+s2w_status s2w_ball_nodes(const s2w_ball_plan* plan, double* r, double* omega);
+/* Eq. 7 on every angular coefficient column: f_r -> f_p. */
+s2w_status s2w_laguerre_forward(const s2w_ball_plan* plan, const void* f_r, void* f_p, void* stream);
+/* Eq. 8: f_p -> f_r. */
+s2w_status s2w_laguerre_inverse(const s2w_ball_plan* plan, const void* f_p, void* f_r, void* stream);
+/* Z (Eq. 10): ball pixels -> f_lmp = Laguerre-forward of the per-node spin SHT. */
+s2w_status s2w_ball_sl_forward(const s2w_ball_plan* plan, const void* f, void* flmp, void* stream);
+/* Z^-1 (Eq. 11): f_lmp -> ball pixels. */
+s2w_status s2w_ball_sl_inverse(const s2w_ball_plan* plan, const void* flmp, void* f, void* stream);
+
 /* The inverse spin SHT of s2w_sht_inverse, for callers that cannot allocate device memory
  * when they need it (a host application that owns every device allocation and forbids new
  * ones after start-up, or code running while a CUDA graph is captured, where cudaMalloc is not

@@ -25,7 +25,9 @@ STATUS = {0: "S2W_OK", 1: "S2W_EINVAL", 2: "S2W_ENOMEM", 3: "S2W_ECUDA", 4: "S2W
 EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forward", "s2w_inverse",
            "s2w_sht_forward", "s2w_sht_inverse", "s2w_wigner_forward", "s2w_wigner_inverse",
            "s2w_check", "s2w_last_error", "s2w_version", "s2w_trace_enable", "s2w_trace_reset",
-           "s2w_trace_read", "s2w_kernel_name", "s2w_sht_inverse_static"]
+           "s2w_trace_read", "s2w_kernel_name", "s2w_sht_inverse_static", "s2w_ball_plan_create",
+           "s2w_ball_plan_destroy", "s2w_ball_nodes", "s2w_laguerre_forward", "s2w_laguerre_inverse",
+           "s2w_ball_sl_forward", "s2w_ball_sl_inverse"]
 KERNEL_KINDS = 4
 
 
@@ -33,6 +35,11 @@ class S2WError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class BallParams(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("P", ctypes.c_int), ("spin", ctypes.c_int), ("reality", ctypes.c_int),
+                ("batch", ctypes.c_int), ("precision", ctypes.c_int), ("tau", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -67,6 +74,11 @@ def load(path: str = LIB_PATH):
     lib.s2w_trace_reset.argtypes = [vp]
     lib.s2w_trace_read.argtypes = [vp, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]
+    lib.s2w_ball_plan_create.argtypes = [ctypes.POINTER(BallParams), vp, ctypes.POINTER(vp)]
+    lib.s2w_ball_plan_destroy.argtypes = [vp]
+    lib.s2w_ball_nodes.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    for nm in ("s2w_laguerre_forward", "s2w_laguerre_inverse", "s2w_ball_sl_forward", "s2w_ball_sl_inverse"):
+        getattr(lib, nm).argtypes = [vp, vp, vp, vp]
     lib.s2w_kernel_name.argtypes = [ctypes.c_int]
     lib.s2w_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -221,6 +233,65 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             _lib.s2w_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BallPlan:
+    """Fourier-Laguerre (Eqs. 6-8) and spherical-Laguerre (Eqs. 9-11) transforms of a batch of
+    ball signals with angular band-limit L and radial band-limit P."""
+
+    def __init__(self, L: int, P: int, tau: float = 1.0, spin: int = 0, reality: bool = False,
+                 batch: int = 1, precision: int = S2W_FP64, stream=None):
+        lib = load()
+        self.params = BallParams(L, P, spin, int(reality), batch, precision, float(tau))
+        h = ctypes.c_void_p()
+        _check(lib.s2w_ball_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.L, self.P, self.tau, self.batch = L, P, tau, batch
+        self.real = bool(reality) and spin == 0
+        self.Mc = L if self.real else 2 * L - 1
+
+    def nodes(self):
+        import numpy as np
+        r = (ctypes.c_double * self.P)()
+        om = (ctypes.c_double * self.P)()
+        _check(_lib.s2w_ball_nodes(self._h, r, om))
+        return np.array(r[:]), np.array(om[:])
+
+    def empty_coeffs(self, device="cuda"):
+        import torch
+        return torch.empty((self.batch, self.P, self.L, self.Mc), dtype=torch.complex128, device=device)
+
+    def empty_pixels(self, device="cuda"):
+        import torch
+        dt = torch.float64 if self.real else torch.complex128
+        return torch.empty((self.batch, self.P, self.L, 2 * self.L - 1), dtype=dt, device=device)
+
+    def laguerre_forward(self, f_r, f_p, stream=None):
+        _check(_lib.s2w_laguerre_forward(self._h, _ptr(f_r, False, "f_r"), _ptr(f_p, False, "f_p"),
+                                         _stream(stream)))
+
+    def laguerre_inverse(self, f_p, f_r, stream=None):
+        _check(_lib.s2w_laguerre_inverse(self._h, _ptr(f_p, False, "f_p"), _ptr(f_r, False, "f_r"),
+                                         _stream(stream)))
+
+    def sl_forward(self, f, flmp, stream=None):
+        _check(_lib.s2w_ball_sl_forward(self._h, _ptr(f, self.real, "f"), _ptr(flmp, False, "flmp"),
+                                        _stream(stream)))
+
+    def sl_inverse(self, flmp, f, stream=None):
+        _check(_lib.s2w_ball_sl_inverse(self._h, _ptr(flmp, False, "flmp"), _ptr(f, self.real, "f"),
+                                        _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.s2w_ball_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -657,7 +657,18 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
   a.MT2 = g.MT2;
   a.T = rec_tables(g);
   const bool c32 = !P->native64;
+  // Compensated blocks use 16-row recursion tiles so that two blocks fit on an SM (one
+  // block's float64 recursion phase overlaps the other's float32 contraction phase).
   if (in.L <= 256) {
+    if (c32) {
+      switch (pick_mb(in.B, 16)) {
+        case 1: return launch_fwd_mb<1, 16>(a, t.nact, c32, st);
+        case 2: return launch_fwd_mb<2, 16>(a, t.nact, c32, st);
+        case 4: return launch_fwd_mb<4, 16>(a, t.nact, c32, st);
+        case 8: return launch_fwd_mb<8, 16>(a, t.nact, c32, st);
+        default: return launch_fwd_mb<16, 16>(a, t.nact, c32, st);
+      }
+    }
     switch (pick_mb(in.B, 16)) {
       case 1: return launch_fwd_mb<1, 32>(a, t.nact, c32, st);
       case 2: return launch_fwd_mb<2, 32>(a, t.nact, c32, st);
