@@ -40,6 +40,7 @@ PEAKS = {
     "fp64_native": (FP64_PEAK_TFLOPS, "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (probe measured "
                     "1.196 TFLOP/s FP64 at 1987 MHz)"),
 }
+PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64"]
 
 
 def dist_init():
@@ -124,11 +125,15 @@ def cpu_baseline_sample():
     return dt, err
 
 
-PRECISIONS = {"fp64": 0, "fp64_native": 3}
+PRECISIONS = {"fp64": 0, "fp64_native": 3, "fp32_split": 1, "bf16": 2}
 PRECISION_DOC = {
-    "fp64": "float64 accuracy: Wigner-d recursion and l-contractions in float64, DFTs and "
-            "colatitude quadrature in compensated float32 pairs",
+    "fp64": "float64 accuracy: Wigner-d recursion in float64; l-contractions, DFTs and colatitude "
+            "quadrature in compensated float32 pairs",
     "fp64_native": "plain float64: every step in native float64",
+    "fp32_split": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, fp16 hi/lo operands "
+                  "(3 MMAs), float32 accumulation; compensated-float32 DFTs",
+    "bf16": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, bf16 operands, float32 "
+            "accumulation; compensated-float32 DFTs",
 }
 
 
@@ -222,21 +227,24 @@ def run_ours(args, world, rank, local):
         e2e_ms = float(t.item())
     e2e_err = float(np.abs(out_host.numpy() - f_host.numpy()).max() / np.abs(f_host.numpy()).max())
 
-    # the plain float64 path on the same inputs, for comparison (not the headline)
+    # the other precision modes on the same inputs, for comparison (not the headline)
     other = {}
-    if args.precision != "fp64_native" and not args.no_compare:
-        nat = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS["fp64_native"])
-        for _ in range(2):
-            nat.forward(f, wav, scal)
-            nat.inverse(wav, scal, f2)
-        ms = time_steps(torch, nat, f, wav, scal, f2, flush, stream, max(2, args.steps // 2))
-        nat.check()
-        flm3 = plan.empty_flm()
-        plan.sht_forward(f2, flm3)
-        other["fp64_native"] = {"value": B * len(ms) / (sum(ms) * 1e-3), "ms_per_step": sum(ms) / len(ms),
-                                "max_rel_err": float(np.abs(flm3.cpu().numpy() - flm).max() / np.abs(flm).max()),
-                                "precision": PRECISION_DOC["fp64_native"]}
-        nat.close()
+    if not args.no_compare:
+        for name in ("fp64_native", "fp32_split", "bf16"):
+            if name == args.precision:
+                continue
+            alt = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[name])
+            for _ in range(2):
+                alt.forward(f, wav, scal)
+                alt.inverse(wav, scal, f2)
+            ms = time_steps(torch, alt, f, wav, scal, f2, flush, stream, max(2, args.steps // 2))
+            alt.check()
+            flm3 = plan.empty_flm()
+            plan.sht_forward(f2, flm3)
+            other[name] = {"value": B * len(ms) / (sum(ms) * 1e-3), "ms_per_step": sum(ms) / len(ms),
+                           "max_rel_err": float(np.abs(flm3.cpu().numpy() - flm).max() / np.abs(flm).max()),
+                           "precision": PRECISION_DOC[name]}
+            alt.close()
 
     if rank != 0:
         if dist:

@@ -111,12 +111,13 @@ s2w_status fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, i
   {
     TraceScope ts(P, st, K_DFT_FWD, P->trace_on ? dft_flops(P, t) : 0.0);
     S2W_CUDA(P->native64 ? launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st)
-                         : launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st),
+                         : launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st, t.tc != nullptr),
              "azimuthal DFT (forward)");
   }
   {
     TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
-    S2W_CUDA(launch_wigner_forward(P, g, t, c, out, st), "forward contraction");
+    S2W_CUDA(t.tc ? launch_tc_forward(P, g, t, c, out, st) : launch_wigner_forward(P, g, t, c, out, st),
+             "forward contraction");
   }
   return S2W_OK;
 }
@@ -128,12 +129,13 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
   ColumnArgs c = cols(P, t.nact, t.L);
   {
     TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
-    S2W_CUDA(launch_wigner_inverse(P, g, t, in, c, st), "inverse contraction");
+    S2W_CUDA(t.tc ? launch_tc_inverse(P, g, t, in, c, st) : launch_wigner_inverse(P, g, t, in, c, st),
+             "inverse contraction");
   }
   {
     TraceScope ts(P, st, K_DFT_INV, P->trace_on ? dft_flops(P, t) : 0.0);
     S2W_CUDA(P->native64 ? launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st)
-                         : launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st),
+                         : launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr),
              "azimuthal DFT (inverse)");
   }
   return S2W_OK;
@@ -285,6 +287,7 @@ s2w_status s2w_wigner_forward(const s2w_plan* cP, int scale, const void* f, void
   if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
   s2w_plan* P = const_cast<s2w_plan*>(cP);
   if (scale < 0 || scale >= P->nscales) return fail(S2W_EINVAL, "scale index out of range");
+  if (P->tensor) return fail(S2W_EUNSUPPORTED, "the raw Wigner transforms run in the float64 modes only");
   s2w_status s;
   if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(flmn, false, "flmn"))) return s;
   cudaStream_t st = (cudaStream_t)stream;
@@ -299,6 +302,7 @@ s2w_status s2w_wigner_inverse(const s2w_plan* cP, int scale, const void* flmn, v
   if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
   s2w_plan* P = const_cast<s2w_plan*>(cP);
   if (scale < 0 || scale >= P->nscales) return fail(S2W_EINVAL, "scale index out of range");
+  if (P->tensor) return fail(S2W_EUNSUPPORTED, "the raw Wigner transforms run in the float64 modes only");
   s2w_status s;
   if ((s = check_ptr(f, P->real, "f")) || (s = check_ptr(flmn, false, "flmn"))) return s;
   cudaStream_t st = (cudaStream_t)stream;

@@ -270,6 +270,14 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
   S2W_TRY(upload(P, sm, &g.spow_m, st, err));
   S2W_TRY(upload(P, se, &g.spow_e, st, err));
   S2W_TRY(upload(P, sc, &g.sqrtC, st, err));
+  g.Lb = ((L + 127) / 128) * 128;
+  {
+    double mx = 0.0;
+    for (double v : MT) mx = std::max(mx, std::fabs(v));
+    int e = 0;
+    std::frexp(mx, &e);
+    g.qscale = std::ldexp(1.0, 14 - e);   // packed quadrature entries below 2^14
+  }
   std::vector<float2> MT2(MT.size());
   for (size_t i = 0; i < MT.size(); ++i) {
     float h = (float)MT[i];
@@ -311,6 +319,82 @@ s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int
   return S2W_OK;
 }
 
+template <class T>
+s2w_status alloc_dev(s2w_plan* P, size_t n, T** d, std::string& err) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "device allocation of the packed Wigner-d tables failed";
+    return S2W_ENOMEM;
+  }
+  P->owned.push_back(q);
+  *d = static_cast<T*>(q);
+  return S2W_OK;
+}
+
+// Reduced-precision modes: packed Wigner-d tiles for the wavelet-scale Wigner transforms
+// (cached per band-limit and n set, so scales with equal (L_j, N_j) share them) and packed
+// quadrature matrices.  The spin SHT and the scaling transform stay on the float64-accurate
+// path: Y f sets the accuracy of every small high-l coefficient the top scales see, and with a
+// steep spectrum a 16-bit quantisation relative to f_00 would swamp them.
+s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+  const bool split = P->p.precision == S2W_FP32_SPLIT;
+  for (GridTables& g : P->grids) {
+    const size_t n = (size_t)2 * g.Lb * g.Lb;
+    S2W_TRY(alloc_dev(P, n, &g.Q_hi, err));
+    S2W_TRY(alloc_dev(P, n, &g.Q_lo, err));   // quadrature entries are pairs in both modes
+    if (launch_tc_build_quad(g, split, st) != cudaSuccess) {
+      err = "quadrature packing kernel failed to launch";
+      return S2W_ECUDA;
+    }
+  }
+  std::map<std::pair<int, std::vector<int>>, TcTable*> cache;
+  std::vector<TransformSpec*> specs;
+  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+  for (TransformSpec* t : specs) {
+    auto key = std::make_pair(t->L, t->nvals_h);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      t->tc = it->second;
+      continue;
+    }
+    const GridTables& g = P->grids[t->grid];
+    const int L = t->L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
+    TcTable* tab = new TcTable();
+    P->tc_tables.push_back(tab);
+    tab->Lb = g.Lb;
+    std::vector<int64_t> off((size_t)Mc * t->nact, 0);
+    std::vector<int> kl((size_t)Mc * t->nact, 0);
+    int64_t run = 0;
+    for (int mi = 0; mi < Mc; ++mi)
+      for (int ni = 0; ni < t->nact; ++ni) {
+        const int l0 = std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni]));
+        if (l0 >= L) continue;
+        const int l0a = l0 & ~15, k = ((L - l0a + 127) / 128) * 128;
+        off[(size_t)mi * t->nact + ni] = run;
+        kl[(size_t)mi * t->nact + ni] = k;
+        run += (int64_t)g.Lb * k;
+        tab->klmax = std::max(tab->klmax, k);
+      }
+    tab->elems = run;
+    S2W_TRY(upload(P, off, &tab->off, st, err));
+    S2W_TRY(upload(P, kl, &tab->kl, st, err));
+    S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_hi, err));
+    S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_hi, err));
+    if (split) {
+      S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_lo, err));
+      S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_lo, err));
+    }
+    if (launch_tc_build(g, *t, *tab, Mc, mlo, split, st) != cudaSuccess) {
+      err = "Wigner-d table kernel failed to launch";
+      return S2W_ECUDA;
+    }
+    cache[key] = tab;
+    t->tc = tab;
+  }
+  return S2W_OK;
+}
+
 }  // namespace
 
 s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::string& err) {
@@ -320,8 +404,13 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   if (std::abs(p.spin) >= p.L) { err = "|spin| must be < L"; return S2W_EINVAL; }
   if (p.batch < 1) { err = "batch must be >= 1"; return S2W_EINVAL; }
   if (p.reality && p.spin != 0) { err = "reality requires spin 0"; return S2W_EINVAL; }
-  if (p.precision != S2W_FP64 && p.precision != S2W_FP64_NATIVE) {
-    err = "precision mode not implemented in this build";
+  if (p.precision != S2W_FP64 && p.precision != S2W_FP64_NATIVE && p.precision != S2W_FP32_SPLIT &&
+      p.precision != S2W_BF16) {
+    err = "unknown precision mode";
+    return S2W_EINVAL;
+  }
+  if ((p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16) && p.L > 256) {
+    err = "the reduced-precision tensor-core modes support L <= 256 in this build";
     return S2W_EUNSUPPORTED;
   }
   if (p.precompute != 0) { err = "precompute mode is not implemented"; return S2W_EUNSUPPORTED; }
@@ -331,6 +420,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
 
   P->p = p;
   P->native64 = p.precision == S2W_FP64_NATIVE;
+  P->tensor = p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16;
   P->real = p.reality != 0;
   P->Mc = P->real ? p.L : 2 * p.L - 1;
   P->mlo = P->real ? 0 : -(p.L - 1);
@@ -415,6 +505,8 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     P->raw_t[sc].gscale = 2.0 * kPi / (2.0 * Nj - 1.0);
   }
 
+  if (P->tensor) S2W_TRY(build_tc_tables(P, st, err));
+
   // workspaces
   const int64_t B = p.batch;
   int64_t gmax = B * (int64_t)L * P->Mc;
@@ -441,6 +533,8 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
 void free_plan(s2w_plan* P) {
   for (void* q : P->owned) cudaFree(q);
   P->owned.clear();
+  for (TcTable* t : P->tc_tables) delete t;
+  P->tc_tables.clear();
 }
 
 }  // namespace s2w

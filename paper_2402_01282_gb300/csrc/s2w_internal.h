@@ -27,6 +27,20 @@ struct GridTables {
   float2* MT2 = nullptr;       // the same as float pairs (hi, lo)
   double2* tw = nullptr;       // [n] exp(+2 pi i e / n)
   float4* tw4 = nullptr;       // [n] the same as float pairs (re_hi, re_lo, im_hi, im_lo)
+  // reduced-precision modes: quadrature matrices packed for the tensor cores
+  int Lb = 0;                  // L rounded up to 128
+  double qscale = 1.0;         // power-of-two scale of the packed quadrature entries
+  uint16_t* Q_hi = nullptr;    // [2][Lb/128][128 x Lb] core-matrix packed (fp16 hi or bf16)
+  uint16_t* Q_lo = nullptr;    // lo parts (the quadrature is a pair in both modes)
+};
+
+// Packed Wigner-d tiles of one transform for the tensor-core contractions (kernels_tc.cu).
+struct TcTable {
+  int Lb = 0, klmax = 0;
+  int64_t* off = nullptr;      // device [Mc * nact] element offset of tile (m, n)
+  int* kl = nullptr;           // device [Mc * nact] padded l extent (multiple of 128; 0 if empty)
+  uint16_t *inv_hi = nullptr, *inv_lo = nullptr, *fwd_hi = nullptr, *fwd_lo = nullptr;
+  int64_t elems = 0;
 };
 
 // One Wigner / SHT transform instance: band-limit, the n values it carries and the
@@ -42,6 +56,7 @@ struct TransformSpec {
   double2* gphase = nullptr;    // [nact][2N-1] exp(+i n gamma_g)
   float4* gphase4 = nullptr;    // the same as float pairs
   double gscale = 1.0;          // gamma quadrature factor 2 pi/(2N-1) (1 for the SHT)
+  const TcTable* tc = nullptr;  // reduced-precision modes: packed tiles (shared between specs)
 };
 
 struct s2w_plan_impl;
@@ -64,6 +79,8 @@ struct s2w_plan {
   std::vector<s2w::TransformSpec> wav_t;   // wavelet scales (active n only, Psi multipliers)
   std::vector<s2w::TransformSpec> raw_t;   // raw Wigner transforms per scale (all n)
 
+  bool tensor = false;                 // reduced-precision modes (S2W_FP32_SPLIT, S2W_BF16)
+  std::vector<s2w::TcTable*> tc_tables;  // owned
   double2* flm_ws = nullptr;           // [batch][L][Mc] harmonic workspace
   double2* g_ws = nullptr;             // largest [batch][nact or 2N-1][L_j][Mc_j] column buffer
   int64_t g_ws_elems = 0;
@@ -119,10 +136,22 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
 
 cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st);
 
+// Tensor-core reduced-precision path (kernels_tc.cu).
+cudaError_t launch_tc_build(const GridTables& g, const TransformSpec& t, const TcTable& tab, int Mc, int mlo,
+                            bool split, cudaStream_t st);
+cudaError_t launch_tc_build_quad(const GridTables& g, bool split, cudaStream_t st);
+cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
+                              ColumnArgs out, cudaStream_t st);
+cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
+                              CoefArgs out, cudaStream_t st);
+size_t tc_inv_smem(bool split, int klmax);
+size_t tc_fwd_smem(bool split, int Lb);
+
 // Compensated-float32 versions of the two DFT launchers (kernels_dft_c32.cu); same contract.
+// plain = ordinary float32 arithmetic (the reduced-precision modes).
 cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, const void* pix, int64_t pix_sb,
-                                bool real, ColumnArgs c, cudaStream_t st);
+                                bool real, ColumnArgs c, cudaStream_t st, bool plain = false);
 cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, ColumnArgs c, void* pix,
-                                int64_t pix_sb, bool real, cudaStream_t st);
+                                int64_t pix_sb, bool real, cudaStream_t st, bool plain = false);
 
 }  // namespace s2w
