@@ -50,6 +50,22 @@ def dist_init():
     return world, rank, local
 
 
+def replica_items(rank: int):
+    """Map indices of one replica's batch: rank r transforms maps r*B .. r*B+B-1 of the seeded
+    workload (replicas only: no rank reads another's data)."""
+    return [b + B * rank for b in range(B)]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (the job's time); identity on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -101,8 +117,8 @@ class ClockSampler:
 def make_inputs(torch, plan, rank):
     import numpy as np
     import synth
-    flm = np.stack([synth.flm_random(L, synth.rng_for(2, b + B * rank), reality=True)[:, L - 1:]
-                    for b in range(B)])
+    flm = np.stack([synth.flm_random(L, synth.rng_for(2, item), reality=True)[:, L - 1:]
+                    for item in replica_items(rank)])
     flm_d = torch.from_numpy(np.ascontiguousarray(flm)).cuda()
     f = plan.empty_map()
     plan.sht_inverse(flm_d, f)
@@ -191,10 +207,7 @@ def run_ours(args, world, rank, local):
     total_ms = sum(step_ms)
     trace = plan.trace_read()
     plan.trace(False)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
 
     # accuracy of the round trip (Sec. 4.4 protocol): f_lm' = Y f' against the seeded f_lm
     flm2 = plan.empty_flm()
@@ -221,10 +234,7 @@ def run_ours(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     e2e_err = float(np.abs(out_host.numpy() - f_host.numpy()).max() / np.abs(f_host.numpy()).max())
 
     # the other precision modes on the same inputs, for comparison (not the headline)
