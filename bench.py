@@ -41,6 +41,10 @@ PEAKS = {
                     "1.196 TFLOP/s FP64 at 1987 MHz)"),
 }
 PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64"]
+# DRAM bytes (read + write) per launch of a kernel, mean over one step's launches, from one ncu
+# capture of the kernel as it is built now (profiles/k_wig_fwd_traffic_L256_N8_B16_fp64.md).
+# An entry is dropped whenever its kernel changes; a missing entry reports null.
+TRAFFIC_BYTES = {("fp64", "wigner_forward"): 368.88e6 / 9 + 0.54e6 / 9}
 
 
 def dist_init():
@@ -266,7 +270,8 @@ def run_ours(args, world, rank, local):
     achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
     peak, peak_src = PEAKS[args.precision]
     roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_BYTES.get((args.precision, name)), "traffic_unit": "bytes/launch",
                 "peak_source": peak_src,
                 "per_kernel": {k: {"launches": v[0], "ms": v[1], "tflops": (v[2] / (v[1] * 1e-3) / 1e12) if v[1] else 0.0}
                                for k, v in trace.items()}}
