@@ -40,7 +40,7 @@ PEAKS = {
     "fp64_native": (FP64_PEAK_TFLOPS, "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (probe measured "
                     "1.196 TFLOP/s FP64 at 1987 MHz)"),
 }
-PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64"]
+PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64"]
 # DRAM bytes (read + write) per launch of a kernel, mean over one step's launches, from one ncu
 # capture of the kernel as it is built now (profiles/k_wig_fwd_traffic_L256_N8_B16_fp64.md).
 # An entry is dropped whenever its kernel changes; a missing entry reports null.
@@ -145,16 +145,75 @@ def cpu_baseline_sample():
     return dt, err
 
 
-PRECISIONS = {"fp64": 0, "fp64_native": 3, "fp32_split": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "fp64_table": 0, "fp64_native": 3, "fp32_split": 1, "bf16": 2}
+PRECOMPUTE = {"fp64_table": 1}
 PRECISION_DOC = {
     "fp64": "float64 accuracy: Wigner-d recursion in float64; l-contractions, DFTs and colatitude "
             "quadrature in compensated float32 pairs",
     "fp64_native": "plain float64: every step in native float64",
+    "fp64_table": "float64 accuracy: precomputed Wigner-d tables (float64 recursion at plan time, "
+                  "colatitude quadrature folded into the forward tables) in float pairs; "
+                  "compensated-float32 table contractions and DFTs",
     "fp32_split": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, fp16 hi/lo operands "
-                  "(3 MMAs), float32 accumulation; compensated-float32 DFTs",
-    "bf16": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, bf16 operands, float32 "
-            "accumulation; compensated-float32 DFTs",
+                  "(3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
+    "bf16": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, bf16 tables and bf16-pair "
+            "data (2 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
 }
+# Differentiation study: gradient of sum_j mean |W^j|^2 w.r.t. the pixels of 8 real maps at
+# L = 512, N = 4, lambda = 2, J0 = 3 (analysis + its hand-written adjoint per step).
+DIFF_L, DIFF_N, DIFF_J0, DIFF_B = 512, 4, 3, 8
+
+
+def run_differentiation(torch, s2w, stream, flush, steps):
+    """Loss-gradient evaluations per second (analysis + adjoint, device time, L2 flushed) and
+    a central finite-difference check of one directional derivative."""
+    import numpy as np
+    import synth
+    plan = s2w.Plan(DIFF_L, DIFF_N, LAM, DIFF_J0, reality=True, batch=DIFF_B, precision=PRECISIONS["fp64"])
+    flm = np.stack([synth.flm_random(DIFF_L, synth.rng_for(4, b), reality=True)[:, DIFF_L - 1:]
+                    for b in range(DIFF_B)])
+    f = plan.empty_map()
+    plan.sht_inverse(torch.from_numpy(flm).cuda(), f)
+    wav, scal, gf = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
+    gscal = torch.zeros_like(scal)
+    norm = torch.empty_like(wav)
+    for s in range(plan.nscales):
+        a, b = plan.wav_offsets[s], plan.wav_offsets[s + 1]
+        norm[:, a:b] = 2.0 / (b - a)
+
+    def step(x):
+        plan.forward(x, wav, scal)
+        torch.mul(wav, norm, out=wav)          # dLoss/dW^j = 2 W^j / n_j
+        plan.forward_adjoint(wav, gscal, gf)
+
+    for _ in range(3):
+        step(f)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        step(f)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    plan.check()
+    # directional derivative against central differences of the library's own loss
+    step(f)
+    v = torch.from_numpy(synth.pixels_random((DIFF_B, DIFF_L, 2 * DIFF_L - 1), synth.rng_for(4, 99))).cuda()
+    an = float((gf * v).sum())
+
+    def loss(x):
+        plan.forward(x, wav, scal)
+        return sum(float((plan.scale_view(wav, s) ** 2).mean(dim=(1, 2, 3)).sum()) for s in range(plan.nscales))
+    h = 1e-6
+    fd = (loss(f + h * v) - loss(f - h * v)) / (2 * h)
+    plan.close()
+    return {"workload": f"L={DIFF_L} N={DIFF_N} lambda=2 J0={DIFF_J0}, {DIFF_B} real maps, "
+                        "loss sum_j mean |W^j|^2, gradient w.r.t. pixels by the adjoint",
+            "value": DIFF_B * len(ms) / (sum(ms) * 1e-3), "unit": "gradients/s (per map)",
+            "ms_per_step": sum(ms) / len(ms),
+            "fd_check_rel": abs(fd - an) / max(abs(an), 1e-300)}
 
 
 def time_steps(torch, plan, f, wav, scal, f2, flush, stream, steps):
@@ -180,7 +239,8 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    plan = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[args.precision])
+    plan = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[args.precision],
+                    precompute=PRECOMPUTE.get(args.precision, 0))
     flm, f = make_inputs(torch, plan, rank)
     wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -244,10 +304,11 @@ def run_ours(args, world, rank, local):
     # the other precision modes on the same inputs, for comparison (not the headline)
     other = {}
     if not args.no_compare:
-        for name in ("fp64_native", "fp32_split", "bf16"):
+        for name in ("fp64", "fp64_table", "fp64_native", "fp32_split", "bf16"):
             if name == args.precision:
                 continue
-            alt = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[name])
+            alt = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[name],
+                           precompute=PRECOMPUTE.get(name, 0))
             for _ in range(2):
                 alt.forward(f, wav, scal)
                 alt.inverse(wav, scal, f2)
@@ -259,6 +320,9 @@ def run_ours(args, world, rank, local):
                            "max_rel_err": float(np.abs(flm3.cpu().numpy() - flm).max() / np.abs(flm).max()),
                            "precision": PRECISION_DOC[name]}
             alt.close()
+    diff = None
+    if not args.no_diff:
+        diff = run_differentiation(torch, s2w, stream, flush, max(3, args.steps // 2))
 
     if rank != 0:
         if dist:
@@ -286,6 +350,7 @@ def run_ours(args, world, rank, local):
         "precision_detail": PRECISION_DOC[args.precision],
         "max_rel_err": err,
         "other_modes": other,
+        "differentiation": diff,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
@@ -343,6 +408,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the plain float64 path")
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-study timing")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":

@@ -59,7 +59,13 @@ typedef enum {
  *                  float64; DFTs in compensated float32 pairs (error-free transformations).
  * S2W_FP64_NATIVE  every step in native float64: the plain float64 path, kept as the
  *                  baseline the other modes are compared with.
- * S2W_FP32_SPLIT, S2W_BF16  reduced-precision modes (not implemented in this build). */
+ * S2W_FP32_SPLIT  wavelet-scale l-contractions on the tensor cores (tcgen05) against
+ *                  precomputed Wigner-d tables stored as fp16 hi + lo pairs, data as fp16
+ *                  pairs, float32 accumulation (1e-5 target); plain float32 DFTs there.
+ * S2W_BF16         the same with single bf16 tables and bf16-pair data (1e-3 target on the
+ *                  round trip; a single wavelet map carries ~2e-3 of table rounding).
+ *                  Both reduced modes keep the spin SHT Y, Y^-1 float64-accurate and
+ *                  support L <= 256 (S2W_EUNSUPPORTED above). */
 typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3 } s2w_precision;
 
 /* Problem statement of the sphere transform (Algorithm 1; Sec. 3.3; App. A).
@@ -69,7 +75,7 @@ typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE =
  *   spin     spin of the signal, |spin| < L
  *   reality  1 for real spin-0 signals (real pixel arrays, m >= 0 stored)
  *   batch    number of maps transformed per call                   (>= 1)
- *   precision  s2w_precision (S2W_FP64 or S2W_FP64_NATIVE in this build)
+ *   precision  s2w_precision
  *   precompute 0 (Wigner-d functions by recursion inside the kernels)
  *   lambda   dilation factor lambda > 1 (Eq. A2); scale j uses band-limit
  *            L_j = min(ceil(lambda^(j+1)), L) and N_j = min(N, L_j), j = J0..J with J
@@ -108,6 +114,30 @@ s2w_status s2w_forward(const s2w_plan* plan, const void* f, void* wav, void* sca
  * band-limited signals (the admissibility condition, Eq. 30). */
 s2w_status s2w_inverse(const s2w_plan* plan, const void* wav, const void* scal, void* f,
                        void* stream);
+
+/* ---- adjoints (Sec. 4.3: the transforms are differentiable; the gradient of a loss
+ * through a linear transform is its adjoint applied to the loss's gradient) -------------
+ * Both are linear maps between the same buffers as the transforms they transpose, with
+ * the roles of input and output exchanged; layouts and element types as above.  The adjoint
+ * is taken for the inner product <x, y> = Re sum conj(x_i) y_i over every stored sample;
+ * for real plans (real maps and real wavelet coefficients) that is the ordinary transpose.
+ * Every step of the transform is transposed in order: the DFTs (forward <-> inverse with
+ * the normalisation moved), the l-contraction (the same recursion, summed over the other
+ * index), the harmonic products (conjugated) and the colatitude quadrature (its transpose,
+ * applied between the inverse contraction and the inverse DFT).  The Wigner-d values are
+ * recomputed by the recursion, never stored.  Accuracy: float64 (<= 1e-11 relative) in
+ * every precision mode; the reduced modes run their adjoints on the float64-accurate
+ * kernels.  Same stream, allocation and error behaviour as s2w_forward. */
+
+/* Adjoint of s2w_forward: (gwav, gscal) -> gf.  gf = A^H (gwav, gscal) where A is the
+ * analysis operator f -> (wav, scal) of Eqs. 40-41.  gf is overwritten. */
+s2w_status s2w_forward_adjoint(const s2w_plan* plan, const void* gwav, const void* gscal, void* gf,
+                               void* stream);
+
+/* Adjoint of s2w_inverse: gf -> (gwav, gscal).  (gwav, gscal) = S^H gf where S is the
+ * synthesis operator (wav, scal) -> f of Eq. 42.  gwav and gscal are overwritten. */
+s2w_status s2w_inverse_adjoint(const s2w_plan* plan, const void* gf, void* gwav, void* gscal,
+                               void* stream);
 
 /* Forward spin SHT (Eq. 2) of the plan's batch of maps at band-limit L and spin: f -> flm. */
 s2w_status s2w_sht_forward(const s2w_plan* plan, const void* f, void* flm, void* stream);
@@ -187,6 +217,7 @@ const char* s2w_version(void);
  *   1 "dft_inverse"   m-columns -> pixels
  *   2 "wigner_inverse" inverse l-contraction with the fused Wigner-d recursion
  *   3 "wigner_forward" colatitude quadrature + forward l-contraction
+ *   4 "quadrature_adjoint" transposed colatitude quadrature (adjoints only)
  * When tracing is on, every kernel launch of the plan is bracketed by two CUDA events
  * recorded on the launching stream (events come from a pool created by
  * s2w_trace_enable; launches beyond its capacity are not recorded).  Besides the device
@@ -195,7 +226,10 @@ const char* s2w_version(void);
  *              8 per gamma-DFT multiply-add;
  *   wigner_*   per contraction term (beta, m, n, l >= max|m|,|n|): 5 for the recursion
  *              step plus 4 per map (complex coefficient times real d^l_mn);
- *              the dense colatitude quadrature of wigner_forward is not counted. */
+ *              the dense colatitude quadrature of wigner_forward is not counted;
+ *   quadrature_adjoint  4 per (map, n, m, t, t') (complex column times real matrix):
+ *              the transposed quadrature has no cheaper form in this design, so its dense
+ *              cost is the count. */
 s2w_status s2w_trace_enable(s2w_plan* plan, int on, int capacity);
 /* Clears the recorded launches (does not synchronise). */
 s2w_status s2w_trace_reset(s2w_plan* plan);

@@ -27,8 +27,8 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_check", "s2w_last_error", "s2w_version", "s2w_trace_enable", "s2w_trace_reset",
            "s2w_trace_read", "s2w_kernel_name", "s2w_sht_inverse_static", "s2w_ball_plan_create",
            "s2w_ball_plan_destroy", "s2w_ball_nodes", "s2w_laguerre_forward", "s2w_laguerre_inverse",
-           "s2w_ball_sl_forward", "s2w_ball_sl_inverse"]
-KERNEL_KINDS = 4
+           "s2w_ball_sl_forward", "s2w_ball_sl_inverse", "s2w_forward_adjoint", "s2w_inverse_adjoint"]
+KERNEL_KINDS = 5
 
 
 class S2WError(RuntimeError):
@@ -62,6 +62,8 @@ def load(path: str = LIB_PATH):
     lib.s2w_query_layout.argtypes = [vp, i64p, i64p, i64p, ip, i64p, ip, ip, ip]
     lib.s2w_forward.argtypes = [vp, vp, vp, vp, vp]
     lib.s2w_inverse.argtypes = [vp, vp, vp, vp, vp]
+    lib.s2w_forward_adjoint.argtypes = [vp, vp, vp, vp, vp]
+    lib.s2w_inverse_adjoint.argtypes = [vp, vp, vp, vp, vp]
     lib.s2w_sht_forward.argtypes = [vp, vp, vp, vp]
     lib.s2w_sht_inverse.argtypes = [vp, vp, vp, vp]
     lib.s2w_sht_inverse_static.argtypes = [vp, vp, vp, vp]
@@ -121,9 +123,10 @@ class Plan:
     """
 
     def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, spin: int = 0,
-                 reality: bool = False, batch: int = 1, precision: int = S2W_FP64, stream=None):
+                 reality: bool = False, batch: int = 1, precision: int = S2W_FP64, stream=None,
+                 precompute: int = 0):
         lib = load()
-        self.params = Params(L, N, J0, spin, int(reality), batch, precision, 0, float(lam))
+        self.params = Params(L, N, J0, spin, int(reality), batch, precision, int(precompute), float(lam))
         h = ctypes.c_void_p()
         _check(lib.s2w_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
         self._h = h
@@ -189,6 +192,16 @@ class Plan:
     def inverse(self, wav, scal, f, stream=None):
         _check(_lib.s2w_inverse(self._h, _ptr(wav, self.real, "wav"), _ptr(scal, self.real, "scal"),
                                 _ptr(f, self.real, "f"), _stream(stream)))
+
+    def forward_adjoint(self, gwav, gscal, gf, stream=None):
+        """gf = A^H (gwav, gscal), A the analysis operator of forward()."""
+        _check(_lib.s2w_forward_adjoint(self._h, _ptr(gwav, self.real, "gwav"), _ptr(gscal, self.real, "gscal"),
+                                        _ptr(gf, self.real, "gf"), _stream(stream)))
+
+    def inverse_adjoint(self, gf, gwav, gscal, stream=None):
+        """(gwav, gscal) = S^H gf, S the synthesis operator of inverse()."""
+        _check(_lib.s2w_inverse_adjoint(self._h, _ptr(gf, self.real, "gf"), _ptr(gwav, self.real, "gwav"),
+                                        _ptr(gscal, self.real, "gscal"), _stream(stream)))
 
     def sht_forward(self, f, flm, stream=None):
         _check(_lib.s2w_sht_forward(self._h, _ptr(f, self.real, "f"), _ptr(flm, False, "flm"),

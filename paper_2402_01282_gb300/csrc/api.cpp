@@ -65,8 +65,9 @@ ColumnArgs cols(const s2w_plan* P, int nact, int L) {
 }
 
 // ---- tracing: events around each launch plus its algorithmic float64 operation count
-enum Kind { K_DFT_FWD = 0, K_DFT_INV = 1, K_WIG_INV = 2, K_WIG_FWD = 3, K_NKINDS = 4 };
-const char* kKindNames[K_NKINDS] = {"dft_forward", "dft_inverse", "wigner_inverse", "wigner_forward"};
+enum Kind { K_DFT_FWD = 0, K_DFT_INV = 1, K_WIG_INV = 2, K_WIG_FWD = 3, K_QUAD_ADJ = 4, K_NKINDS = 5 };
+const char* kKindNames[K_NKINDS] = {"dft_forward", "dft_inverse", "wigner_inverse", "wigner_forward",
+                                    "quadrature_adjoint"};
 
 double contraction_terms(const s2w_plan* P, const TransformSpec& t) {
   const int L = t.L, mlo = mlo_at(P, L), Mc = Mc_at(P, L);
@@ -83,6 +84,12 @@ double dft_flops(const s2w_plan* P, const TransformSpec& t) {
   const double n = 2.0 * t.L - 1.0, B = P->p.batch, Ng = 2.0 * t.N - 1.0;
   const double ring = (P->real ? 2.5 : 5.0) * n * std::log2(n);
   return B * Ng * t.L * ring + 8.0 * B * t.L * Mc_at(P, t.L) * t.nact * Ng;
+}
+
+// algorithmic flops per contraction term: the recursion step (5, unless the d values come
+// from precomputed tables) plus a complex-times-real multiply-add (4) per map
+double term_flops(const s2w_plan* P, const TransformSpec& t) {
+  return (t.tab || t.tc ? 0.0 : 5.0) + 4.0 * P->p.batch;
 }
 
 struct TraceScope {
@@ -115,8 +122,10 @@ s2w_status fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, i
              "azimuthal DFT (forward)");
   }
   {
-    TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
-    S2W_CUDA(t.tc ? launch_tc_forward(P, g, t, c, out, st) : launch_wigner_forward(P, g, t, c, out, st),
+    TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * term_flops(P, t) : 0.0);
+    S2W_CUDA(t.tc    ? launch_tc_forward(P, g, t, c, out, st)
+             : t.tab ? launch_tab_forward(g, t, c, out, st)
+                     : launch_wigner_forward(P, g, t, c, out, st),
              "forward contraction");
   }
   return S2W_OK;
@@ -128,8 +137,10 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
   const GridTables& g = grid_of(P, t);
   ColumnArgs c = cols(P, t.nact, t.L);
   {
-    TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
-    S2W_CUDA(t.tc ? launch_tc_inverse(P, g, t, in, c, st) : launch_wigner_inverse(P, g, t, in, c, st),
+    TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * term_flops(P, t) : 0.0);
+    S2W_CUDA(t.tc    ? launch_tc_inverse(P, g, t, in, c, st)
+             : t.tab ? launch_tab_inverse(g, t, in, c, st)
+                     : launch_wigner_inverse(P, g, t, in, c, st),
              "inverse contraction");
   }
   {
@@ -137,6 +148,61 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
     S2W_CUDA(P->native64 ? launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st)
                          : launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr),
              "azimuthal DFT (inverse)");
+  }
+  return S2W_OK;
+}
+
+// ---- adjoints: each step of fwd_transform / inv_transform transposed, in reverse order.
+// The contractions run on the float64-accurate kernels in every mode (tc = nullptr); the
+// products are conjugated and carry the DFT normalisation moved across (adj_fwd, adj_inv).
+
+// Adjoint of inv_transform: out += adj_fwd * (contraction over beta, no quadrature) of the
+// forward DFT of pix.
+s2w_status adj_inv_transform(s2w_plan* P, const TransformSpec& t, const void* pix, int64_t pix_sb, CoefArgs out,
+                             cudaStream_t st) {
+  const GridTables& g = grid_of(P, t);
+  ColumnArgs c = cols(P, t.nact, t.L);
+  TransformSpec ta = t;
+  ta.mult_fwd = t.adj_fwd;
+  ta.tc = nullptr;
+  ta.tab = nullptr;
+  {
+    TraceScope ts(P, st, K_DFT_FWD, P->trace_on ? dft_flops(P, t) : 0.0);
+    S2W_CUDA(P->native64 ? launch_dft_forward(P, g, ta, pix, pix_sb, P->real, c, st)
+                         : launch_dftc_forward(g, ta, pix, pix_sb, P->real, c, st, false),
+             "azimuthal DFT (adjoint of the inverse DFT)");
+  }
+  {
+    TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
+    S2W_CUDA(launch_wigner_forward(P, g, ta, c, out, st, false), "adjoint of the inverse contraction");
+  }
+  return S2W_OK;
+}
+
+// Adjoint of fwd_transform: pix = inverse DFT of the transposed quadrature of the inverse
+// contraction of (adj_inv * coef).
+s2w_status adj_fwd_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void* pix, int64_t pix_sb,
+                             cudaStream_t st) {
+  const GridTables& g = grid_of(P, t);
+  ColumnArgs c = cols(P, t.nact, t.L);
+  TransformSpec ta = t;
+  ta.mult_inv = t.adj_inv;
+  ta.tc = nullptr;
+  ta.tab = nullptr;
+  {
+    TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
+    S2W_CUDA(launch_wigner_inverse(P, g, ta, in, c, st), "adjoint of the forward contraction");
+  }
+  {
+    TraceScope ts(P, st, K_QUAD_ADJ,
+                  P->trace_on ? 4.0 * P->p.batch * t.nact * (double)Mc_at(P, t.L) * t.L * t.L : 0.0);
+    S2W_CUDA(launch_quad_adjoint(P, g, ta, c, st), "transposed colatitude quadrature");
+  }
+  {
+    TraceScope ts(P, st, K_DFT_INV, P->trace_on ? dft_flops(P, t) : 0.0);
+    S2W_CUDA(P->native64 ? launch_dft_inverse(P, g, ta, c, pix, pix_sb, P->real, st)
+                         : launch_dftc_inverse(g, ta, c, pix, pix_sb, P->real, st, false),
+             "azimuthal DFT (adjoint of the forward DFT)");
   }
   return S2W_OK;
 }
@@ -245,6 +311,51 @@ s2w_status s2w_inverse(const s2w_plan* cP, const void* wav, const void* scal, vo
   }
   // f = Y^-1 f_lm
   return inv_transform(P, P->sht, flm_ws_args(P), f, P->map_elems, st);
+}
+
+s2w_status s2w_forward_adjoint(const s2w_plan* cP, const void* gwav, const void* gscal, void* gf, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  s2w_status s;
+  if ((s = check_ptr(gf, P->real, "gf")) || (s = check_ptr(gwav, P->real, "gwav")) ||
+      (s = check_ptr(gscal, P->real, "gscal")))
+    return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const int64_t B = P->p.batch;
+  S2W_CUDA(launch_zero(P->flm_ws, B * (int64_t)P->p.L * P->Mc * sizeof(double2), st), "zero f_lm");
+  // g_lm = sum over the scaling map and the scales of (Y^-1 Phi)^H gscal, (D^-1 N Psi^j)^H gwav^j
+  if ((s = adj_inv_transform(P, P->scal_t, gscal, P->scal_elems, flm_ws_args(P), st))) return s;
+  const char* wbase = static_cast<const char*>(gwav);
+  for (int sc = 0; sc < P->nscales; ++sc) {
+    const void* pix = wbase + P->wav_off[sc] * pix_bytes(P);
+    if ((s = adj_inv_transform(P, P->wav_t[sc], pix, P->wav_elems, flm_ws_args(P), st))) return s;
+  }
+  // gf = Y^H g_lm
+  return adj_fwd_transform(P, P->sht, flm_ws_args(P), gf, P->map_elems, st);
+}
+
+s2w_status s2w_inverse_adjoint(const s2w_plan* cP, const void* gf, void* gwav, void* gscal, void* stream) {
+  if (cP == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  s2w_status s;
+  if ((s = check_ptr(gf, P->real, "gf")) || (s = check_ptr(gwav, P->real, "gwav")) ||
+      (s = check_ptr(gscal, P->real, "gscal")))
+    return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const int64_t B = P->p.batch;
+  // g_lm = (Y^-1)^H gf
+  S2W_CUDA(launch_zero(P->flm_ws, B * (int64_t)P->p.L * P->Mc * sizeof(double2), st), "zero f_lm");
+  if ((s = adj_inv_transform(P, P->sht, gf, P->map_elems, flm_ws_args(P), st))) return s;
+  // gscal = (Phi Y)^H g_lm, gwav^j = (Psi^j+ D)^H g_lm
+  if ((s = adj_fwd_transform(P, P->scal_t, flm_ws_args(P), gscal, P->scal_elems, st))) return s;
+  char* wbase = static_cast<char*>(gwav);
+  for (int sc = 0; sc < P->nscales; ++sc) {
+    void* pix = wbase + P->wav_off[sc] * pix_bytes(P);
+    if ((s = adj_fwd_transform(P, P->wav_t[sc], flm_ws_args(P), pix, P->wav_elems, st))) return s;
+  }
+  return S2W_OK;
 }
 
 s2w_status s2w_sht_forward(const s2w_plan* cP, const void* f, void* flm, void* stream) {

@@ -285,6 +285,7 @@ struct WigFwdArgs {
   int mlo_out;
   const double* MT;      // [2][L][L]
   const float2* MT2;     // the same as float pairs (compensated quadrature)
+  int quad;              // 0: skip the quadrature (adjoint of the inverse contraction)
   RecTables T;
 };
 
@@ -321,7 +322,9 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
     }
     __syncthreads();
     // colatitude quadrature: Gs <- M^{par} Gs
-    if (C32) {
+    if (!a.quad) {
+      // columns enter the beta sum as they are
+    } else if (C32) {
       const float2* MT2 = a.MT2 + (size_t)par * L * L;
       const float4* G4 = reinterpret_cast<const float4*>(Gs);
       Acc ar[MB], ai[MB];
@@ -421,6 +424,77 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
         }
       }
     }
+  }
+}
+
+// ------------------------------------------------- transposed colatitude quadrature
+// Adjoint of the forward transforms' quadrature step.  In place: a block owns kQaCols
+// columns m of one (map, n) slab, all of one parity of m + n (m = mlo + 2 (kQaCols q + k) +
+// cls), reads them whole into shared memory and thread t writes
+// sum_t' M^{par}[t'][t] G[t'], reading the row-major matrix along t (coalesced).
+constexpr int kQaCols = 8;
+
+struct QuadAdjArgs {
+  double2* G;            // [B][nact][L][Mc]
+  int B, nact, L, Mc, mlo;
+  const int* nvals;
+  const double* MR;      // [2][L][L] row-major M[par][t][t']
+  const float2* MR2;     // the same as float pairs
+};
+
+template <bool C32>
+__global__ void k_quad_adj(QuadAdjArgs a) {
+  extern __shared__ double smd[];
+  double2* Gs = (double2*)smd;                 // [L][kQaCols]
+  const int cls = blockIdx.x & 1, q = blockIdx.x >> 1;
+  const int ni = blockIdx.y, b = blockIdx.z, L = a.L;
+  const int par = (a.mlo + cls + a.nvals[ni]) & 1;
+  const int64_t slab = ((int64_t)b * a.nact + ni) * L * a.Mc;
+  for (int idx = threadIdx.x; idx < L * kQaCols; idx += blockDim.x) {
+    const int tp = idx / kQaCols, k = idx - tp * kQaCols, mi = 2 * (kQaCols * q + k) + cls;
+    const double2 gv = (mi < a.Mc) ? a.G[slab + (int64_t)tp * a.Mc + mi] : make_double2(0.0, 0.0);
+    if (C32) reinterpret_cast<float4*>(Gs)[idx] = split(gv);
+    else Gs[idx] = gv;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t >= L) return;
+  double2 r[kQaCols];
+  if (C32) {
+    const float2* M2 = a.MR2 + (size_t)par * L * L;
+    const float4* G4 = reinterpret_cast<const float4*>(Gs);
+    Acc ar[kQaCols], ai[kQaCols];
+#pragma unroll
+    for (int k = 0; k < kQaCols; ++k) ar[k] = ai[k] = Acc{0.f, 0.f};
+    for (int tp = 0; tp < L; ++tp) {
+      const float2 w = M2[(size_t)tp * L + t];
+#pragma unroll
+      for (int k = 0; k < kQaCols; ++k) {
+        const float4 gv = G4[tp * kQaCols + k];
+        acc_add(ar[k], gv.x, gv.y, w.x, w.y);
+        acc_add(ai[k], gv.z, gv.w, w.x, w.y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kQaCols; ++k) r[k] = make_double2(to_double(ar[k]), to_double(ai[k]));
+  } else {
+    const double* M = a.MR + (size_t)par * L * L;
+#pragma unroll
+    for (int k = 0; k < kQaCols; ++k) r[k] = make_double2(0.0, 0.0);
+    for (int tp = 0; tp < L; ++tp) {
+      const double w = M[(size_t)tp * L + t];
+#pragma unroll
+      for (int k = 0; k < kQaCols; ++k) {
+        const double2 gv = Gs[tp * kQaCols + k];
+        r[k].x = fma(w, gv.x, r[k].x);
+        r[k].y = fma(w, gv.y, r[k].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kQaCols; ++k) {
+    const int mi = 2 * (kQaCols * q + k) + cls;
+    if (mi < a.Mc) a.G[slab + (int64_t)t * a.Mc + mi] = r[k];
   }
 }
 
@@ -562,8 +636,9 @@ cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const 
 }
 
 cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
-                                  CoefArgs out, cudaStream_t st) {
+                                  CoefArgs out, cudaStream_t st, bool quad) {
   WigFwdArgs a;
+  a.quad = quad ? 1 : 0;
   a.G = in.G;
   a.B = in.B;
   a.L = in.L;
@@ -614,6 +689,35 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
       default: return launch_fwd_mb<4, 16>(a, t.nact, c32, st);
     }
   }
+}
+
+cudaError_t launch_quad_adjoint(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                                cudaStream_t st) {
+  QuadAdjArgs a;
+  a.G = c.G;
+  a.B = c.B;
+  a.nact = c.nact;
+  a.L = c.L;
+  a.Mc = c.Mc;
+  a.mlo = c.mlo;
+  a.nvals = t.nvals;
+  a.MR = g.MR;
+  a.MR2 = g.MR2;
+  const int nq = ((c.Mc + 1) / 2 + kQaCols - 1) / kQaCols;   // column tiles per parity class
+  const int threads = ((c.L + 31) / 32) * 32;
+  const size_t smem = (size_t)c.L * kQaCols * sizeof(double2);
+  dim3 grid(2 * nq, c.nact, c.B);
+  cudaError_t e;
+  if (P->native64) {
+    e = cudaFuncSetAttribute(k_quad_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_quad_adj<false><<<grid, threads, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_quad_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_quad_adj<true><<<grid, threads, smem, st>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace s2w

@@ -278,13 +278,21 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
     std::frexp(mx, &e);
     g.qscale = std::ldexp(1.0, 14 - e);   // packed quadrature entries below 2^14
   }
-  std::vector<float2> MT2(MT.size());
+  std::vector<float2> MT2(MT.size()), MR2(MT.size());
+  std::vector<double> MR(MT.size());
+  for (int par = 0; par < 2; ++par)
+    for (int t = 0; t < L; ++t)
+      for (int tp = 0; tp < L; ++tp) MR[(size_t)par * L * L + (size_t)t * L + tp] = MT[(size_t)par * L * L + (size_t)tp * L + t];
   for (size_t i = 0; i < MT.size(); ++i) {
     float h = (float)MT[i];
     MT2[i] = make_float2(h, (float)(MT[i] - (double)h));
+    h = (float)MR[i];
+    MR2[i] = make_float2(h, (float)(MR[i] - (double)h));
   }
   S2W_TRY(upload(P, MT, &g.MT, st, err));
   S2W_TRY(upload(P, MT2, &g.MT2, st, err));
+  S2W_TRY(upload(P, MR, &g.MR, st, err));
+  S2W_TRY(upload(P, MR2, &g.MR2, st, err));
   S2W_TRY(upload(P, tw, &g.tw, st, err));
   S2W_TRY(upload(P, tw4, &g.tw4, st, err));
   return S2W_OK;
@@ -292,7 +300,7 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
 
 s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int N, int grid,
                       const std::vector<int>& nvals, const std::vector<cplx>& minv,
-                      const std::vector<cplx>& mfwd, std::string& err) {
+                      const std::vector<cplx>& mfwd, double gscale, std::string& err) {
   t.L = L;
   t.N = N;
   t.grid = grid;
@@ -310,7 +318,17 @@ s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int
       ph[(size_t)i * ng + gi] = make_double2(std::cos(ang), std::sin(ang));
       ph4[(size_t)i * ng + gi] = split4(ph[(size_t)i * ng + gi]);
     }
-  t.gscale = 1.0;
+  t.gscale = gscale;
+  // adjoint multipliers: the forward DFT kernel carries (2 pi/(2L-1)) gscale, the inverse
+  // none, so transposing a DFT moves that factor into the contraction beside it.
+  const double dft_scale = (2.0 * kPi / (2.0 * L - 1.0)) * gscale;
+  std::vector<double2> af(minv.size()), ai(mfwd.size());
+  for (size_t i = 0; i < minv.size(); ++i)
+    af[i] = make_double2(minv[i].real() / dft_scale, -minv[i].imag() / dft_scale);
+  for (size_t i = 0; i < mfwd.size(); ++i)
+    ai[i] = make_double2(mfwd[i].real() * dft_scale, -mfwd[i].imag() * dft_scale);
+  S2W_TRY(upload(P, af, &t.adj_fwd, st, err));
+  S2W_TRY(upload(P, ai, &t.adj_inv, st, err));
   S2W_TRY(upload(P, nvals, &t.nvals, st, err));
   S2W_TRY(upload(P, a, &t.mult_inv, st, err));
   S2W_TRY(upload(P, b, &t.mult_fwd, st, err));
@@ -395,6 +413,57 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
   return S2W_OK;
 }
 
+// Float64-accurate precomputed tables (precompute = 1) for the SHT, the scaling function and
+// every wavelet scale; specs with the same (L, n values) share one table.
+s2w_status build_tab_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+  std::map<std::pair<int, std::vector<int>>, TabTable*> cache;
+  std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
+  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+  for (TransformSpec* t : specs) {
+    auto key = std::make_pair(t->L, t->nvals_h);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      t->tab = it->second;
+      continue;
+    }
+    const GridTables& g = P->grids[t->grid];
+    const int L = t->L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
+    TabTable* tab = new TabTable();
+    P->tab_tables.push_back(tab);
+    tab->Lp = ((L + 63) / 64) * 64;
+    tab->Lk = ((L + 31) / 32) * 32;
+    std::vector<int64_t> oi((size_t)Mc * t->nact, 0), of((size_t)Mc * t->nact, 0);
+    std::vector<int> kp((size_t)Mc * t->nact, 0);
+    int64_t ri = 0, rf = 0;
+    for (int mi = 0; mi < Mc; ++mi)
+      for (int ni = 0; ni < t->nact; ++ni) {
+        const size_t idx = (size_t)mi * t->nact + ni;
+        const int l0 = std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni]));
+        oi[idx] = ri;
+        of[idx] = rf;
+        if (l0 >= L) continue;
+        const int l0a = l0 & ~31, k = ((L - l0a + 63) / 64) * 64;
+        kp[idx] = k;
+        ri += (int64_t)k * tab->Lp;
+        rf += (int64_t)tab->Lk * k;
+        tab->kpmax = std::max(tab->kpmax, k);
+      }
+    tab->elems = std::max(ri, rf);
+    S2W_TRY(upload(P, oi, &tab->off_inv, st, err));
+    S2W_TRY(upload(P, of, &tab->off_fwd, st, err));
+    S2W_TRY(upload(P, kp, &tab->kp, st, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ri, 1), &tab->inv, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(rf, 1), &tab->fwd, err));
+    if (tab->kpmax > 0 && launch_tab_build(g, *t, *tab, Mc, mlo, st) != cudaSuccess) {
+      err = "Wigner-d table kernels failed to launch";
+      return S2W_ECUDA;
+    }
+    cache[key] = tab;
+    t->tab = tab;
+  }
+  return S2W_OK;
+}
+
 }  // namespace
 
 s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::string& err) {
@@ -413,7 +482,11 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     err = "the reduced-precision tensor-core modes support L <= 256 in this build";
     return S2W_EUNSUPPORTED;
   }
-  if (p.precompute != 0) { err = "precompute mode is not implemented"; return S2W_EUNSUPPORTED; }
+  if (p.precompute != 0 && p.precompute != 1) { err = "precompute must be 0 or 1"; return S2W_EINVAL; }
+  if (p.precompute == 1 && p.precision == S2W_FP64_NATIVE) {
+    err = "the plain float64 path computes the Wigner-d functions on the fly (precompute = 0)";
+    return S2W_EUNSUPPORTED;
+  }
   int J = 0;
   while (ceil_pow(p.lambda, J) < p.L) ++J;
   if (p.J0 < 0 || p.J0 > J) { err = "J0 must satisfy 0 <= J0 <= J"; return S2W_EINVAL; }
@@ -421,6 +494,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   P->p = p;
   P->native64 = p.precision == S2W_FP64_NATIVE;
   P->tensor = p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16;
+  P->precompute = p.precompute == 1 && p.precision == S2W_FP64;
   P->real = p.reality != 0;
   P->Mc = P->real ? p.L : 2 * p.L - 1;
   P->mlo = P->real ? 0 : -(p.L - 1);
@@ -464,7 +538,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
       double v = (l >= std::abs(s)) ? ((s % 2 == 0) ? 1.0 : -1.0) * std::sqrt((2.0 * l + 1.0) / (4.0 * kPi)) : 0.0;
       mi[l] = mf[l] = v;
     }
-    S2W_TRY(build_spec(P, st, P->sht, L, 1, gidx[L], {-s}, mi, mf, err));
+    S2W_TRY(build_spec(P, st, P->sht, L, 1, gidx[L], {-s}, mi, mf, 1.0, err));
   }
   // scaling function at L_phi: Phi_l0 = sqrt((2l+1)/(4 pi)) sqrt(k(l / lambda^J0)); the
   // scaling map is a spin-0 function, so its harmonic multiplier is Phi_l0 (Eq. 29, Eq. 41).
@@ -474,7 +548,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     double scale = std::pow(p.lambda, p.J0);
     for (int l = 0; l < LP; ++l)
       m[l] = (l >= std::abs(s)) ? std::sqrt((2.0 * l + 1.0) / (4.0 * kPi)) * std::sqrt(tile.k(l / scale)) : 0.0;
-    S2W_TRY(build_spec(P, st, P->scal_t, LP, 1, gidx[LP], {0}, m, m, err));
+    S2W_TRY(build_spec(P, st, P->scal_t, LP, 1, gidx[LP], {0}, m, m, 1.0, err));
   }
   P->wav_t.resize(P->nscales);
   P->raw_t.resize(P->nscales);
@@ -496,16 +570,15 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
         mf[(size_t)l * act.size() + i] = psi;
       }
     }
-    S2W_TRY(build_spec(P, st, P->wav_t[sc], Lj, Nj, gidx[Lj], act, mi, mf, err));
-    P->wav_t[sc].gscale = 2.0 * kPi / (2.0 * Nj - 1.0);
+    S2W_TRY(build_spec(P, st, P->wav_t[sc], Lj, Nj, gidx[Lj], act, mi, mf, 2.0 * kPi / (2.0 * Nj - 1.0), err));
     std::vector<cplx> ri((size_t)Lj * all.size()), rf((size_t)Lj * all.size(), 1.0);
     for (int l = 0; l < Lj; ++l)
       for (size_t i = 0; i < all.size(); ++i) ri[(size_t)l * all.size() + i] = (2.0 * l + 1.0) / (8.0 * kPi * kPi);
-    S2W_TRY(build_spec(P, st, P->raw_t[sc], Lj, Nj, gidx[Lj], all, ri, rf, err));
-    P->raw_t[sc].gscale = 2.0 * kPi / (2.0 * Nj - 1.0);
+    S2W_TRY(build_spec(P, st, P->raw_t[sc], Lj, Nj, gidx[Lj], all, ri, rf, 2.0 * kPi / (2.0 * Nj - 1.0), err));
   }
 
   if (P->tensor) S2W_TRY(build_tc_tables(P, st, err));
+  if (P->precompute) S2W_TRY(build_tab_tables(P, st, err));
 
   // workspaces
   const int64_t B = p.batch;
@@ -535,6 +608,8 @@ void free_plan(s2w_plan* P) {
   P->owned.clear();
   for (TcTable* t : P->tc_tables) delete t;
   P->tc_tables.clear();
+  for (TabTable* t : P->tab_tables) delete t;
+  P->tab_tables.clear();
 }
 
 }  // namespace s2w

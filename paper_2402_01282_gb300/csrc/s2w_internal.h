@@ -25,6 +25,8 @@ struct GridTables {
   double* sqrtC = nullptr;     // [L][n] sqrt(binom(2l, k)), k = 0..2l
   double* MT = nullptr;        // [2][L][L] quadrature matrices, transposed: MT[par][t'][t]
   float2* MT2 = nullptr;       // the same as float pairs (hi, lo)
+  double* MR = nullptr;        // [2][L][L] the same matrices row-major, MR[par][t][t'] (adjoints)
+  float2* MR2 = nullptr;       // the same as float pairs
   double2* tw = nullptr;       // [n] exp(+2 pi i e / n)
   float4* tw4 = nullptr;       // [n] the same as float pairs (re_hi, re_lo, im_hi, im_lo)
   // reduced-precision modes: quadrature matrices packed for the tensor cores
@@ -43,6 +45,21 @@ struct TcTable {
   int64_t elems = 0;
 };
 
+// Precomputed Wigner-d tables of one transform for the float64-accurate table contractions
+// (kernels_tab.cu), float pairs.  Tile (m, n) covers l = l0a .. l0a + kp - 1 with
+// l0a = max(|m|,|n|) rounded down to a multiple of 32 and kp a multiple of 64.
+struct TabTable {
+  int Lp = 0;                  // beta rows of the inverse tiles (L rounded up to 64)
+  int Lk = 0;                  // beta' rows of the forward tiles (L rounded up to 32)
+  int kpmax = 0;               // largest kp
+  int64_t* off_inv = nullptr;  // device [Mc * nact] float2 offset of inverse tile (m, n): [kp][Lp]
+  int64_t* off_fwd = nullptr;  // device [Mc * nact] offset of forward tile (m, n): [Lk][kp]
+  int* kp = nullptr;           // device [Mc * nact] padded l extent (0 if l0 >= L)
+  float2* inv = nullptr;       // d^l_mn(beta)
+  float2* fwd = nullptr;       // (M^{par(m+n)})^T d^l_mn, the quadrature folded in
+  int64_t elems = 0;           // float2 elements of each of inv and fwd
+};
+
 // One Wigner / SHT transform instance: band-limit, the n values it carries and the
 // per-(l, n) multipliers that fuse the harmonic products into the contraction.
 struct TransformSpec {
@@ -56,7 +73,11 @@ struct TransformSpec {
   double2* gphase = nullptr;    // [nact][2N-1] exp(+i n gamma_g)
   float4* gphase4 = nullptr;    // the same as float pairs
   double gscale = 1.0;          // gamma quadrature factor 2 pi/(2N-1) (1 for the SHT)
+  // adjoint multipliers: the transposed products with the DFT normalisation moved across
+  double2* adj_fwd = nullptr;   // [L][nact] conj(mult_inv) / ((2 pi/(2L-1)) gscale)
+  double2* adj_inv = nullptr;   // [L][nact] conj(mult_fwd) * (2 pi/(2L-1)) gscale
   const TcTable* tc = nullptr;  // reduced-precision modes: packed tiles (shared between specs)
+  const TabTable* tab = nullptr;  // precompute = 1: float64-accurate tables (shared between specs)
 };
 
 struct s2w_plan_impl;
@@ -81,6 +102,8 @@ struct s2w_plan {
 
   bool tensor = false;                 // reduced-precision modes (S2W_FP32_SPLIT, S2W_BF16)
   std::vector<s2w::TcTable*> tc_tables;  // owned
+  bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
+  std::vector<s2w::TabTable*> tab_tables;  // owned
   double2* flm_ws = nullptr;           // [batch][L][Mc] harmonic workspace
   double2* g_ws = nullptr;             // largest [batch][nact or 2N-1][L_j][Mc_j] column buffer
   int64_t g_ws_elems = 0;
@@ -131,8 +154,13 @@ struct CoefArgs {
 cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
                                   CoefArgs in, ColumnArgs out, cudaStream_t st);
 // out(b,n,l,m) += mult_fwd[l][n] * sum_beta (M^{par(m+n)} G)[beta] d^l_{m n}(beta)
+// (quad = false: the colatitude quadrature is skipped, G enters the sum as it is).
 cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
-                                  ColumnArgs in, CoefArgs out, cudaStream_t st);
+                                  ColumnArgs in, CoefArgs out, cudaStream_t st, bool quad = true);
+// In place on every column of c: G[b][n][.][m] <- (M^{par(m+n)})^T G[b][n][.][m], the transposed
+// colatitude quadrature (adjoint of the forward transforms).
+cudaError_t launch_quad_adjoint(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                                cudaStream_t st);
 
 cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st);
 
@@ -146,6 +174,15 @@ cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const Tran
                               CoefArgs out, cudaStream_t st);
 size_t tc_inv_smem(bool split, int klmax);
 size_t tc_fwd_smem(bool split, int Lb);
+
+// Float64-accurate table contractions (kernels_tab.cu): build (recursion + folded quadrature)
+// and the two contractions; same contracts as launch_wigner_inverse / launch_wigner_forward.
+cudaError_t launch_tab_build(const GridTables& g, const TransformSpec& t, const TabTable& tab, int Mc, int mlo,
+                             cudaStream_t st);
+cudaError_t launch_tab_inverse(const GridTables& g, const TransformSpec& t, CoefArgs in, ColumnArgs out,
+                               cudaStream_t st);
+cudaError_t launch_tab_forward(const GridTables& g, const TransformSpec& t, ColumnArgs in, CoefArgs out,
+                               cudaStream_t st);
 
 // Compensated-float32 versions of the two DFT launchers (kernels_dft_c32.cu); same contract.
 // plain = ordinary float32 arithmetic (the reduced-precision modes).

@@ -12,7 +12,8 @@ from oracle import filters, harmonic, wavelet
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
-MODES = [0, 3]          # S2W_FP64 (compensated-float32 DFT and quadrature), S2W_FP64_NATIVE
+MODES = [(0, 0), (3, 0), (0, 1)]   # (precision, precompute): S2W_FP64 on the fly, S2W_FP64_NATIVE,
+                                   # S2W_FP64 with precomputed quadrature-folded Wigner-d tables
 
 
 def rel(a, b):
@@ -35,7 +36,7 @@ def internal_flm(flm_full, L, real):
 @pytest.mark.parametrize("L,spin,real,B", [(2, 0, True, 1), (8, 0, True, 3), (17, 0, False, 2), (33, 0, True, 2),
                                            (16, 1, False, 1), (11, 2, False, 3), (64, 0, True, 1)])
 def test_sht_parity(lib, L, spin, real, B, mode):
-    plan = lib.Plan(L, min(2, L), 2.0, 0, spin=spin, reality=real, batch=B, precision=mode)
+    plan = lib.Plan(L, min(2, L), 2.0, 0, spin=spin, reality=real, batch=B, precision=mode[0], precompute=mode[1])
     rng = synth.rng_for(500, L)
     # arbitrary samples: pins the exact MW forward operator, not only its band-limited action
     f = synth.pixels_random((B, L, 2 * L - 1), rng, complex_=not real)
@@ -59,7 +60,7 @@ def test_sht_parity(lib, L, spin, real, B, mode):
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("L,N,real,B", [(33, 4, True, 2), (20, 3, False, 1), (9, 9, False, 2)])
 def test_wigner_parity(lib, L, N, real, B, mode):
-    plan = lib.Plan(L, N, 2.0, 0, reality=real, batch=B, precision=mode)
+    plan = lib.Plan(L, N, 2.0, 0, reality=real, batch=B, precision=mode[0], precompute=mode[1])
     rng = synth.rng_for(501, L)
     for s in range(plan.nscales):
         Lj, Nj = plan.Lj[s], plan.Nj[s]
@@ -93,8 +94,8 @@ def lib_empty(plan, s):
     return torch.empty((plan.batch, *plan.scale_shape(s)), dtype=plan.dtype, device="cuda")
 
 
-def _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg, mode=0):
-    plan = lib.Plan(L, N, lam, J0, spin=spin, reality=real, batch=B, precision=mode)
+def _wavelet_case(lib, L, N, lam, J0, spin, real, B, cfg, mode=(0, 0)):
+    plan = lib.Plan(L, N, lam, J0, spin=spin, reality=real, batch=B, precision=mode[0], precompute=mode[1])
     flms = [synth.flm_random(L, synth.rng_for(cfg, b), spin=spin, reality=real) for b in range(B)]
     fs = [harmonic.sht_inverse(x, L, spin) for x in flms]
     if real:
@@ -155,7 +156,7 @@ def test_full_size_256(lib, oracle_256):
     L, N, lam, J0, B = 256, 8, 2.0, 2, 16
     f, W_ref, Wp_ref = oracle_256
     for mode in MODES:
-        plan = lib.Plan(L, N, lam, J0, reality=True, batch=B, precision=mode)
+        plan = lib.Plan(L, N, lam, J0, reality=True, batch=B, precision=mode[0], precompute=mode[1])
         wav, scal = plan.empty_wav(), plan.empty_scal()
         plan.forward(to_dev(f), wav, scal)
         f2 = plan.empty_map()
