@@ -9,6 +9,8 @@
 // outputs are float64; twiddles are float64 values split into pairs on the host.
 #include <math.h>
 
+#include <algorithm>
+
 #include "comp32.cuh"
 #include "s2w_internal.h"
 
@@ -94,6 +96,7 @@ struct DftcArgs {
   int B, nact, Ng, L, Mc, mlo, n, n1, n2;
   const float4* tw;     // [n] exp(+2 pi i e/n) as pairs
   const float4* gph;    // [nact][Ng] exp(+i n gamma_g) as pairs
+  const int* nvals;     // [nact] the n values carried
   double scale;
 };
 
@@ -180,6 +183,180 @@ __global__ void k_dftc_inv(DftcArgs a) {
   }
 }
 
+// ----------------------------------------------------------- gamma on the map side
+// SO(3) transforms with several gamma samples: the gamma DFT is taken on the map side of
+// the alpha DFT (forward: gamma first, inverse: gamma last), so one complex alpha DFT of
+// length n serves each carried n instead of one per gamma sample.  For real signals
+// G_{-m,-n} = conj G_{m,n}: a single complex transform over all n outputs gives both n and
+// -n (m >= 0 of each), so only the n >= 0 values are transformed ("jobs").  The wavelet
+// transforms carry N of the 2N-1 values of n, so this halves the alpha-DFT work.
+constexpr int kMaxJobs = 64;
+constexpr int kJobChunk = 4;   // jobs whose gamma sums share one pass over the samples
+
+__device__ __forceinline__ void make_jobs(const int* nvals, int nact, bool real, int* jn, int* jp, int& nj) {
+  nj = 0;
+  for (int ni = 0; ni < nact && nj < kMaxJobs; ++ni) {
+    const int v = nvals[ni];
+    if (real && v < 0) continue;
+    int partner = -1;
+    if (real && v > 0)
+      for (int q = 0; q < nact; ++q)
+        if (nvals[q] == -v) partner = q;
+    jn[nj] = ni;
+    jp[nj] = partner;
+    ++nj;
+  }
+}
+
+template <bool REAL, bool PLAIN>
+__global__ void k_dftg_fwd(DftcArgs a) {
+  extern __shared__ float4 s4[];
+  __shared__ int jn[kMaxJobs], jp[kMaxJobs], njs;
+  const int n = a.n, L = a.L, t = blockIdx.x, b = blockIdx.y;
+  if (threadIdx.x == 0) {
+    int nj;
+    make_jobs(a.nvals, a.nact, REAL, jn, jp, nj);
+    njs = nj;
+  }
+  float4* tw = s4;
+  float4* tmp = tw + n;
+  float4* HZ = tmp + n;   // [jobs][n]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
+  __syncthreads();
+  const int nj = njs;
+  const int64_t ring = (int64_t)L * n;
+  const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
+  // H_j(alpha) = sum_g W(alpha, gamma_g) exp(-i n_j gamma_g)
+  for (int j0 = 0; j0 < nj; j0 += kJobChunk) {
+    const int jc = min(kJobChunk, nj - j0);
+    for (int al = threadIdx.x; al < n; al += blockDim.x) {
+      Acc hr[kJobChunk], hi[kJobChunk];
+#pragma unroll
+      for (int q = 0; q < kJobChunk; ++q) hr[q] = hi[q] = Acc{0.f, 0.f};
+      for (int g = 0; g < a.Ng; ++g) {
+        float4 x;
+        if (REAL) x = split(make_double2(((const double*)a.pix_in)[base + g * ring + al], 0.0));
+        else x = split(((const double2*)a.pix_in)[base + g * ring + al]);
+#pragma unroll
+        for (int q = 0; q < kJobChunk; ++q) {
+          if (q < jc) {
+            const float4 ph = a.gph[jn[j0 + q] * a.Ng + g];
+            if (REAL && !PLAIN) {
+              acc_add(hr[q], x.x, x.y, ph.x, ph.y);
+              acc_add(hi[q], x.x, x.y, -ph.z, -ph.w);
+            } else {
+              cmac<-1, PLAIN>(hr[q], hi[q], x, ph);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kJobChunk; ++q)
+        if (q < jc) HZ[(j0 + q) * n + al] = pack<PLAIN>(hr[q], hi[q]);
+    }
+  }
+  // one complex alpha DFT per job
+  for (int j = 0; j < nj; ++j) {
+    __syncthreads();
+    stage1<-1, PLAIN>(HZ + j * n, tmp, tw, n, a.n1, a.n2);
+    __syncthreads();
+    const int ni = jn[j], pi = jp[j];
+    const int kcount = (REAL && pi < 0) ? L : n;   // n = 0 of a real signal: m >= 0 only
+    double2* Gn = a.G + (((int64_t)b * a.nact + ni) * L + t) * a.Mc;
+    double2* Gp = (pi >= 0) ? a.G + (((int64_t)b * a.nact + pi) * L + t) * a.Mc : nullptr;
+    for (int k = threadIdx.x; k < kcount; k += blockDim.x) {
+      Acc re, im;
+      stage2_one<-1, false, PLAIN>(tmp, tw, n, a.n1, a.n2, k, re, im);
+      const double zr = to_double(re) * a.scale, zi = to_double(im) * a.scale;
+      if (REAL) {
+        if (k < L) Gn[k] = make_double2(zr, zi);                 // G_{m=k, n}
+        if (Gp != nullptr) {
+          const int mp = (k == 0) ? 0 : n - k;                      // G_{m', -n} = conj Z(-m')
+          if (mp < L) Gp[mp] = make_double2(zr, -zi);
+        }
+      } else {
+        const int m = (k < L) ? k : k - n;
+        Gn[m - a.mlo] = make_double2(zr, zi);
+      }
+    }
+  }
+}
+
+template <bool REAL, bool PLAIN>
+__global__ void k_dftg_inv(DftcArgs a) {
+  extern __shared__ float4 s4[];
+  __shared__ int jn[kMaxJobs], jp[kMaxJobs], njs;
+  const int n = a.n, L = a.L, t = blockIdx.x, b = blockIdx.y;
+  if (threadIdx.x == 0) {
+    int nj;
+    make_jobs(a.nvals, a.nact, REAL, jn, jp, nj);
+    njs = nj;
+  }
+  float4* tw = s4;
+  float4* x = tw + n;
+  float4* tmp = x + n;
+  float4* HZ = tmp + n;   // [jobs][n]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
+  __syncthreads();
+  const int nj = njs;
+  for (int j = 0; j < nj; ++j) {
+    const int ni = jn[j], pi = jp[j];
+    const double2* Gn = a.G + (((int64_t)b * a.nact + ni) * L + t) * a.Mc;
+    const double2* Gp = a.G + (((int64_t)b * a.nact + (pi >= 0 ? pi : ni)) * L + t) * a.Mc;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      double2 v;
+      if (REAL) {
+        if (k < L) {
+          v = Gn[k];
+        } else {                      // m = k - n < 0: G_{m,n} = conj G_{-m,-n}
+          const double2 w = Gp[n - k];
+          v = make_double2(w.x, -w.y);
+        }
+      } else {
+        const int m = (k < L) ? k : k - n;
+        v = Gn[m - a.mlo];
+      }
+      x[k] = split(v);
+    }
+    __syncthreads();
+    stage1<1, PLAIN>(x, tmp, tw, n, a.n1, a.n2);
+    __syncthreads();
+    for (int al = threadIdx.x; al < n; al += blockDim.x) {
+      Acc re, im;
+      stage2_one<1, false, PLAIN>(tmp, tw, n, a.n1, a.n2, al, re, im);
+      HZ[j * n + al] = pack<PLAIN>(re, im);
+    }
+  }
+  __syncthreads();
+  // W(alpha, gamma_g) = sum_j Z_j(alpha) exp(+i n_j gamma_g)  (real signals: the n, -n pair
+  // contributes 2 Re, the n = 0 job Re)
+  const int64_t ring = (int64_t)L * n;
+  const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
+  for (int g = 0; g < a.Ng; ++g) {
+    for (int al = threadIdx.x; al < n; al += blockDim.x) {
+      Acc re{0.f, 0.f}, im{0.f, 0.f};
+      for (int j = 0; j < nj; ++j) {
+        const float4 z = HZ[j * n + al];
+        const float4 ph = a.gph[jn[j] * a.Ng + g];
+        if (REAL) {
+          const float f = (jp[j] >= 0) ? 2.f : 1.f;
+          if (PLAIN) {
+            re.s = fmaf(f * z.x, ph.x, fmaf(-f * z.z, ph.z, re.s));
+          } else {
+            acc_add(re, f * z.x, f * z.y, ph.x, ph.y);
+            acc_add(re, -f * z.z, -f * z.w, ph.z, ph.w);
+          }
+        } else {
+          cmac<1, PLAIN>(re, im, z, ph);
+        }
+      }
+      if (REAL) ((double*)a.pix_out)[base + g * ring + al] = to_double(re);
+      else ((double2*)a.pix_out)[base + g * ring + al] = make_double2(to_double(re), to_double(im));
+    }
+  }
+}
+
 DftcArgs make_args(const GridTables& g, const TransformSpec& t, ColumnArgs c) {
   DftcArgs a;
   a.G = c.G;
@@ -194,8 +371,27 @@ DftcArgs make_args(const GridTables& g, const TransformSpec& t, ColumnArgs c) {
   a.n2 = g.n2;
   a.tw = g.tw4;
   a.gph = t.gphase4;
+  a.nvals = t.nvals;
   a.scale = 0.0;
   return a;
+}
+
+// the gamma-side kernels apply when there are several gamma samples, the job list fits and
+// the shared memory of one block stays within the opt-in limit
+int dftg_jobs(const TransformSpec& t, bool real) {
+  int nj = 0;
+  for (int v : t.nvals_h)
+    if (!real || v >= 0) ++nj;
+  return nj;
+}
+size_t dftg_smem(const GridTables& g, const TransformSpec& t, bool real, bool fwd) {
+  return (size_t)((fwd ? 2 : 3) * g.n + dftg_jobs(t, real) * g.n) * sizeof(float4);
+}
+bool use_dftg(const GridTables& g, const TransformSpec& t, bool real, bool fwd) {
+  if (real)   // every negative n needs its partner -n among the carried values
+    for (int v : t.nvals_h)
+      if (v < 0 && std::find(t.nvals_h.begin(), t.nvals_h.end(), -v) == t.nvals_h.end()) return false;
+  return t.N > 1 && dftg_jobs(t, real) <= kMaxJobs && dftg_smem(g, t, real, fwd) <= 200 * 1024;
 }
 
 template <class K>
@@ -215,8 +411,13 @@ cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, con
   a.pix_out = nullptr;
   a.pix_sb = pix_sb;
   a.scale = (2.0 * 3.14159265358979323846 / g.n) * t.gscale;
-  const size_t smem = (size_t)(3 * g.n + a.Ng * c.Mc) * sizeof(float4);
   dim3 grid(c.L, c.B);
+  if (use_dftg(g, t, real, true)) {
+    const size_t sm = dftg_smem(g, t, real, true);
+    if (plain) return real ? launch(k_dftg_fwd<true, true>, grid, sm, st, a) : launch(k_dftg_fwd<false, true>, grid, sm, st, a);
+    return real ? launch(k_dftg_fwd<true, false>, grid, sm, st, a) : launch(k_dftg_fwd<false, false>, grid, sm, st, a);
+  }
+  const size_t smem = (size_t)(3 * g.n + a.Ng * c.Mc) * sizeof(float4);
   if (plain) return real ? launch(k_dftc_fwd<true, true>, grid, smem, st, a) : launch(k_dftc_fwd<false, true>, grid, smem, st, a);
   return real ? launch(k_dftc_fwd<true, false>, grid, smem, st, a) : launch(k_dftc_fwd<false, false>, grid, smem, st, a);
 }
@@ -227,8 +428,13 @@ cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, Col
   a.pix_in = nullptr;
   a.pix_out = pix;
   a.pix_sb = pix_sb;
-  const size_t smem = (size_t)(3 * g.n + c.nact * c.Mc) * sizeof(float4);
   dim3 grid(c.L, c.B);
+  if (use_dftg(g, t, real, false)) {
+    const size_t sm = dftg_smem(g, t, real, false);
+    if (plain) return real ? launch(k_dftg_inv<true, true>, grid, sm, st, a) : launch(k_dftg_inv<false, true>, grid, sm, st, a);
+    return real ? launch(k_dftg_inv<true, false>, grid, sm, st, a) : launch(k_dftg_inv<false, false>, grid, sm, st, a);
+  }
+  const size_t smem = (size_t)(3 * g.n + c.nact * c.Mc) * sizeof(float4);
   if (plain) return real ? launch(k_dftc_inv<true, true>, grid, smem, st, a) : launch(k_dftc_inv<false, true>, grid, smem, st, a);
   return real ? launch(k_dftc_inv<true, false>, grid, smem, st, a) : launch(k_dftc_inv<false, false>, grid, smem, st, a);
 }
