@@ -139,7 +139,7 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
   {
     TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * term_flops(P, t) : 0.0);
     S2W_CUDA(t.tc    ? launch_tc_inverse(P, g, t, in, c, st)
-             : t.tab ? launch_tab_inverse(g, t, in, c, st)
+             : (t.tab && t.minv_factored) ? launch_tab_inverse(g, t, in, c, st)
                      : launch_wigner_inverse(P, g, t, in, c, st),
              "inverse contraction");
   }

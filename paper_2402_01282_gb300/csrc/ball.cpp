@@ -8,6 +8,7 @@
 // omega_i = tau^3 w_i e^{x_i} = tau^3 (P+2)/(P+1) x_i (e^{x_i/2} / L^(2)_{P+1}(x_i))^2 and
 // K_p(r_i) = tau^(-3/2) e^{-x_i/2} L^(2)_p(x_i) / sqrt((p+1)(p+2)): every factor stays inside
 // the float64 range for P <= 256, so no logarithms are needed.
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
@@ -154,6 +155,31 @@ int64_t ncol(const s2w_ball_plan* B) { return (int64_t)B->p.L * B->Mc; }
 
 }  // namespace
 
+namespace s2w {
+
+void laguerre_rule(int P, double tau, int kmax, std::vector<double>& r, std::vector<double>& omega,
+                   std::vector<double>& K) {
+  const std::vector<dd> x = laguerre_nodes(P);
+  std::vector<dd> Lv;
+  r.assign(P, 0.0);
+  omega.assign(P, 0.0);
+  K.assign((size_t)P * kmax, 0.0);
+  for (int i = 0; i < P; ++i) {
+    laguerre2(std::max(P + 1, kmax), x[i], Lv);
+    // e^{x/2} to ~1 ulp at the double-double node: e^{hi/2} (1 + lo/2)
+    const double eh = std::exp(0.5 * x[i].hi) * (1.0 + 0.5 * x[i].lo);
+    const dd q = div(dd{eh, 0.0}, Lv[P + 1]);
+    const dd q2 = mul(mul(q, q), x[i]);
+    r[i] = tau * (x[i].hi + x[i].lo);
+    omega[i] = tau * tau * tau * (P + 2.0) / (P + 1.0) * (q2.hi + q2.lo);
+    const double damp = 1.0 / (eh * std::pow(tau, 1.5));
+    for (int k = 0; k < kmax; ++k)
+      K[(size_t)i * kmax + k] = damp * (Lv[k].hi + Lv[k].lo) / std::sqrt((k + 1.0) * (k + 2.0));
+  }
+}
+
+}  // namespace s2w
+
 using namespace s2w;
 
 extern "C" {
@@ -190,26 +216,14 @@ s2w_status s2w_ball_plan_create(const s2w_ball_params* prm, void* stream, s2w_ba
   B->Mc = p.reality ? p.L : 2 * p.L - 1;
   const int P = p.P;
   const double tau = p.tau;
-  std::vector<dd> x = laguerre_nodes(P), Lv;
-  std::vector<double> Rf((size_t)P * P), Ri((size_t)P * P);
-  B->r.resize(P);
-  B->omega.resize(P);
-  for (int i = 0; i < P; ++i) {
-    laguerre2(P + 1, x[i], Lv);
-    const double xi = x[i].hi + x[i].lo;
-    // e^{x/2} to ~1 ulp at the double-double node: e^{hi/2} (1 + lo/2)
-    const double eh = std::exp(0.5 * x[i].hi) * (1.0 + 0.5 * x[i].lo);
-    const dd q = div(dd{eh, 0.0}, Lv[P + 1]);
-    const dd q2 = mul(mul(q, q), x[i]);
-    B->r[i] = tau * xi;
-    B->omega[i] = tau * tau * tau * (P + 2.0) / (P + 1.0) * (q2.hi + q2.lo);
-    const double damp = 1.0 / (eh * std::pow(tau, 1.5));
+  std::vector<double> Rf((size_t)P * P), Ri((size_t)P * P), Kt;
+  laguerre_rule(P, tau, P, B->r, B->omega, Kt);
+  for (int i = 0; i < P; ++i)
     for (int k = 0; k < P; ++k) {
-      const double K = damp * (Lv[k].hi + Lv[k].lo) / std::sqrt((k + 1.0) * (k + 2.0));   // K_k(r_i)
+      const double K = Kt[(size_t)i * P + k];   // K_k(r_i)
       Rf[(size_t)k * P + i] = B->omega[i] * K;
       Ri[(size_t)i * P + k] = K;
     }
-  }
   std::vector<float2> Rf2(Rf.size()), Ri2(Ri.size());
   for (size_t k = 0; k < Rf.size(); ++k) {
     float h = (float)Rf[k];

@@ -183,13 +183,140 @@ __global__ void k_dftc_inv(DftcArgs a) {
   }
 }
 
+// ------------------------------------------------- symmetric odd-length DFT stages
+// Every length here is odd (n = 2L-1 = n1 n2, Ng = 2N-1).  An odd-length DFT
+// X(k) = sum_j x_j w^{SIGN j k} (w = exp(2 pi i/p), h = (p-1)/2) pairs index j with p - j:
+//   X(0) = sum_j x_j,   X(k), X(p-k) = x_0 + C_k +- SIGN i S_k   (1 <= k <= h)
+//   C_k = sum_{j=1..h} a_j cos(2 pi j k/p),  S_k = sum_{j=1..h} b_j sin(2 pi j k/p),
+//   a_j = x_j + x_{p-j},  b_j = x_j - x_{p-j},
+// so each pair of outputs costs 2h complex-times-real products: a quarter of the direct sum.
+
+// (ah + al) + (bh + bl) as a renormalised pair
+__device__ __forceinline__ float2 add_pair(float ah, float al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float z = __fsub_rn(s, ah);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(ah, __fsub_rn(s, z)), __fsub_rn(bh, z)), __fadd_rn(al, bl));
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ float4 cadd(float4 x, float4 y, float sy) {   // x + sy * y, sy = +-1
+  if (PLAIN) return make_float4(x.x + sy * y.x, 0.f, x.z + sy * y.z, 0.f);
+  const float2 r = add_pair(x.x, x.y, sy * y.x, sy * y.y), i = add_pair(x.z, x.w, sy * y.z, sy * y.w);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ Acc comb(Acc a, float sb, Acc b) {   // a + sb * b
+  if (PLAIN) return Acc{a.s + sb * b.s, 0.f};
+  const float2 r = add_pair(a.s, a.c, sb * b.s, sb * b.c);
+  return Acc{r.x, r.y};
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ void racc(Acc& a, float xh, float xl, float wh, float wl) {   // a += x w (real)
+  if (PLAIN) a.s = fmaf(xh, wh, a.s);
+  else acc_add(a, xh, xl, wh, wl);
+}
+
+// Stage 1: for every column j2, the length-n1 DFT over j1 of x[n2 j1 + j2], times the twiddle
+// w_n^{SIGN j2 k1}, into tmp[k1 n2 + j2].  Work items: (j2, output pair).
+template <int SIGN, bool PLAIN>
+__device__ void stage1_sym(const float4* x, float4* tmp, const float4* tw, int n, int n1, int n2) {
+  const int h1 = (n1 - 1) / 2, nit = n2 * (h1 + 1);
+  for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+    const int j2 = it / (h1 + 1), kk = it - j2 * (h1 + 1);
+    const float4 x0 = x[j2];
+    if (kk == 0) {
+      Acc re{x0.x, x0.y}, im{x0.z, x0.w};
+      for (int j = 1; j < n1; ++j) {
+        const float4 v = x[n2 * j + j2];
+        racc<PLAIN>(re, v.x, v.y, 1.f, 0.f);
+        racc<PLAIN>(im, v.z, v.w, 1.f, 0.f);
+      }
+      tmp[j2] = pack<PLAIN>(re, im);
+      continue;
+    }
+    Acc cr{x0.x, x0.y}, ci{x0.z, x0.w}, sr{0.f, 0.f}, si{0.f, 0.f};
+    const int step = (n2 * kk) % n;
+    int e = step;
+    for (int j = 1; j <= h1; ++j) {
+      const float4 u = x[n2 * j + j2], v = x[n2 * (n1 - j) + j2];
+      const float4 a = cadd<PLAIN>(u, v, 1.f), b = cadd<PLAIN>(u, v, -1.f);
+      const float4 w = tw[e];
+      racc<PLAIN>(cr, a.x, a.y, w.x, w.y);
+      racc<PLAIN>(ci, a.z, a.w, w.x, w.y);
+      racc<PLAIN>(sr, b.x, b.y, w.z, w.w);
+      racc<PLAIN>(si, b.z, b.w, w.z, w.w);
+      e += step;
+      if (e >= n) e -= n;
+    }
+    const float sg = (float)SIGN;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const float t = side == 0 ? sg : -sg;   // X(kk) = C + SIGN i S, X(n1 - kk) = C - SIGN i S
+      const Acc xr = comb<PLAIN>(cr, -t, si), xi = comb<PLAIN>(ci, t, sr);
+      const int k1 = side == 0 ? kk : n1 - kk;
+      Acc r{0.f, 0.f}, i{0.f, 0.f};
+      cmac<SIGN, PLAIN>(r, i, make_float4(xr.s, xr.c, xi.s, xi.c), tw[(j2 * k1) % n]);
+      tmp[k1 * n2 + j2] = pack<PLAIN>(r, i);
+    }
+  }
+}
+
+// Stage 2: for every row k1, the length-n2 DFT of tmp[k1 n2 + j2] over j2; output k1 + n1 k2
+// goes to store(k, re, im).  AB (n float4) receives the row sums and differences first.
+template <int SIGN, bool PLAIN, class Store>
+__device__ void stage2_sym(const float4* tmp, float4* AB, const float4* tw, int n, int n1, int n2, Store store) {
+  const int h2 = (n2 - 1) / 2;
+  for (int it = threadIdx.x; it < n1 * h2; it += blockDim.x) {
+    const int k1 = it / h2, j = it - k1 * h2 + 1;
+    const float4* row = tmp + k1 * n2;
+    AB[2 * it] = cadd<PLAIN>(row[j], row[n2 - j], 1.f);
+    AB[2 * it + 1] = cadd<PLAIN>(row[j], row[n2 - j], -1.f);
+  }
+  __syncthreads();
+  const int nit = n1 * (h2 + 1);
+  for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+    const int k1 = it / (h2 + 1), kk = it - k1 * (h2 + 1);
+    const float4 x0 = tmp[k1 * n2];
+    const float4* ab = AB + 2 * k1 * h2;
+    if (kk == 0) {
+      Acc re{x0.x, x0.y}, im{x0.z, x0.w};
+      for (int j = 0; j < h2; ++j) {
+        const float4 a = ab[2 * j];
+        racc<PLAIN>(re, a.x, a.y, 1.f, 0.f);
+        racc<PLAIN>(im, a.z, a.w, 1.f, 0.f);
+      }
+      store(k1, re, im);
+      continue;
+    }
+    Acc cr{x0.x, x0.y}, ci{x0.z, x0.w}, sr{0.f, 0.f}, si{0.f, 0.f};
+    const int step = (n1 * kk) % n;
+    int e = step;
+    for (int j = 0; j < h2; ++j) {
+      const float4 a = ab[2 * j], b = ab[2 * j + 1];
+      const float4 w = tw[e];
+      racc<PLAIN>(cr, a.x, a.y, w.x, w.y);
+      racc<PLAIN>(ci, a.z, a.w, w.x, w.y);
+      racc<PLAIN>(sr, b.x, b.y, w.z, w.w);
+      racc<PLAIN>(si, b.z, b.w, w.z, w.w);
+      e += step;
+      if (e >= n) e -= n;
+    }
+    const float sg = (float)SIGN;
+    store(k1 + n1 * kk, comb<PLAIN>(cr, -sg, si), comb<PLAIN>(ci, sg, sr));
+    store(k1 + n1 * (n2 - kk), comb<PLAIN>(cr, sg, si), comb<PLAIN>(ci, -sg, sr));
+  }
+}
+
 // ----------------------------------------------------------- gamma on the map side
-// SO(3) transforms with several gamma samples: the gamma DFT is taken on the map side of
-// the alpha DFT (forward: gamma first, inverse: gamma last), so one complex alpha DFT of
-// length n serves each carried n instead of one per gamma sample.  For real signals
-// G_{-m,-n} = conj G_{m,n}: a single complex transform over all n outputs gives both n and
-// -n (m >= 0 of each), so only the n >= 0 values are transformed ("jobs").  The wavelet
-// transforms carry N of the 2N-1 values of n, so this halves the alpha-DFT work.
+// SO(3) transforms: the gamma DFT is taken on the map side of the alpha DFT (forward: gamma
+// first, inverse: gamma last), so one complex alpha DFT of length n serves each carried n
+// instead of one per gamma sample.  For real signals G_{-m,-n} = conj G_{m,n}: one complex
+// transform over all n outputs gives both n and -n (m >= 0 of each), so only the n >= 0 values
+// are transformed ("jobs").  The gamma sums pair gamma_g with gamma_{Ng-g} like the stages above.
 constexpr int kMaxJobs = 64;
 constexpr int kJobChunk = 4;   // jobs whose gamma sums share one pass over the samples
 
@@ -208,6 +335,16 @@ __device__ __forceinline__ void make_jobs(const int* nvals, int nact, bool real,
   }
 }
 
+__device__ __forceinline__ float4 load_pix(const void* pix, bool real, int64_t i) {
+  if (real) {
+    const float2 v = split1_bits(((const double*)pix)[i]);
+    return make_float4(v.x, v.y, 0.f, 0.f);
+  }
+  const double2 v = ((const double2*)pix)[i];
+  const float2 r = split1_bits(v.x), im = split1_bits(v.y);
+  return make_float4(r.x, r.y, im.x, im.y);
+}
+
 template <bool REAL, bool PLAIN>
 __global__ void k_dftg_fwd(DftcArgs a) {
   extern __shared__ float4 s4[];
@@ -220,32 +357,38 @@ __global__ void k_dftg_fwd(DftcArgs a) {
   }
   float4* tw = s4;
   float4* tmp = tw + n;
-  float4* HZ = tmp + n;   // [jobs][n]
+  float4* AB = tmp + n;
+  float4* HZ = AB + n;   // [jobs][n]
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   __syncthreads();
-  const int nj = njs;
+  const int nj = njs, Ng = a.Ng, hg = (Ng - 1) / 2;
   const int64_t ring = (int64_t)L * n;
   const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
   // H_j(alpha) = sum_g W(alpha, gamma_g) exp(-i n_j gamma_g)
   for (int j0 = 0; j0 < nj; j0 += kJobChunk) {
     const int jc = min(kJobChunk, nj - j0);
     for (int al = threadIdx.x; al < n; al += blockDim.x) {
+      const float4 w0 = load_pix(a.pix_in, REAL, base + al);
       Acc hr[kJobChunk], hi[kJobChunk];
 #pragma unroll
-      for (int q = 0; q < kJobChunk; ++q) hr[q] = hi[q] = Acc{0.f, 0.f};
-      for (int g = 0; g < a.Ng; ++g) {
-        float4 x;
-        if (REAL) x = split(make_double2(((const double*)a.pix_in)[base + g * ring + al], 0.0));
-        else x = split(((const double2*)a.pix_in)[base + g * ring + al]);
+      for (int q = 0; q < kJobChunk; ++q) {
+        hr[q] = Acc{w0.x, w0.y};
+        hi[q] = Acc{w0.z, w0.w};
+      }
+      for (int g = 1; g <= hg; ++g) {
+        const float4 xp = load_pix(a.pix_in, REAL, base + g * ring + al);
+        const float4 xm = load_pix(a.pix_in, REAL, base + (Ng - g) * ring + al);
+        const float4 u = cadd<PLAIN>(xp, xm, 1.f), v = cadd<PLAIN>(xp, xm, -1.f);
 #pragma unroll
         for (int q = 0; q < kJobChunk; ++q) {
           if (q < jc) {
-            const float4 ph = a.gph[jn[j0 + q] * a.Ng + g];
-            if (REAL && !PLAIN) {
-              acc_add(hr[q], x.x, x.y, ph.x, ph.y);
-              acc_add(hi[q], x.x, x.y, -ph.z, -ph.w);
-            } else {
-              cmac<-1, PLAIN>(hr[q], hi[q], x, ph);
+            const float4 ph = a.gph[jn[j0 + q] * Ng + g];   // cos, sin of n gamma_g
+            // u cos - i v sin
+            racc<PLAIN>(hr[q], u.x, u.y, ph.x, ph.y);
+            racc<PLAIN>(hi[q], v.x, v.y, -ph.z, -ph.w);
+            if (!REAL) {
+              racc<PLAIN>(hr[q], v.z, v.w, ph.z, ph.w);
+              racc<PLAIN>(hi[q], u.z, u.w, ph.x, ph.y);
             }
           }
         }
@@ -258,16 +401,15 @@ __global__ void k_dftg_fwd(DftcArgs a) {
   // one complex alpha DFT per job
   for (int j = 0; j < nj; ++j) {
     __syncthreads();
-    stage1<-1, PLAIN>(HZ + j * n, tmp, tw, n, a.n1, a.n2);
+    stage1_sym<-1, PLAIN>(HZ + j * n, tmp, tw, n, a.n1, a.n2);
     __syncthreads();
     const int ni = jn[j], pi = jp[j];
-    const int kcount = (REAL && pi < 0) ? L : n;   // n = 0 of a real signal: m >= 0 only
     double2* Gn = a.G + (((int64_t)b * a.nact + ni) * L + t) * a.Mc;
     double2* Gp = (pi >= 0) ? a.G + (((int64_t)b * a.nact + pi) * L + t) * a.Mc : nullptr;
-    for (int k = threadIdx.x; k < kcount; k += blockDim.x) {
-      Acc re, im;
-      stage2_one<-1, false, PLAIN>(tmp, tw, n, a.n1, a.n2, k, re, im);
-      const double zr = to_double(re) * a.scale, zi = to_double(im) * a.scale;
+    const double sc = a.scale;
+    const int mlo = a.mlo;
+    stage2_sym<-1, PLAIN>(tmp, AB, tw, n, a.n1, a.n2, [&](int k, Acc re, Acc im) {
+      const double zr = to_double(re) * sc, zi = to_double(im) * sc;
       if (REAL) {
         if (k < L) Gn[k] = make_double2(zr, zi);                 // G_{m=k, n}
         if (Gp != nullptr) {
@@ -276,9 +418,9 @@ __global__ void k_dftg_fwd(DftcArgs a) {
         }
       } else {
         const int m = (k < L) ? k : k - n;
-        Gn[m - a.mlo] = make_double2(zr, zi);
+        Gn[m - mlo] = make_double2(zr, zi);
       }
-    }
+    });
   }
 }
 
@@ -295,7 +437,8 @@ __global__ void k_dftg_inv(DftcArgs a) {
   float4* tw = s4;
   float4* x = tw + n;
   float4* tmp = x + n;
-  float4* HZ = tmp + n;   // [jobs][n]
+  float4* AB = tmp + n;
+  float4* HZ = AB + n;   // [jobs][n]
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   __syncthreads();
   const int nj = njs;
@@ -317,42 +460,49 @@ __global__ void k_dftg_inv(DftcArgs a) {
         const int m = (k < L) ? k : k - n;
         v = Gn[m - a.mlo];
       }
-      x[k] = split(v);
+      const float2 r = split1_bits(v.x), im = split1_bits(v.y);
+      x[k] = make_float4(r.x, r.y, im.x, im.y);
     }
     __syncthreads();
-    stage1<1, PLAIN>(x, tmp, tw, n, a.n1, a.n2);
+    stage1_sym<1, PLAIN>(x, tmp, tw, n, a.n1, a.n2);
     __syncthreads();
-    for (int al = threadIdx.x; al < n; al += blockDim.x) {
-      Acc re, im;
-      stage2_one<1, false, PLAIN>(tmp, tw, n, a.n1, a.n2, al, re, im);
-      HZ[j * n + al] = pack<PLAIN>(re, im);
-    }
+    float4* Z = HZ + j * n;
+    stage2_sym<1, PLAIN>(tmp, AB, tw, n, a.n1, a.n2,
+                         [&](int k, Acc re, Acc im) { Z[k] = make_float4(re.s, re.c, im.s, im.c); });
   }
   __syncthreads();
-  // W(alpha, gamma_g) = sum_j Z_j(alpha) exp(+i n_j gamma_g)  (real signals: the n, -n pair
-  // contributes 2 Re, the n = 0 job Re)
+  // W(alpha, gamma_g) = sum_j Z_j(alpha) exp(+i n_j gamma_g); gamma_g and gamma_{Ng-g} share
+  // P = sum_j Z_j cos, Q = sum_j Z_j sin.  Real signals: the n, -n pair contributes 2 Re, the
+  // n = 0 job Re.
+  const int Ng = a.Ng, hg = (Ng - 1) / 2;
   const int64_t ring = (int64_t)L * n;
   const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
-  for (int g = 0; g < a.Ng; ++g) {
-    for (int al = threadIdx.x; al < n; al += blockDim.x) {
-      Acc re{0.f, 0.f}, im{0.f, 0.f};
+  for (int al = threadIdx.x; al < n; al += blockDim.x) {
+    for (int g = 0; g <= hg; ++g) {
+      Acc pr{0.f, 0.f}, pim{0.f, 0.f}, qr{0.f, 0.f}, qim{0.f, 0.f};
       for (int j = 0; j < nj; ++j) {
-        const float4 z = HZ[j * n + al];
-        const float4 ph = a.gph[jn[j] * a.Ng + g];
-        if (REAL) {
-          const float f = (jp[j] >= 0) ? 2.f : 1.f;
-          if (PLAIN) {
-            re.s = fmaf(f * z.x, ph.x, fmaf(-f * z.z, ph.z, re.s));
-          } else {
-            acc_add(re, f * z.x, f * z.y, ph.x, ph.y);
-            acc_add(re, -f * z.z, -f * z.w, ph.z, ph.w);
-          }
-        } else {
-          cmac<1, PLAIN>(re, im, z, ph);
+        float4 z = HZ[j * n + al];
+        if (REAL && jp[j] >= 0) z = make_float4(2.f * z.x, 2.f * z.y, 2.f * z.z, 2.f * z.w);
+        const float4 ph = a.gph[jn[j] * Ng + g];
+        racc<PLAIN>(pr, z.x, z.y, ph.x, ph.y);
+        if (g > 0) racc<PLAIN>(qim, z.z, z.w, ph.z, ph.w);
+        if (!REAL) {
+          racc<PLAIN>(pim, z.z, z.w, ph.x, ph.y);
+          if (g > 0) racc<PLAIN>(qr, z.x, z.y, ph.z, ph.w);
         }
       }
-      if (REAL) ((double*)a.pix_out)[base + g * ring + al] = to_double(re);
-      else ((double2*)a.pix_out)[base + g * ring + al] = make_double2(to_double(re), to_double(im));
+      if (REAL) {
+        double* out = (double*)a.pix_out;
+        out[base + g * ring + al] = to_double(comb<PLAIN>(pr, -1.f, qim));            // P - Q
+        if (g > 0) out[base + (Ng - g) * ring + al] = to_double(comb<PLAIN>(pr, 1.f, qim));
+      } else {
+        double2* out = (double2*)a.pix_out;   // P + i Q and P - i Q
+        out[base + g * ring + al] =
+            make_double2(to_double(comb<PLAIN>(pr, -1.f, qim)), to_double(comb<PLAIN>(pim, 1.f, qr)));
+        if (g > 0)
+          out[base + (Ng - g) * ring + al] =
+              make_double2(to_double(comb<PLAIN>(pr, 1.f, qim)), to_double(comb<PLAIN>(pim, -1.f, qr)));
+      }
     }
   }
 }
@@ -385,13 +535,13 @@ int dftg_jobs(const TransformSpec& t, bool real) {
   return nj;
 }
 size_t dftg_smem(const GridTables& g, const TransformSpec& t, bool real, bool fwd) {
-  return (size_t)((fwd ? 2 : 3) * g.n + dftg_jobs(t, real) * g.n) * sizeof(float4);
+  return (size_t)((fwd ? 3 : 4) * g.n + dftg_jobs(t, real) * g.n) * sizeof(float4);
 }
 bool use_dftg(const GridTables& g, const TransformSpec& t, bool real, bool fwd) {
   if (real)   // every negative n needs its partner -n among the carried values
     for (int v : t.nvals_h)
       if (v < 0 && std::find(t.nvals_h.begin(), t.nvals_h.end(), -v) == t.nvals_h.end()) return false;
-  return t.N > 1 && dftg_jobs(t, real) <= kMaxJobs && dftg_smem(g, t, real, fwd) <= 200 * 1024;
+  return dftg_jobs(t, real) <= kMaxJobs && dftg_smem(g, t, real, fwd) <= 200 * 1024;
 }
 
 template <class K>

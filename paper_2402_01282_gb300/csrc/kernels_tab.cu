@@ -148,11 +148,44 @@ __device__ __forceinline__ void mac_tile(Acc (&acc)[4][4], const float4* Ak, con
   }
 }
 
+// asynchronous 16-byte global -> shared copies (one group per reduction chunk)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// complex float64 -> (re_hi, re_lo, im_hi, im_lo) with integer operations only
+__device__ __forceinline__ float4 split_bits(double2 v) {
+  const float2 r = split1_bits(v.x), i = split1_bits(v.y);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+
+// Copies the 32 x 64 table tile (k rows k0.., row columns row0..) into As: 1024 granules of
+// 16 bytes, 8 per thread.  `ld` = row stride of the table in float2.
+__device__ __forceinline__ void issue_tile(float4 (*As)[kRows / 2], const float2* T, int64_t ld, int k0, int row0,
+                                           int tid) {
+#pragma unroll
+  for (int q = 0; q < (kK * kRows / 2) / kThreads; ++q) {
+    const int gi = tid + q * kThreads, k = gi / (kRows / 2), c = gi - k * (kRows / 2);
+    cp_async16(&As[k][c], T + (int64_t)(k0 + k) * ld + row0 + 2 * c);
+  }
+  cp_async_commit();
+}
+
+constexpr int kBPer = kK * kMaps / kThreads;   // B entries per thread per chunk (4)
+
 struct TabInvArgs {
   const double2* coef;
   int64_t s_b, s_n, s_l;
   int mlo_in;
-  const double2* mult;
+  const double* mult_r;   // [L][nact] real factor of the inverse multiplier
+  double2 phase;          // its constant complex phase
   const int* nvals;
   int nact;
   const int64_t* off;
@@ -163,42 +196,62 @@ struct TabInvArgs {
   int B, L, Mc, mlo;
 };
 
+// Double-buffered: the table tile of chunk c+1 is copied asynchronously and its data
+// operand is fetched into registers while chunk c is contracted.
 __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
-  __shared__ float4 As[kK][kRows / 2];    // [k][row] pairs
-  __shared__ float4 Bs[kK][kMaps];        // [k][map] (re_hi, re_lo, im_hi, im_lo)
+  __shared__ __align__(16) float4 As[2][kK][kRows / 2];   // [k][row] pairs
+  __shared__ __align__(16) float4 Bs[2][kK][kMaps];       // [k][map] (re_hi, re_lo, im_hi, im_lo)
   const int rt = blockIdx.x, mi = blockIdx.y, ni = blockIdx.z;
   const int L = a.L, row0 = rt * kRows;
   if (row0 >= L) return;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~31;
-  const int kuse = kp == 0 ? 0 : ((L - l0a + kK - 1) / kK) * kK;
+  const int nch = kp == 0 ? 0 : (L - l0a + kK - 1) / kK;
   const float2* T = a.tab + a.off[idx];
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  auto load_b = [&](int c, int map0, double2 (&f)[kBPer]) {
+#pragma unroll
+    for (int q = 0; q < kBPer; ++q) {
+      const int i = tid + q * kThreads, k = i / kMaps, mp = i - k * kMaps;
+      const int l = l0a + c * kK + k, bm = map0 + mp;
+      f[q] = make_double2(0.0, 0.0);
+      if (l >= l0 && l < L && bm < a.B) {
+        const double2 v = a.coef[(int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_in)];
+        const double r = a.mult_r[(int64_t)l * a.nact + ni];
+        f[q] = make_double2(v.x * r, v.y * r);
+      }
+    }
+  };
   for (int map0 = 0; map0 < a.B; map0 += kMaps) {
     Acc acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = Acc{0.f, 0.f};
-    for (int k0 = 0; k0 < kuse; k0 += kK) {
-      __syncthreads();
-      float2* As2 = reinterpret_cast<float2*>(&As[0][0]);
-      for (int i = tid; i < kK * kRows; i += kThreads) {
-        const int k = i / kRows, r = i - k * kRows;
-        As2[i] = T[(int64_t)(k0 + k) * a.Lp + row0 + r];
+    double2 f[kBPer];
+    if (nch > 0) {
+      issue_tile(As[0], T, a.Lp, 0, row0, tid);
+      load_b(0, map0, f);
+    }
+    for (int c = 0; c < nch; ++c) {
+      const int buf = c & 1;
+#pragma unroll
+      for (int q = 0; q < kBPer; ++q) {
+        const int i = tid + q * kThreads;
+        Bs[buf][i / kMaps][i % kMaps] = split_bits(f[q]);
       }
-      for (int i = tid; i < kK * kMaps; i += kThreads) {
-        const int k = i / kMaps, mp = i - k * kMaps, l = l0a + k0 + k, bm = map0 + mp;
-        double2 f = make_double2(0.0, 0.0);
-        if (l >= l0 && l < L && bm < a.B)
-          f = cmul2(a.coef[(int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_in)],
-                    a.mult[(int64_t)l * a.nact + ni]);
-        Bs[k][mp] = split(f);
+      if (c + 1 < nch) {
+        issue_tile(As[buf ^ 1], T, a.Lp, (c + 1) * kK, row0, tid);
+        load_b(c + 1, map0, f);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
       __syncthreads();
 #pragma unroll 4
-      for (int k = 0; k < kK; ++k) mac_tile(acc, As[k], Bs[k], ty, tx);
+      for (int k = 0; k < kK; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
+      __syncthreads();
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -207,9 +260,11 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int bm = map0 + 2 * tx + p;
-        if (bm < a.B)
+        if (bm < a.B) {
+          const double x = to_double(acc[r][2 * p]), y = to_double(acc[r][2 * p + 1]);
           a.G[(((int64_t)bm * a.nact + ni) * L + beta) * a.Mc + mi] =
-              make_double2(to_double(acc[r][2 * p]), to_double(acc[r][2 * p + 1]));
+              make_double2(fma(x, a.phase.x, -y * a.phase.y), fma(x, a.phase.y, y * a.phase.x));
+        }
       }
     }
   }
@@ -231,38 +286,53 @@ struct TabFwdArgs {
 };
 
 __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
-  __shared__ float4 As[kK][kRows / 2];    // [k = beta'][row = l] pairs
-  __shared__ float4 Bs[kK][kMaps];        // [k = beta'][map]
+  __shared__ __align__(16) float4 As[2][kK][kRows / 2];   // [k = beta'][row = l] pairs
+  __shared__ __align__(16) float4 Bs[2][kK][kMaps];       // [k = beta'][map]
   const int rt = blockIdx.x, mi = blockIdx.y, ni = blockIdx.z;
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
   const int row0 = rt * kRows;
   if (row0 >= kp) return;
   const int L = a.L, m = a.mlo + mi, nn = a.nvals[ni];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~31;
+  const int nch = (L + kK - 1) / kK;
   const float2* T = a.tab + a.off[idx];
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  auto load_b = [&](int c, int map0, double2 (&f)[kBPer]) {
+#pragma unroll
+    for (int q = 0; q < kBPer; ++q) {
+      const int i = tid + q * kThreads, k = i / kMaps, mp = i - k * kMaps;
+      const int beta = c * kK + k, bm = map0 + mp;
+      f[q] = (beta < L && bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * L + beta) * a.Mc + mi]
+                                    : make_double2(0.0, 0.0);
+    }
+  };
   for (int map0 = 0; map0 < a.B; map0 += kMaps) {
     Acc acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = Acc{0.f, 0.f};
-    for (int k0 = 0; k0 < L; k0 += kK) {
-      __syncthreads();
-      float2* As2 = reinterpret_cast<float2*>(&As[0][0]);
-      for (int i = tid; i < kK * kRows; i += kThreads) {
-        const int k = i / kRows, r = i - k * kRows;
-        As2[i] = T[(int64_t)(k0 + k) * kp + row0 + r];
+    double2 f[kBPer];
+    issue_tile(As[0], T, kp, 0, row0, tid);
+    load_b(0, map0, f);
+    for (int c = 0; c < nch; ++c) {
+      const int buf = c & 1;
+#pragma unroll
+      for (int q = 0; q < kBPer; ++q) {
+        const int i = tid + q * kThreads;
+        Bs[buf][i / kMaps][i % kMaps] = split_bits(f[q]);
       }
-      for (int i = tid; i < kK * kMaps; i += kThreads) {
-        const int k = i / kMaps, mp = i - k * kMaps, beta = k0 + k, bm = map0 + mp;
-        double2 g = make_double2(0.0, 0.0);
-        if (beta < L && bm < a.B) g = a.G[(((int64_t)bm * a.nact + ni) * L + beta) * a.Mc + mi];
-        Bs[k][mp] = split(g);
+      if (c + 1 < nch) {
+        issue_tile(As[buf ^ 1], T, kp, (c + 1) * kK, row0, tid);
+        load_b(c + 1, map0, f);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
       __syncthreads();
 #pragma unroll 4
-      for (int k = 0; k < kK; ++k) mac_tile(acc, As[k], Bs[k], ty, tx);
+      for (int k = 0; k < kK; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
+      __syncthreads();
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -343,7 +413,8 @@ cudaError_t launch_tab_inverse(const GridTables& g, const TransformSpec& t, Coef
   a.s_n = in.s_n;
   a.s_l = in.s_l;
   a.mlo_in = in.mlo;
-  a.mult = t.mult_inv;
+  a.mult_r = t.minv_r;
+  a.phase = t.minv_phase;
   a.nvals = t.nvals;
   a.nact = t.nact;
   a.off = tab.off_inv;

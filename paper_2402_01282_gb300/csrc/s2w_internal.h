@@ -70,6 +70,11 @@ struct TransformSpec {
   std::vector<int> nvals_h;
   double2* mult_inv = nullptr;  // [L][nact] multiplier applied before the inverse contraction
   double2* mult_fwd = nullptr;  // [L][nact] multiplier applied after the forward contraction
+  // mult_inv = minv_phase * minv_r with one complex phase for the whole transform (the
+  // wavelet multipliers carry the constant factor xi of Eq. A8); minv_factored says it holds
+  double* minv_r = nullptr;     // [L][nact] real factor
+  double2 minv_phase{1.0, 0.0};
+  bool minv_factored = false;
   double2* gphase = nullptr;    // [nact][2N-1] exp(+i n gamma_g)
   float4* gphase4 = nullptr;    // the same as float pairs
   double gscale = 1.0;          // gamma quadrature factor 2 pi/(2N-1) (1 for the SHT)
