@@ -22,9 +22,11 @@ be read against the paper:
 * ``wavelet``   Algorithm 1 (Sec. 4, Eqs. 40-42) with the multiresolution
                 band-limits of Sec. 3.3 (Eq. 38).
 * ``laguerre``  Fourier-Laguerre radial transform (Sec. 2.3, Eqs. 6-11).
+* ``ballwav``   directional wavelet transform on the ball (Sec. 3.2, App. A.3-A.4) with the
+                radial multiresolution of Sec. 3.3.
 * ``adjoint``   adjoints of the analysis and synthesis operators (Sec. 4.3), by brute
                 force: the conjugate transpose of the operator's matrix (tiny L only).
 
 Parity pins for each function live in ``tests/test_oracle_*.py``.
 """
-from . import sampling, wigner, harmonic, filters, wavelet, laguerre, adjoint  # noqa: F401
+from . import sampling, wigner, harmonic, filters, wavelet, laguerre, adjoint, ballwav  # noqa: F401
