@@ -188,6 +188,51 @@ s2w_status s2w_ball_sl_forward(const s2w_ball_plan* plan, const void* f, void* f
 /* Z^-1 (Eq. 11): f_lmp -> ball pixels. */
 s2w_status s2w_ball_sl_inverse(const s2w_ball_plan* plan, const void* flmp, void* f, void* stream);
 
+/* ---- ball: directional wavelet transform (Sec. 3.2; Sec. 5.1, Algorithm 2) ----------------
+ * Wavelets Psi^{jj'}_lnp = sqrt((2l+1)/(8 pi^2)) kappa^j(l) kappa^{j'}(p) zeta_ln (App. A.4) for
+ * angular scales j = J0..J (as in s2w_params) and radial scales j' = J0r..J', J' the smallest
+ * integer with nu^J' >= P, kappa^{j'}(p) = kappa_nu(p / nu^j').  Multiresolution (Sec. 3.3):
+ * scale (j, j') is sampled on the MW SO(3) grid at (L_j, N_j) and on the P_j'-node
+ * Gauss-Laguerre rule, P_j' = min(ceil(nu^(j'+1)), P), r'_i = tau x'_i.  Scaling function:
+ * |Phi_l0p|^2 (4 pi/(2l+1)) = A + B - A B with A = k_lambda(l/lambda^J0), B = k_nu(p/nu^J0r)
+ * (the reading of App. A.4 that satisfies the admissibility condition of Sec. 3.2); the
+ * scaling coefficients W^Phi are sampled at full resolution (P nodes, MW grid at L).
+ * Spin 0 only (S2W_EUNSUPPORTED otherwise); real fields when reality = 1.
+ * Layouts: field f and scaling coefficients [batch][P node][L][2L-1]; wavelet coefficients
+ * wav: one block per scale k in the order of s2w_ball_wav_query_layout (j outer, j' inner),
+ * block k = [batch][P_j' node][2N_j-1 gamma][L_j beta][2L_j-1 alpha], starting at element
+ * wav_offsets[k] (offsets over the WHOLE batch, unlike s2w_query_layout).
+ * The plan holds a sphere wavelet plan over batch*P node maps and two workspaces of
+ * batch*P*L*Mc complex.  Same stream, allocation and error conventions as s2w_forward. */
+typedef struct {
+  int L, N, P, J0, J0r, spin, reality, batch, precision, precompute;   /* precision/precompute as s2w_params */
+  double lambda, nu, tau;
+} s2w_ball_wav_params;
+
+typedef struct s2w_ball_wav_plan s2w_ball_wav_plan;
+
+s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* params, void* stream, s2w_ball_wav_plan** out);
+s2w_status s2w_ball_wav_plan_destroy(s2w_ball_wav_plan* plan);
+/* Element counts of one field and of all wavelet blocks; the number of scales; per scale k its
+ * (j, j'), offset, L_j, N_j and P_j' (arrays of nscales entries, offsets nscales+1; any may be
+ * NULL; query nscales first). */
+s2w_status s2w_ball_wav_query_layout(const s2w_ball_wav_plan* plan, int64_t* field_elems, int64_t* wav_elems,
+                                     int* nscales, int* j, int* jr, int64_t* wav_offsets, int* Lj, int* Nj,
+                                     int* Pj);
+/* Analysis (Sec. 5.1, Algorithm 2): f -> wav, scal. */
+s2w_status s2w_ball_forward(const s2w_ball_wav_plan* plan, const void* f, void* wav, void* scal, void* stream);
+/* Synthesis (Sec. 5.1, Eq. for the inverse): wav, scal -> f; exact inverse of s2w_ball_forward on
+ * band-limited fields. */
+s2w_status s2w_ball_inverse(const s2w_ball_wav_plan* plan, const void* wav, const void* scal, void* f,
+                            void* stream);
+/* Adjoints (transposes for real fields) of the two, as for the sphere. */
+s2w_status s2w_ball_forward_adjoint(const s2w_ball_wav_plan* plan, const void* gwav, const void* gscal, void* gf,
+                                    void* stream);
+s2w_status s2w_ball_inverse_adjoint(const s2w_ball_wav_plan* plan, const void* gf, void* gwav, void* gscal,
+                                    void* stream);
+/* s2w_check of the plan's sphere transforms (synchronises, reads the device error word). */
+s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
+
 /* The inverse spin SHT of s2w_sht_inverse, for callers that cannot allocate device memory
  * when they need it (a host application that owns every device allocation and forbids new
  * ones after start-up, or code running while a CUDA graph is captured, where cudaMalloc is not

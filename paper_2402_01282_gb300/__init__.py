@@ -27,7 +27,10 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_check", "s2w_last_error", "s2w_version", "s2w_trace_enable", "s2w_trace_reset",
            "s2w_trace_read", "s2w_kernel_name", "s2w_sht_inverse_static", "s2w_ball_plan_create",
            "s2w_ball_plan_destroy", "s2w_ball_nodes", "s2w_laguerre_forward", "s2w_laguerre_inverse",
-           "s2w_ball_sl_forward", "s2w_ball_sl_inverse", "s2w_forward_adjoint", "s2w_inverse_adjoint"]
+           "s2w_ball_sl_forward", "s2w_ball_sl_inverse", "s2w_forward_adjoint", "s2w_inverse_adjoint",
+           "s2w_ball_wav_plan_create", "s2w_ball_wav_plan_destroy", "s2w_ball_wav_query_layout",
+           "s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint",
+           "s2w_ball_wav_check"]
 KERNEL_KINDS = 5
 
 
@@ -40,6 +43,13 @@ class S2WError(RuntimeError):
 class BallParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("P", ctypes.c_int), ("spin", ctypes.c_int), ("reality", ctypes.c_int),
                 ("batch", ctypes.c_int), ("precision", ctypes.c_int), ("tau", ctypes.c_double)]
+
+
+class BallWavParams(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("N", ctypes.c_int), ("P", ctypes.c_int), ("J0", ctypes.c_int),
+                ("J0r", ctypes.c_int), ("spin", ctypes.c_int), ("reality", ctypes.c_int), ("batch", ctypes.c_int),
+                ("precision", ctypes.c_int), ("precompute", ctypes.c_int), ("lam", ctypes.c_double),
+                ("nu", ctypes.c_double), ("tau", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -70,6 +80,12 @@ def load(path: str = LIB_PATH):
     lib.s2w_wigner_forward.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.s2w_wigner_inverse.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.s2w_check.argtypes = [vp]
+    lib.s2w_ball_wav_plan_create.argtypes = [ctypes.POINTER(BallWavParams), vp, ctypes.POINTER(vp)]
+    lib.s2w_ball_wav_plan_destroy.argtypes = [vp]
+    lib.s2w_ball_wav_query_layout.argtypes = [vp, i64p, i64p, ip, ip, ip, i64p, ip, ip, ip]
+    for name in ("s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp, vp]
+    lib.s2w_ball_wav_check.argtypes = [vp]
     lib.s2w_last_error.restype = ctypes.c_char_p
     lib.s2w_version.restype = ctypes.c_char_p
     lib.s2w_trace_enable.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -305,6 +321,85 @@ class BallPlan:
     def close(self):
         if getattr(self, "_h", None):
             _lib.s2w_ball_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BallWavPlan:
+    """Directional wavelet transform on the ball (Sec. 3.2, Algorithm 2) of a batch of spin-0
+    fields with angular band-limit L, radial band-limit P and N directions."""
+
+    def __init__(self, L: int, N: int, P: int, lam: float = 2.0, nu: float = 2.0, J0: int = 0, J0r: int = 0,
+                 tau: float = 1.0, reality: bool = True, batch: int = 1, precision: int = S2W_FP64,
+                 precompute: int = 0, stream=None):
+        lib = load()
+        self.params = BallWavParams(L, N, P, J0, J0r, 0, int(reality), batch, precision, int(precompute),
+                                    float(lam), float(nu), float(tau))
+        h = ctypes.c_void_p()
+        _check(lib.s2w_ball_wav_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.L, self.N, self.P, self.batch = L, N, P, batch
+        self.real = bool(reality)
+        fe, we, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib.s2w_ball_wav_query_layout(h, ctypes.byref(fe), ctypes.byref(we), ctypes.byref(ns),
+                                             None, None, None, None, None, None))
+        n = ns.value
+        arr = lambda t, k: (t * k)()   # noqa: E731
+        j, jr, Lj, Nj, Pj = arr(ctypes.c_int, n), arr(ctypes.c_int, n), arr(ctypes.c_int, n), arr(ctypes.c_int, n), \
+            arr(ctypes.c_int, n)
+        offs = arr(ctypes.c_int64, n + 1)
+        _check(lib.s2w_ball_wav_query_layout(h, None, None, None, j, jr, offs, Lj, Nj, Pj))
+        self.field_elems, self.wav_elems, self.nscales = fe.value, we.value, n
+        self.scales = [(j[k], jr[k]) for k in range(n)]
+        self.Lj, self.Nj, self.Pj = list(Lj), list(Nj), list(Pj)
+        self.wav_offsets = list(offs)
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.real else torch.complex128
+
+    def empty_field(self, device="cuda"):
+        import torch
+        return torch.empty((self.batch, self.P, self.L, 2 * self.L - 1), dtype=self.dtype, device=device)
+
+    def empty_wav(self, device="cuda"):
+        import torch
+        return torch.empty((self.wav_elems,), dtype=self.dtype, device=device)
+
+    def scale_view(self, wav, k: int):
+        """Block k of the wavelet coefficients as [batch, P_j', 2N_j-1, L_j, 2L_j-1]."""
+        a, b = self.wav_offsets[k], self.wav_offsets[k + 1]
+        return wav[a:b].view(self.batch, self.Pj[k], 2 * self.Nj[k] - 1, self.Lj[k], 2 * self.Lj[k] - 1)
+
+    def forward(self, f, wav, scal, stream=None):
+        _check(_lib.s2w_ball_forward(self._h, _ptr(f, self.real, "f"), _ptr(wav, self.real, "wav"),
+                                     _ptr(scal, self.real, "scal"), _stream(stream)))
+
+    def inverse(self, wav, scal, f, stream=None):
+        _check(_lib.s2w_ball_inverse(self._h, _ptr(wav, self.real, "wav"), _ptr(scal, self.real, "scal"),
+                                     _ptr(f, self.real, "f"), _stream(stream)))
+
+    def forward_adjoint(self, gwav, gscal, gf, stream=None):
+        _check(_lib.s2w_ball_forward_adjoint(self._h, _ptr(gwav, self.real, "gwav"),
+                                             _ptr(gscal, self.real, "gscal"), _ptr(gf, self.real, "gf"),
+                                             _stream(stream)))
+
+    def inverse_adjoint(self, gf, gwav, gscal, stream=None):
+        _check(_lib.s2w_ball_inverse_adjoint(self._h, _ptr(gf, self.real, "gf"), _ptr(gwav, self.real, "gwav"),
+                                             _ptr(gscal, self.real, "gscal"), _stream(stream)))
+
+    def check(self):
+        _check(_lib.s2w_ball_wav_check(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.s2w_ball_wav_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -39,6 +39,9 @@ s2w_status check_ptr(const void* p, bool real_elems, const char* name) {
 }
 
 int Mc_at(const s2w_plan* P, int L) { return P->real ? L : 2 * L - 1; }
+// maps per launch: the plan's batch unless an internal caller (the ball transforms) runs a
+// different number of maps through the plan's transforms
+int batch_of(const s2w_plan* P) { return P->cur_batch > 0 ? P->cur_batch : P->p.batch; }
 int mlo_at(const s2w_plan* P, int L) { return P->real ? 0 : -(L - 1); }
 
 const GridTables& grid_of(const s2w_plan* P, const TransformSpec& t) { return P->grids[t.grid]; }
@@ -56,7 +59,7 @@ CoefArgs flm_ws_args(const s2w_plan* P) {
 ColumnArgs cols(const s2w_plan* P, int nact, int L) {
   ColumnArgs c;
   c.G = P->g_ws;
-  c.B = P->p.batch;
+  c.B = batch_of(P);
   c.nact = nact;
   c.L = L;
   c.Mc = Mc_at(P, L);
@@ -81,7 +84,7 @@ double contraction_terms(const s2w_plan* P, const TransformSpec& t) {
 }
 
 double dft_flops(const s2w_plan* P, const TransformSpec& t) {
-  const double n = 2.0 * t.L - 1.0, B = P->p.batch, Ng = 2.0 * t.N - 1.0;
+  const double n = 2.0 * t.L - 1.0, B = batch_of(P), Ng = 2.0 * t.N - 1.0;
   const double ring = (P->real ? 2.5 : 5.0) * n * std::log2(n);
   return B * Ng * t.L * ring + 8.0 * B * t.L * Mc_at(P, t.L) * t.nact * Ng;
 }
@@ -89,7 +92,7 @@ double dft_flops(const s2w_plan* P, const TransformSpec& t) {
 // algorithmic flops per contraction term: the recursion step (5, unless the d values come
 // from precomputed tables) plus a complex-times-real multiply-add (4) per map
 double term_flops(const s2w_plan* P, const TransformSpec& t) {
-  return (t.tab || t.tc ? 0.0 : 5.0) + 4.0 * P->p.batch;
+  return (t.tab || t.tc ? 0.0 : 5.0) + 4.0 * batch_of(P);
 }
 
 struct TraceScope {
@@ -173,7 +176,7 @@ s2w_status adj_inv_transform(s2w_plan* P, const TransformSpec& t, const void* pi
              "azimuthal DFT (adjoint of the inverse DFT)");
   }
   {
-    TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
+    TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * batch_of(P)) : 0.0);
     S2W_CUDA(launch_wigner_forward(P, g, ta, c, out, st, false), "adjoint of the inverse contraction");
   }
   return S2W_OK;
@@ -190,12 +193,12 @@ s2w_status adj_fwd_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, v
   ta.tc = nullptr;
   ta.tab = nullptr;
   {
-    TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * P->p.batch) : 0.0);
+    TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * batch_of(P)) : 0.0);
     S2W_CUDA(launch_wigner_inverse(P, g, ta, in, c, st), "adjoint of the forward contraction");
   }
   {
     TraceScope ts(P, st, K_QUAD_ADJ,
-                  P->trace_on ? 4.0 * P->p.batch * t.nact * (double)Mc_at(P, t.L) * t.L * t.L : 0.0);
+                  P->trace_on ? 4.0 * batch_of(P) * t.nact * (double)Mc_at(P, t.L) * t.L * t.L : 0.0);
     S2W_CUDA(launch_quad_adjoint(P, g, ta, c, st), "transposed colatitude quadrature");
   }
   {
@@ -214,6 +217,33 @@ size_t pix_bytes(const s2w_plan* P) { return P->real ? sizeof(double) : sizeof(d
 namespace s2w {
 // Lets other translation units report through s2w_last_error().
 s2w_status record_error(s2w_status s, const std::string& msg) { return fail(s, msg); }
+
+// The per-transform steps for other translation units, with `batch` maps per launch.
+struct BatchScope {
+  s2w_plan* P;
+  BatchScope(s2w_plan* P_, int b) : P(P_) { P->cur_batch = b; }
+  ~BatchScope() { P->cur_batch = 0; }
+};
+s2w_status run_fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, int64_t pix_sb, CoefArgs out,
+                             int batch, cudaStream_t st) {
+  BatchScope bs(P, batch);
+  return fwd_transform(P, t, pix, pix_sb, out, st);
+}
+s2w_status run_inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void* pix, int64_t pix_sb,
+                             int batch, cudaStream_t st) {
+  BatchScope bs(P, batch);
+  return inv_transform(P, t, in, pix, pix_sb, st);
+}
+s2w_status run_adj_fwd_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void* pix, int64_t pix_sb,
+                                 int batch, cudaStream_t st) {
+  BatchScope bs(P, batch);
+  return adj_fwd_transform(P, t, in, pix, pix_sb, st);
+}
+s2w_status run_adj_inv_transform(s2w_plan* P, const TransformSpec& t, const void* pix, int64_t pix_sb,
+                                 CoefArgs out, int batch, cudaStream_t st) {
+  BatchScope bs(P, batch);
+  return adj_inv_transform(P, t, pix, pix_sb, out, st);
+}
 }  // namespace s2w
 
 extern "C" {

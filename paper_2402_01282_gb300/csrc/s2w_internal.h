@@ -107,6 +107,7 @@ struct s2w_plan {
 
   bool tensor = false;                 // reduced-precision modes (S2W_FP32_SPLIT, S2W_BF16)
   std::vector<s2w::TcTable*> tc_tables;  // owned
+  int cur_batch = 0;                   // > 0: maps per launch for an internal caller (ball transforms)
   bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
   std::vector<s2w::TabTable*> tab_tables;  // owned
   double2* flm_ws = nullptr;           // [batch][L][Mc] harmonic workspace
@@ -127,6 +128,19 @@ namespace s2w {
 
 // Records a failure message for s2w_last_error() and returns s (api.cpp).
 s2w_status record_error(s2w_status s, const std::string& msg);
+
+// One transform's steps (api.cpp) with `batch` maps per launch: fwd = pixels -> harmonic
+// accumulation (DFT, quadrature, contraction, products), inv = harmonic -> pixels, and their
+// adjoints; coefficient strides come from the CoefArgs, pixel strides from pix_sb.
+struct CoefArgs;
+s2w_status run_fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, int64_t pix_sb, CoefArgs out,
+                             int batch, cudaStream_t st);
+s2w_status run_inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void* pix, int64_t pix_sb,
+                             int batch, cudaStream_t st);
+s2w_status run_adj_fwd_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void* pix, int64_t pix_sb,
+                                 int batch, cudaStream_t st);
+s2w_status run_adj_inv_transform(s2w_plan* P, const TransformSpec& t, const void* pix, int64_t pix_sb,
+                                 CoefArgs out, int batch, cudaStream_t st);
 
 // Host-side plan construction (plan.cpp).
 s2w_status build_plan(const s2w_params& p, cudaStream_t stream, s2w_plan* plan, std::string& err);
