@@ -167,6 +167,47 @@ PRECISION_DOC = {
 DIFF_L, DIFF_N, DIFF_J0, DIFF_B = 512, 4, 3, 8
 
 
+# Ball study: one real field at L = P = 128, N = 4, lambda = nu = 2, J0 = J0' = 0.
+BALL_L, BALL_P, BALL_N = 128, 128, 4
+
+
+def run_ball(torch, s2w, stream, flush, steps, precision):
+    """Ball wavelet round trips per second (analysis + synthesis of one field, device time,
+    L2 flushed) and the round-trip error."""
+    import numpy as np
+    import synth
+    plan = s2w.BallWavPlan(BALL_L, BALL_N, BALL_P, 2.0, 2.0, 0, 0, batch=1, precision=PRECISIONS[precision],
+                           precompute=PRECOMPUTE.get(precision, 0))
+    bp = s2w.BallPlan(BALL_L, BALL_P, reality=True, batch=1)
+    flmp = synth.flmp_random(BALL_L, BALL_P, synth.rng_for(5, 0), reality=True)[None, :, :, BALL_L - 1:]
+    f = plan.empty_field()
+    bp.sl_inverse(torch.from_numpy(np.ascontiguousarray(flmp)).cuda(), f)
+    wav, scal, f2 = plan.empty_wav(), plan.empty_field(), plan.empty_field()
+    for _ in range(3):
+        plan.forward(f, wav, scal)
+        plan.inverse(wav, scal, f2)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        plan.forward(f, wav, scal)
+        plan.inverse(wav, scal, f2)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    err = float((f2 - f).abs().max() / f.abs().max())
+    out = {"workload": f"ball L={BALL_L} P={BALL_P} N={BALL_N} lambda=nu=2 J0=J0'=0, 1 real field, "
+                       "f_lmp ~ N(0, (l+1)^-2 (p+1)^-2)",
+           "value": len(ms) / (sum(ms) * 1e-3), "unit": "ball transforms/s (fwd+inv)",
+           "ms_per_step": sum(ms) / len(ms), "precision": precision, "max_rel_err": err,
+           "wavelet_coefficients_bytes": int(plan.wav_elems * 8)}
+    plan.close()
+    bp.close()
+    return out
+
+
 def run_differentiation(torch, s2w, stream, flush, steps):
     """Loss-gradient evaluations per second (analysis + adjoint, device time, L2 flushed) and
     a central finite-difference check of one directional derivative."""
@@ -326,6 +367,9 @@ def run_ours(args, world, rank, local):
     diff = None
     if not args.no_diff:
         diff = run_differentiation(torch, s2w, stream, flush, max(3, args.steps // 2))
+    ball = None
+    if not args.no_ball:
+        ball = run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)
 
     if rank != 0:
         if dist:
@@ -355,6 +399,7 @@ def run_ours(args, world, rank, local):
         "max_rel_err": err,
         "other_modes": other,
         "differentiation": diff,
+        "ball": ball,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
@@ -413,6 +458,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the plain float64 path")
     ap.add_argument("--precision", default="fp64_table", choices=sorted(PRECISIONS))
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-study timing")
+    ap.add_argument("--no-ball", action="store_true", help="skip the ball-study timing")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
