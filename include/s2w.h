@@ -246,6 +246,34 @@ s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
  * layouts and results as s2w_sht_inverse. */
 s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f, void* stream);
 
+/* ---- runtime: autotuner and batch executor ------------------------------------------
+ * s2w_plan_autotune times, on the plan's own shapes and workspace, the candidate launch shapes
+ * of its kernels (threads per block of the DFT kernels: 128, 256, 512; maps per block of the
+ * on-the-fly inverse contraction: 4, 8, 16) for every transform of the plan (spin SHT,
+ * scaling function, each wavelet scale) and keeps the fastest.  Synchronises the stream;
+ * allocates a pixel scratch for the duration of the call; overwrites the plan's workspaces.
+ * The paper has no counterpart (its kernels are compiled by XLA). */
+s2w_status s2w_plan_autotune(s2w_plan* plan, void* stream);
+/* The launch shapes in use for transform `transform` (0 = spin SHT, 1 = scaling function,
+ * 2 + s = wavelet scale s); any output may be NULL. */
+s2w_status s2w_plan_launch_shapes(const s2w_plan* plan, int transform, int* dft_threads_fwd,
+                                  int* dft_threads_inv, int* inv_mb);
+
+/* A batch runs the transforms of `count` distinct plans (maps of different band-limits, spins
+ * and sizes) as one CUDA graph: the plans' calls are captured once on a fork of streams (one
+ * per plan), so independent transforms overlap on the GPU, and s2w_batch_launch replays the
+ * whole graph with one launch.  what = 0: analysis in[i] -> wav[i], scal[i]; 1: synthesis
+ * wav[i], scal[i] -> out[i]; 2: both in sequence.  The device buffers are fixed at creation
+ * (arrays of count pointers; in or out may be NULL when unused) and must outlive the batch.
+ * A plan may appear once.  The plans must not be used by other calls while a launch of the
+ * batch is running (they share the plans' workspaces).  (Batching of Sec. 4.3; the graph is
+ * this library's form of it.) */
+typedef struct s2w_batch s2w_batch;
+s2w_status s2w_batch_create(s2w_plan* const* plans, int count, const void* const* in, void* const* wav,
+                            void* const* scal, void* const* out, int what, void* stream, s2w_batch** batch);
+s2w_status s2w_batch_launch(s2w_batch* batch, void* stream);
+s2w_status s2w_batch_destroy(s2w_batch* batch);
+
 /* Synchronises the plan's last stream, then reads and clears the device error word.
  * Returns S2W_OK, S2W_ECUDA (asynchronous CUDA error) or the recorded status. */
 s2w_status s2w_check(const s2w_plan* plan);

@@ -30,7 +30,8 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_ball_sl_forward", "s2w_ball_sl_inverse", "s2w_forward_adjoint", "s2w_inverse_adjoint",
            "s2w_ball_wav_plan_create", "s2w_ball_wav_plan_destroy", "s2w_ball_wav_query_layout",
            "s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint",
-           "s2w_ball_wav_check"]
+           "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_batch_create",
+           "s2w_batch_launch", "s2w_batch_destroy"]
 KERNEL_KINDS = 5
 
 
@@ -86,6 +87,12 @@ def load(path: str = LIB_PATH):
     for name in ("s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint"):
         getattr(lib, name).argtypes = [vp, vp, vp, vp, vp]
     lib.s2w_ball_wav_check.argtypes = [vp]
+    lib.s2w_plan_autotune.argtypes = [vp, vp]
+    lib.s2w_plan_launch_shapes.argtypes = [vp, ctypes.c_int, ip, ip, ip]
+    vpp = ctypes.POINTER(vp)
+    lib.s2w_batch_create.argtypes = [vpp, ctypes.c_int, vpp, vpp, vpp, vpp, ctypes.c_int, vp, vpp]
+    lib.s2w_batch_launch.argtypes = [vp, vp]
+    lib.s2w_batch_destroy.argtypes = [vp]
     lib.s2w_last_error.restype = ctypes.c_char_p
     lib.s2w_version.restype = ctypes.c_char_p
     lib.s2w_trace_enable.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -243,6 +250,18 @@ class Plan:
     def check(self):
         _check(_lib.s2w_check(self._h))
 
+    # ------------------------------------------------------------------ runtime
+    def autotune(self, stream=None):
+        """Times the candidate launch shapes on this plan's shapes and keeps the fastest."""
+        _check(_lib.s2w_plan_autotune(self._h, _stream(stream)))
+
+    def launch_shapes(self, transform: int):
+        """(DFT threads forward, DFT threads inverse, maps per block of the inverse contraction)
+        of transform 0 (spin SHT), 1 (scaling function) or 2 + s (wavelet scale s)."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.s2w_plan_launch_shapes(self._h, transform, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
     # ------------------------------------------------------------------ tracing
     def trace(self, on: bool = True, capacity: int = 4096):
         _check(_lib.s2w_trace_enable(self._h, int(on), capacity))
@@ -321,6 +340,44 @@ class BallPlan:
     def close(self):
         if getattr(self, "_h", None):
             _lib.s2w_ball_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Transforms of several plans replayed as one CUDA graph (s2w_batch_*).  `what`: 0 analysis,
+    1 synthesis, 2 both.  The tensors are bound at creation and must stay alive."""
+
+    def __init__(self, plans, f=None, wav=None, scal=None, out=None, what: int = 2, stream=None):
+        lib = load()
+        n = len(plans)
+        vp = ctypes.c_void_p
+
+        def arr(ts, name):
+            if ts is None:
+                return None
+            a = (vp * n)()
+            for i, (t, p) in enumerate(zip(ts, plans)):
+                a[i] = _ptr(t, p.real, name)
+            return a
+        self._keep = (list(plans), f, wav, scal, out)
+        hp = (vp * n)(*[p._h for p in plans])
+        h = vp()
+        _check(lib.s2w_batch_create(hp, n, arr(f, "f"), arr(wav, "wav"), arr(scal, "scal"), arr(out, "out"), what,
+                                    _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.s2w_batch_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.s2w_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -545,10 +545,10 @@ bool use_dftg(const GridTables& g, const TransformSpec& t, bool real, bool fwd) 
 }
 
 template <class K>
-cudaError_t launch(K kern, dim3 grid, size_t smem, cudaStream_t st, const DftcArgs& a) {
+cudaError_t launch(K kern, dim3 grid, size_t smem, cudaStream_t st, const DftcArgs& a, int threads = 256) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 256, smem, st>>>(a);
+  kern<<<grid, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -564,8 +564,10 @@ cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, con
   dim3 grid(c.L, c.B);
   if (use_dftg(g, t, real, true)) {
     const size_t sm = dftg_smem(g, t, real, true);
-    if (plain) return real ? launch(k_dftg_fwd<true, true>, grid, sm, st, a) : launch(k_dftg_fwd<false, true>, grid, sm, st, a);
-    return real ? launch(k_dftg_fwd<true, false>, grid, sm, st, a) : launch(k_dftg_fwd<false, false>, grid, sm, st, a);
+    const int th = t.dft_threads_fwd;
+    if (plain)
+      return real ? launch(k_dftg_fwd<true, true>, grid, sm, st, a, th) : launch(k_dftg_fwd<false, true>, grid, sm, st, a, th);
+    return real ? launch(k_dftg_fwd<true, false>, grid, sm, st, a, th) : launch(k_dftg_fwd<false, false>, grid, sm, st, a, th);
   }
   const size_t smem = (size_t)(3 * g.n + a.Ng * c.Mc) * sizeof(float4);
   if (plain) return real ? launch(k_dftc_fwd<true, true>, grid, smem, st, a) : launch(k_dftc_fwd<false, true>, grid, smem, st, a);
@@ -581,8 +583,10 @@ cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, Col
   dim3 grid(c.L, c.B);
   if (use_dftg(g, t, real, false)) {
     const size_t sm = dftg_smem(g, t, real, false);
-    if (plain) return real ? launch(k_dftg_inv<true, true>, grid, sm, st, a) : launch(k_dftg_inv<false, true>, grid, sm, st, a);
-    return real ? launch(k_dftg_inv<true, false>, grid, sm, st, a) : launch(k_dftg_inv<false, false>, grid, sm, st, a);
+    const int th = t.dft_threads_inv;
+    if (plain)
+      return real ? launch(k_dftg_inv<true, true>, grid, sm, st, a, th) : launch(k_dftg_inv<false, true>, grid, sm, st, a, th);
+    return real ? launch(k_dftg_inv<true, false>, grid, sm, st, a, th) : launch(k_dftg_inv<false, false>, grid, sm, st, a, th);
   }
   const size_t smem = (size_t)(3 * g.n + c.nact * c.Mc) * sizeof(float4);
   if (plain) return real ? launch(k_dftc_inv<true, true>, grid, smem, st, a) : launch(k_dftc_inv<false, true>, grid, smem, st, a);

@@ -626,7 +626,7 @@ cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const 
   a.Mc = out.Mc;
   a.mlo = out.mlo;
   a.T = rec_tables(g);
-  switch (pick_mb(out.B, 16)) {
+  switch (pick_mb(out.B, t.inv_mb)) {
     case 1: return launch_inv_mb<1>(a, t.nact, !P->native64, st);
     case 2: return launch_inv_mb<2>(a, t.nact, !P->native64, st);
     case 4: return launch_inv_mb<4>(a, t.nact, !P->native64, st);

@@ -83,6 +83,9 @@ struct TransformSpec {
   double2* adj_inv = nullptr;   // [L][nact] conj(mult_fwd) * (2 pi/(2L-1)) gscale
   const TcTable* tc = nullptr;  // reduced-precision modes: packed tiles (shared between specs)
   const TabTable* tab = nullptr;  // precompute = 1: float64-accurate tables (shared between specs)
+  // launch shapes chosen by s2w_plan_autotune (defaults otherwise)
+  int dft_threads_fwd = 256, dft_threads_inv = 256;   // threads per block of the DFT kernels
+  int inv_mb = 16;                                     // maps per block of the inverse contraction
 };
 
 struct s2w_plan_impl;

@@ -1,0 +1,118 @@
+"""Runtime around the transforms on the GPU: the autotuner (s2w_plan_autotune) and the batch
+executor (s2w_batch_*: several plans of mixed band-limit and spin replayed as one CUDA graph).
+
+* After autotuning, the chosen shapes are among the candidates and the transforms still match
+  the oracle element by element (1e-11).
+* A mixed batch (band-limits, spins, real and complex maps, batch sizes) run as one graph gives
+  every plan's wavelet coefficients within 1e-11 of the oracle and its round trip within 1e-11.
+* The batching study's configuration (64 complex maps, L in {64, 128, 256, 512} x 16, spin 0 and
+  2 alternating, N = 4, white coefficients) as one graph: the round trip of every map within
+  1e-11, and one L = 64 map of it against the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import harmonic, wavelet
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def rel(a, b):
+    d = np.abs(np.asarray(a) - np.asarray(b)).max()
+    s = np.abs(np.asarray(b)).max()
+    return d / s if s > 0 else d
+
+
+def to_dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def maps_for(L, spin, real, B, cfg, white=False):
+    var = (lambda l: np.ones_like(l)) if white else synth.power_law
+    flm = [synth.flm_random(L, synth.rng_for(cfg, b), spin=spin, reality=real, variance=var) for b in range(B)]
+    f = np.stack([harmonic.sht_inverse(x, L, spin) for x in flm])
+    return f.real.copy() if real else f
+
+
+def check_against_oracle(plan, f, wav, L, N, lam, J0, spin, real, maps=None):
+    w = wav.cpu().numpy()
+    for b in (range(plan.batch) if maps is None else maps):
+        W_ref, _ = wavelet.analysis(f[b], L, N, lam, J0, spin, real)
+        for s in range(plan.nscales):
+            got = w[b, plan.wav_offsets[s]:plan.wav_offsets[s + 1]].reshape(plan.scale_shape(s))
+            assert rel(got, W_ref[s]) < TOL, (L, spin, b, s)
+
+
+def test_autotune_keeps_results(lib):
+    L, N, lam, J0, B = 24, 4, 2.0, 0, 3
+    plan = lib.Plan(L, N, lam, J0, reality=True, batch=B)
+    plan.autotune()
+    for k in range(plan.nscales + 2):
+        th_f, th_i, mb = plan.launch_shapes(k)
+        assert th_f in (128, 256, 512) and th_i in (128, 256, 512) and mb in (4, 8, 16)
+    f = maps_for(L, 0, True, B, 930)
+    wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
+    plan.forward(to_dev(f), wav, scal)
+    plan.inverse(wav, scal, f2)
+    plan.check()
+    check_against_oracle(plan, f, wav, L, N, lam, J0, 0, True)
+    assert rel(f2.cpu().numpy(), f) < TOL
+
+
+def test_batch_mixed_plans(lib):
+    specs = [(16, 3, 0, False, 2), (24, 3, 2, False, 1), (16, 2, 0, True, 3), (9, 4, 1, False, 2)]
+    plans, fs, fd, wavs, scals, outs = [], [], [], [], [], []
+    for (L, N, spin, real, B) in specs:
+        p = lib.Plan(L, N, 2.0, 0, spin=spin, reality=real, batch=B)
+        f = maps_for(L, spin, real, B, 931 + L + spin)
+        plans.append(p)
+        fs.append(f)
+        fd.append(to_dev(f))
+        wavs.append(p.empty_wav())
+        scals.append(p.empty_scal())
+        outs.append(p.empty_map())
+    batch = lib.Batch(plans, fd, wavs, scals, outs, what=2)
+    for _ in range(2):
+        batch.launch()
+    for p in plans:
+        p.check()
+    for (L, N, spin, real, B), p, f, w, o in zip(specs, plans, fs, wavs, outs):
+        check_against_oracle(p, f, w, L, N, 2.0, 0, spin, real)
+        assert rel(o.cpu().numpy(), f) < TOL
+    batch.close()
+
+
+def test_batching_study_config(lib):
+    """64 complex maps, L in {64, 128, 256, 512} (16 each, spin 0 and 2 alternating), N = 4."""
+    import torch
+    plans, fd, wavs, scals, outs, f64 = [], [], [], [], [], None
+    for L in (64, 128, 256, 512):
+        for spin in (0, 2):
+            p = lib.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8)
+            flm = np.stack([synth.flm_random(L, synth.rng_for(3, 16 * L + 2 * b + spin // 2), spin=spin,
+                                             variance=lambda l: np.ones_like(l)) for b in range(8)])
+            x = p.empty_map()
+            p.sht_inverse(to_dev(flm), x)   # timing-free input synthesis (band-limited maps)
+            plans.append(p)
+            fd.append(x)
+            wavs.append(p.empty_wav())
+            scals.append(p.empty_scal())
+            outs.append(p.empty_map())
+            if L == 64 and spin == 2:
+                f64 = harmonic.sht_inverse(flm[0], L, spin)
+    batch = lib.Batch(plans, fd, wavs, scals, outs, what=2)
+    batch.launch()
+    for p in plans:
+        p.check()
+    for x, o in zip(fd, outs):
+        assert float((o - x).abs().max() / x.abs().max()) < TOL
+    # one map of the batch against the oracle (L = 64, spin 2, map 0)
+    p, w = plans[1], wavs[1].cpu().numpy()
+    W_ref, _ = wavelet.analysis(f64, 64, 4, 2.0, 0, 2, False)
+    for s in range(p.nscales):
+        got = w[0, p.wav_offsets[s]:p.wav_offsets[s + 1]].reshape(p.scale_shape(s))
+        assert rel(got, W_ref[s]) < TOL, s
+    batch.close()
