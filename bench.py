@@ -208,6 +208,58 @@ def run_ball(torch, s2w, stream, flush, steps, precision):
     return out
 
 
+# Batching study: 64 complex maps, L in {64, 128, 256, 512} x 16 (spin 0 and 2 alternating),
+# N = 4, lambda = 2, white coefficients; 8 plans of 8 maps.
+def run_batching(torch, s2w, stream, flush, steps, autotune):
+    import numpy as np
+    import synth
+    plans, fd, wavs, scals, outs = [], [], [], [], []
+    for L in (64, 128, 256, 512):
+        for spin in (0, 2):
+            p = s2w.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8)
+            if autotune:
+                p.autotune()
+            flm = np.stack([synth.flm_random(L, synth.rng_for(3, 16 * L + 2 * b + spin // 2), spin=spin,
+                                             variance=lambda l: np.ones_like(l)) for b in range(8)])
+            x = p.empty_map()
+            p.sht_inverse(torch.from_numpy(flm).cuda(), x)
+            plans.append(p)
+            fd.append(x)
+            wavs.append(p.empty_wav())
+            scals.append(p.empty_scal())
+            outs.append(p.empty_map())
+
+    def sequential():
+        for p, x, w, sc, o in zip(plans, fd, wavs, scals, outs):
+            p.forward(x, w, sc)
+            p.inverse(w, sc, o)
+
+    batch = s2w.Batch(plans, fd, wavs, scals, outs, what=2)
+    res = {}
+    for name, fn in (("sequential_one_stream", sequential), ("graph", batch.launch)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        res[name] = {"value": 64 * len(ms) / (sum(ms) * 1e-3), "ms_per_step": sum(ms) / len(ms)}
+    for p in plans:
+        p.check()
+    err = max(float((o - x).abs().max() / x.abs().max()) for x, o in zip(fd, outs))
+    batch.close()
+    for p in plans:
+        p.close()
+    return {"workload": "64 complex maps, L in {64,128,256,512} x 16, spin 0/2 alternating, N=4, lambda=2, "
+                        "white a_lm; 8 plans x 8 maps, precision fp64 (on-the-fly recursion)",
+            "unit": "transforms/s (fwd+inv)", "autotuned": bool(autotune), "max_rel_err": err, **res}
+
+
 def run_differentiation(torch, s2w, stream, flush, steps):
     """Loss-gradient evaluations per second (analysis + adjoint, device time, L2 flushed) and
     a central finite-difference check of one directional derivative."""
@@ -285,6 +337,8 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     plan = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[args.precision],
                     precompute=PRECOMPUTE.get(args.precision, 0))
+    if not args.no_autotune:
+        plan.autotune()
     flm, f = make_inputs(torch, plan, rank)
     wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -367,6 +421,9 @@ def run_ours(args, world, rank, local):
     diff = None
     if not args.no_diff:
         diff = run_differentiation(torch, s2w, stream, flush, max(3, args.steps // 2))
+    batching = None
+    if not args.no_batching:
+        batching = run_batching(torch, s2w, stream, flush, max(3, args.steps // 2), not args.no_autotune)
     ball = None
     if not args.no_ball:
         ball = run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)
@@ -393,6 +450,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded band-limited maps, the paper's random-signal protocol)",
         "config": {"workload": WORKLOAD, "L": L, "N": N, "lambda": LAM, "J0": J0, "spin": 0,
                    "maps_per_gpu": B, "precision": args.precision, "precompute": PRECOMPUTE.get(args.precision, 0),
+                   "launch_shapes": None if args.no_autotune else [plan.launch_shapes(k) for k in range(plan.nscales + 2)],
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MB write)"},
         "precision_detail": PRECISION_DOC[args.precision],
@@ -400,6 +458,7 @@ def run_ours(args, world, rank, local):
         "other_modes": other,
         "differentiation": diff,
         "ball": ball,
+        "batching": batching,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
@@ -459,6 +518,8 @@ def main():
     ap.add_argument("--precision", default="fp64_table", choices=sorted(PRECISIONS))
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-study timing")
     ap.add_argument("--no-ball", action="store_true", help="skip the ball-study timing")
+    ap.add_argument("--no-batching", action="store_true", help="skip the batching-study timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
