@@ -361,7 +361,9 @@ def run_ours(args, world, rank, local):
     if sampler:
         sampler.start()
         time.sleep(0.3)
+    torch.cuda.nvtx.range_push("timed")   # lets a profiler select the timed launches
     step_ms = time_steps(torch, plan, f, wav, scal, f2, flush, stream, args.steps)
+    torch.cuda.nvtx.range_pop()
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None

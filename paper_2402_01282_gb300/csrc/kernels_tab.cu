@@ -3,7 +3,7 @@
 // plan from the same float64 recursion as the on-the-fly kernels and stored as float pairs
 // (hi + lo, ~48 bits); the contractions are compensated-float32 GEMMs (comp32.cuh).
 //
-//  * k_tab_build   T_inv[(m,n)][l - l0a][beta] = d^l_mn(beta_b): one thread per beta runs the
+//  * k_tab_build   T_inv[(m,n)][l - l0a][beta] (l0a = max(|m|,|n|) rounded down to a multiple of 8) = d^l_mn(beta_b): one thread per beta runs the
 //                  recursion over l (wigner_rec.cuh), zero outside l0 <= l < L, beta < L.
 //  * k_tab_fold    T_fwd[(m,n)][beta'][l - l0a] = sum_beta M^{par(m+n)}[beta][beta'] d^l_mn(beta):
 //                  the colatitude quadrature of the forward transforms folded into the table
@@ -47,7 +47,7 @@ __global__ void k_tab_build(TabBuildArgs a) {
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
   if (kp == 0) return;
   const int m = a.mlo + mi, nn = a.nvals[ni], L = a.L;
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~31;
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
   float2* out = a.inv + a.off_inv[idx] + b;
   for (int ll = 0; ll < l0 - l0a; ++ll) out[(int64_t)ll * a.Lp] = make_float2(0.f, 0.f);
   for (int ll = L - l0a; ll < kp; ++ll) out[(int64_t)ll * a.Lp] = make_float2(0.f, 0.f);
@@ -154,6 +154,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
                "l"(gmem)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -168,12 +173,14 @@ __device__ __forceinline__ float4 split_bits(double2 v) {
 
 // Copies the 32 x 64 table tile (k rows k0.., row columns row0..) into As: 1024 granules of
 // 16 bytes, 8 per thread.  `ld` = row stride of the table in float2.
+// Columns row0 + 2c >= rows_valid are zero-filled without a read (source size 0).
 __device__ __forceinline__ void issue_tile(float4 (*As)[kRows / 2], const float2* T, int64_t ld, int k0, int row0,
-                                           int tid) {
+                                           int tid, int rows_valid) {
 #pragma unroll
   for (int q = 0; q < (kK * kRows / 2) / kThreads; ++q) {
     const int gi = tid + q * kThreads, k = gi / (kRows / 2), c = gi - k * (kRows / 2);
-    cp_async16(&As[k][c], T + (int64_t)(k0 + k) * ld + row0 + 2 * c);
+    const bool ok = row0 + 2 * c < rows_valid;
+    cp_async16_zfill(&As[k][c], ok ? T + (int64_t)(k0 + k) * ld + row0 + 2 * c : T, ok ? 16 : 0);
   }
   cp_async_commit();
 }
@@ -206,10 +213,11 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
   if (row0 >= L) return;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~31;
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
   const int nch = kp == 0 ? 0 : (L - l0a + kK - 1) / kK;
   const float2* T = a.tab + a.off[idx];
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  const bool warp_live = row0 + 16 * (tid >> 5) < L;   // a warp owns 16 rows beta
   auto load_b = [&](int c, int map0, double2 (&f)[kBPer]) {
 #pragma unroll
     for (int q = 0; q < kBPer; ++q) {
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
       for (int c = 0; c < 4; ++c) acc[r][c] = Acc{0.f, 0.f};
     double2 f[kBPer];
     if (nch > 0) {
-      issue_tile(As[0], T, a.Lp, 0, row0, tid);
+      issue_tile(As[0], T, a.Lp, 0, row0, tid, a.Lp);
       load_b(0, map0, f);
     }
     for (int c = 0; c < nch; ++c) {
@@ -242,15 +250,18 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
         Bs[buf][i / kMaps][i % kMaps] = split_bits(f[q]);
       }
       if (c + 1 < nch) {
-        issue_tile(As[buf ^ 1], T, a.Lp, (c + 1) * kK, row0, tid);
+        issue_tile(As[buf ^ 1], T, a.Lp, (c + 1) * kK, row0, tid, a.Lp);
         load_b(c + 1, map0, f);
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
       }
       __syncthreads();
+      if (warp_live) {
+        const int kend = min(kK, L - l0a - c * kK);   // the last chunk stops at l = L - 1
 #pragma unroll 4
-      for (int k = 0; k < kK; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
+        for (int k = 0; k < kend; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
+      }
       __syncthreads();
     }
 #pragma unroll
@@ -293,10 +304,13 @@ __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
   const int row0 = rt * kRows;
   if (row0 >= kp) return;
   const int L = a.L, m = a.mlo + mi, nn = a.nvals[ni];
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~31;
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
   const int nch = (L + kK - 1) / kK;
   const float2* T = a.tab + a.off[idx];
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  // a warp owns 16 rows l; it skips the products when none of them lies in [l0, L)
+  const int wl0 = l0a + row0 + 16 * (tid >> 5);
+  const bool warp_live = wl0 + 16 > l0 && wl0 < L;
   auto load_b = [&](int c, int map0, double2 (&f)[kBPer]) {
 #pragma unroll
     for (int q = 0; q < kBPer; ++q) {
@@ -313,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = Acc{0.f, 0.f};
     double2 f[kBPer];
-    issue_tile(As[0], T, kp, 0, row0, tid);
+    issue_tile(As[0], T, kp, 0, row0, tid, kp);
     load_b(0, map0, f);
     for (int c = 0; c < nch; ++c) {
       const int buf = c & 1;
@@ -323,15 +337,18 @@ __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
         Bs[buf][i / kMaps][i % kMaps] = split_bits(f[q]);
       }
       if (c + 1 < nch) {
-        issue_tile(As[buf ^ 1], T, kp, (c + 1) * kK, row0, tid);
+        issue_tile(As[buf ^ 1], T, kp, (c + 1) * kK, row0, tid, kp);
         load_b(c + 1, map0, f);
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
       }
       __syncthreads();
+      if (warp_live) {
+        const int kend = min(kK, L - c * kK);
 #pragma unroll 4
-      for (int k = 0; k < kK; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
+        for (int k = 0; k < kend; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
+      }
       __syncthreads();
     }
 #pragma unroll
@@ -453,7 +470,7 @@ cudaError_t launch_tab_forward(const GridTables& g, const TransformSpec& t, Colu
   a.kp = tab.kp;
   a.Lk = tab.Lk;
   a.tab = tab.fwd;
-  dim3 grid(tab.kpmax / kRows, in.Mc, t.nact);
+  dim3 grid((tab.kpmax + kRows - 1) / kRows, in.Mc, t.nact);
   k_tab_fwd<<<grid, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -379,7 +379,7 @@ s2w_status build_tab_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
         oi[idx] = ri;
         of[idx] = rf;
         if (l0 >= L) continue;
-        const int l0a = l0 & ~31, k = ((L - l0a + 63) / 64) * 64;
+        const int l0a = l0 & ~7, k = ((L - l0a + 31) / 32) * 32;
         kp[idx] = k;
         ri += (int64_t)k * tab->Lp;
         rf += (int64_t)tab->Lk * k;

@@ -47,7 +47,7 @@ struct TcTable {
 
 // Precomputed Wigner-d tables of one transform for the float64-accurate table contractions
 // (kernels_tab.cu), float pairs.  Tile (m, n) covers l = l0a .. l0a + kp - 1 with
-// l0a = max(|m|,|n|) rounded down to a multiple of 32 and kp a multiple of 64.
+// l0a = max(|m|,|n|) rounded down to a multiple of 8 and kp a multiple of 32.
 struct TabTable {
   int Lp = 0;                  // beta rows of the inverse tiles (L rounded up to 64)
   int Lk = 0;                  // beta' rows of the forward tiles (L rounded up to 32)
