@@ -159,8 +159,8 @@ PRECISION_DOC = {
                   "compensated-float32 table contractions and DFTs",
     "fp32_split": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, fp16 hi/lo operands "
                   "(3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
-    "bf16": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, bf16 tables and bf16-pair "
-            "data (2 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
+    "bf16": "reduced: split-bf16, tcgen05 contractions on precomputed Wigner-d tiles, bf16 hi/lo tables "
+            "and data (3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
 }
 # Differentiation study: gradient of sum_j mean |W^j|^2 w.r.t. the pixels of 8 real maps at
 # L = 512, N = 4, lambda = 2, J0 = 3 (analysis + its hand-written adjoint per step).

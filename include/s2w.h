@@ -62,8 +62,8 @@ typedef enum {
  * S2W_FP32_SPLIT  wavelet-scale l-contractions on the tensor cores (tcgen05) against
  *                  precomputed Wigner-d tables stored as fp16 hi + lo pairs, data as fp16
  *                  pairs, float32 accumulation (1e-5 target); plain float32 DFTs there.
- * S2W_BF16         the same with single bf16 tables and bf16-pair data (1e-3 target on the
- *                  round trip; a single wavelet map carries ~2e-3 of table rounding).
+ * S2W_BF16         split-bf16: the same with bf16 hi + lo pairs for the tables and the data
+ *                  (three MMAs per K step, float32 accumulation; 1e-3 target).
  *                  Both reduced modes keep the spin SHT Y, Y^-1 float64-accurate and
  *                  support L <= 256 (S2W_EUNSUPPORTED above). */
 typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3 } s2w_precision;

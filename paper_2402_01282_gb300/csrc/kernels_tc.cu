@@ -3,11 +3,10 @@
 // against the harmonic coefficients (inverse) or the colatitude-weighted columns (forward),
 // with float32 accumulation in TMEM.
 //
-// Two precisions.  "split": every operand is an fp16 pair hi + lo (scaled by a power of two
-// into the fp16 range) and each K step issues three MMAs (hi*hi + hi*lo + lo*hi, ~2^-22 per
-// product).  "bf16": the Wigner-d tables (the bulk of the memory traffic) are single bf16
-// values; the data operands and the quadrature matrices stay bf16 pairs, so each K step issues
-// two MMAs against the tables (d*hi + d*lo) and three in the quadrature.
+// Two precisions, both with every operand a pair hi + lo and three MMAs per K step
+// (hi*hi + hi*lo + lo*hi, the lo*lo term dropped): "split" in fp16 (scaled by a power of two
+// into the fp16 range; 22 bits per pair, ~2^-22 per product) and "bf16" in bf16 (16 bits per
+// pair, ~2^-17 per product; no range scaling needed, the tables are scaled the same way).
 //
 // Tiles are stored in the non-swizzled core-matrix layout (see tc_sm100.cuh) so a tile is
 // one contiguous chunk that a single bulk asynchronous copy (TMA engine) brings to shared
@@ -101,8 +100,8 @@ __global__ void k_tc_build(BuildArgs a) {
         --q;
       }
     }
-    put16<SPLIT, SPLIT>(a.inv_hi + off, a.inv_lo + off, inv_index(beta, ll, kl), x);
-    put16<SPLIT, SPLIT>(a.fwd_hi + off, a.fwd_lo + off, fwd_index(beta, ll, a.Lb), x);
+    put16<SPLIT, true>(a.inv_hi + off, a.inv_lo + off, inv_index(beta, ll, kl), x);
+    put16<SPLIT, true>(a.fwd_hi + off, a.fwd_lo + off, fwd_index(beta, ll, a.Lb), x);
   }
 }
 
@@ -213,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_inv(TcInvArgs a) {
   const int l0 = max(abs(m), abs(n)), l0a = l0 & ~15;
   uint16_t* Ah = reinterpret_cast<uint16_t*>(smem);
   uint16_t* Al = Ah + 128 * a.klmax;
-  uint16_t* Bh = Al + (SPLIT ? 128 * a.klmax : 0);
+  uint16_t* Bh = Al + 128 * a.klmax;
   uint16_t* Bl = Bh + kTcN * a.klmax;   // data operand is a pair in both modes
   if (tid == 0) {
     tc::mbar_init(&bar_ld, 1);
@@ -226,10 +225,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_inv(TcInvArgs a) {
   const uint32_t tmem = tbase;
   if (tid == 0) {
     const uint32_t bytes = 128u * kl * 2u;
-    tc::mbar_expect_tx(&bar_ld, SPLIT ? 2 * bytes : bytes);
+    tc::mbar_expect_tx(&bar_ld, 2 * bytes);
     const int64_t src = a.off[tile] + (int64_t)t * 128 * kl;
     tc::bulk_g2s(Ah, a.A_hi + src, bytes, &bar_ld);
-    if (SPLIT) tc::bulk_g2s(Al, a.A_lo + src, bytes, &bar_ld);
+    tc::bulk_g2s(Al, a.A_lo + src, bytes, &bar_ld);
   }
   const uint32_t idesc = tc::make_idesc(128, kTcN, SPLIT ? 0 : 1, 0, 0);
   bool ok = true;
@@ -265,7 +264,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_inv(TcInvArgs a) {
       }
       if (ok) {
         tc::fence_after_sync();
-        issue_mmas(tmem, Ah, Al, Bh, Bl, kl, idesc, SPLIT);
+        issue_mmas(tmem, Ah, Al, Bh, Bl, kl, idesc, true);
         tc::mma_commit(&bar_mma);
       }
     }
@@ -422,7 +421,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_fwd(TcFwdArgs a) {
     __syncthreads();
     for (int u = 0; u < nlt; ++u) {
       const int64_t e = a.off[tile] + (int64_t)u * 128 * Lb;
-      run_tile(a.E_hi + e, SPLIT ? a.E_lo + e : nullptr, B2h, B2l, 32u * (nbt + u), SPLIT);
+      run_tile(a.E_hi + e, a.E_lo + e, B2h, B2l, 32u * (nbt + u), true);
     }
     ok = __syncthreads_and(ok);
     if (!ok) break;
@@ -456,7 +455,8 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_fwd(TcFwdArgs a) {
 }  // namespace
 
 size_t tc_inv_smem(bool split, int klmax) {
-  return (size_t)((split ? 2 : 1) * 128 + 2 * kTcN) * klmax * sizeof(uint16_t);
+  (void)split;
+  return (size_t)(2 * 128 + 2 * kTcN) * klmax * sizeof(uint16_t);
 }
 size_t tc_fwd_smem(bool split, int Lb) {
   (void)split;

@@ -336,10 +336,8 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     S2W_TRY(upload(P, kl, &tab->kl, st, err));
     S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_hi, err));
     S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_hi, err));
-    if (split) {
-      S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_lo, err));
-      S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_lo, err));
-    }
+    S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_lo, err));   // tables are pairs in both modes
+    S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_lo, err));
     if (launch_tc_build(g, *t, *tab, Mc, mlo, split, st) != cudaSuccess) {
       err = "Wigner-d table kernel failed to launch";
       return S2W_ECUDA;

@@ -1,13 +1,9 @@
-"""Reduced-precision modes (tensor-core contractions against precomputed Wigner-d tiles),
+"""Reduced-precision modes (tensor-core contractions against precomputed Wigner-d tables),
 compared with the float64 oracle as max|x - x_ref| / max|x_ref| per output.
 
-S2W_FP32_SPLIT (fp16 hi/lo operands, float32 accumulation) is held to 1e-5 everywhere.
-S2W_BF16 keeps the Wigner-d tables as single bf16 values (relative rounding up to 2^-9 per
-entry) and the data as bf16 pairs.  It is held to the 1e-3 target on the round trip of the
-L = 256 benchmark workload (the paper's accuracy protocol); a wavelet map itself carries the
-table rounding, so its bound is 2^-8 (measured ~2e-3: the 1e-3 per-map target is not met by
-single-bf16 tables).  On the small operator tests, where an output is a sum of few products,
-the bound is 2^-7."""
+S2W_FP32_SPLIT (fp16 hi/lo tables and data, float32 accumulation) is held to its 1e-5
+target everywhere, S2W_BF16 (split-bf16: bf16 hi/lo tables and data) to its 1e-3 target:
+every wavelet map, the round trip and the small operator tests."""
 import numpy as np
 import pytest
 
@@ -16,8 +12,8 @@ from oracle import harmonic, wavelet
 
 pytestmark = pytest.mark.gpu
 SPLIT, BF16 = 1, 2
-TOLS = {SPLIT: 1e-5, BF16: 2.0 ** -7}      # small operator tests
-TOLS_MAPS = {SPLIT: 1e-5, BF16: 2.0 ** -8}  # L = 256 workload, every wavelet map
+TOLS = {SPLIT: 1e-5, BF16: 1e-3}          # small operator tests
+TOLS_MAPS = {SPLIT: 1e-5, BF16: 1e-3}     # L = 256 workload, every wavelet map
 TOLS_ROUND_TRIP = {SPLIT: 1e-5, BF16: 1e-3}
 
 
