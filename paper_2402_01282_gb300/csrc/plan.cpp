@@ -189,14 +189,6 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
   S2W_TRY(upload(P, sm, &g.spow_m, st, err));
   S2W_TRY(upload(P, se, &g.spow_e, st, err));
   S2W_TRY(upload(P, sc, &g.sqrtC, st, err));
-  g.Lb = ((L + 127) / 128) * 128;
-  {
-    double mx = 0.0;
-    for (double v : MT) mx = std::max(mx, std::fabs(v));
-    int e = 0;
-    std::frexp(mx, &e);
-    g.qscale = std::ldexp(1.0, 14 - e);   // packed quadrature entries below 2^14
-  }
   std::vector<float2> MT2(MT.size()), MR2(MT.size());
   std::vector<double> MR(MT.size());
   for (int par = 0; par < 2; ++par)
@@ -292,58 +284,112 @@ s2w_status alloc_dev(s2w_plan* P, size_t n, T** d, std::string& err) {
 // quadrature matrices.  The spin SHT and the scaling transform stay on the float64-accurate
 // path: Y f sets the accuracy of every small high-l coefficient the top scales see, and with a
 // steep spectrum a 16-bit quantisation relative to f_00 would swamp them.
+s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStream_t st, std::string& err);
+
+// Tensor-core tables of the reduced modes for every wavelet scale (specs with the same (L, n
+// values) share one), packed from temporary float-pair tables (make_tab: float64 recursion and
+// the folded quadrature) that are freed once packed; plus the operand workspace.
 s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
-  const bool split = P->p.precision == S2W_FP32_SPLIT;
-  for (GridTables& g : P->grids) {
-    const size_t n = (size_t)2 * g.Lb * g.Lb;
-    S2W_TRY(alloc_dev(P, n, &g.Q_hi, err));
-    S2W_TRY(alloc_dev(P, n, &g.Q_lo, err));   // quadrature entries are pairs in both modes
-    if (launch_tc_build_quad(g, split, st) != cudaSuccess) {
-      err = "quadrature packing kernel failed to launch";
-      return S2W_ECUDA;
-    }
-  }
+  const bool fp16 = P->p.precision == S2W_FP32_SPLIT;
   std::map<std::pair<int, std::vector<int>>, TcTable*> cache;
-  std::vector<TransformSpec*> specs;
-  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
-  for (TransformSpec* t : specs) {
+  int64_t op_max = 0, sc_max = 0;
+  const int nq = (P->p.batch + 15) / 16;
+  for (TransformSpec& tr : P->wav_t) {
+    TransformSpec* t = &tr;
     auto key = std::make_pair(t->L, t->nvals_h);
     auto it = cache.find(key);
     if (it != cache.end()) {
       t->tc = it->second;
       continue;
     }
-    const GridTables& g = P->grids[t->grid];
     const int L = t->L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
     TcTable* tab = new TcTable();
     P->tc_tables.push_back(tab);
-    tab->Lb = g.Lb;
-    std::vector<int64_t> off((size_t)Mc * t->nact, 0);
-    std::vector<int> kl((size_t)Mc * t->nact, 0);
-    int64_t run = 0;
+    tab->Lb = ((L + 127) / 128) * 128;
+    tab->Lk = ((L + 63) / 64) * 64;
+    std::vector<int64_t> oi((size_t)Mc * t->nact, 0), of((size_t)Mc * t->nact, 0);
+    std::vector<int> ki((size_t)Mc * t->nact, 0), kf((size_t)Mc * t->nact, 0);
+    int64_t ri = 0, rf = 0;
     for (int mi = 0; mi < Mc; ++mi)
       for (int ni = 0; ni < t->nact; ++ni) {
+        const size_t idx = (size_t)mi * t->nact + ni;
         const int l0 = std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni]));
+        oi[idx] = ri;
+        of[idx] = rf;
         if (l0 >= L) continue;
-        const int l0a = l0 & ~15, k = ((L - l0a + 127) / 128) * 128;
-        off[(size_t)mi * t->nact + ni] = run;
-        kl[(size_t)mi * t->nact + ni] = k;
-        run += (int64_t)g.Lb * k;
-        tab->klmax = std::max(tab->klmax, k);
+        const int l0a = l0 & ~7;
+        ki[idx] = ((L - l0a + 63) / 64) * 64;
+        kf[idx] = ((L - l0a + 127) / 128) * 128;
+        ri += (int64_t)tab->Lb * ki[idx];
+        rf += (int64_t)kf[idx] * tab->Lk;
+        tab->klf_max = std::max(tab->klf_max, kf[idx]);
       }
-    tab->elems = run;
-    S2W_TRY(upload(P, off, &tab->off, st, err));
-    S2W_TRY(upload(P, kl, &tab->kl, st, err));
-    S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_hi, err));
-    S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_hi, err));
-    S2W_TRY(alloc_dev(P, (size_t)run, &tab->inv_lo, err));   // tables are pairs in both modes
-    S2W_TRY(alloc_dev(P, (size_t)run, &tab->fwd_lo, err));
-    if (launch_tc_build(g, *t, *tab, Mc, mlo, split, st) != cudaSuccess) {
-      err = "Wigner-d table kernel failed to launch";
+    tab->op_i = 32 * (ri / tab->Lb);
+    tab->op_f = 32 * (int64_t)tab->Lk * Mc * t->nact;
+    op_max = std::max(op_max, std::max(tab->op_i, tab->op_f));
+    sc_max = std::max(sc_max, (int64_t)Mc * t->nact);
+    S2W_TRY(upload(P, oi, &tab->off_i, st, err));
+    S2W_TRY(upload(P, of, &tab->off_f, st, err));
+    S2W_TRY(upload(P, ki, &tab->kli, st, err));
+    S2W_TRY(upload(P, kf, &tab->klf, st, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ri, 1), &tab->inv_hi, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ri, 1), &tab->inv_lo, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(rf, 1), &tab->fwd_hi, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(rf, 1), &tab->fwd_lo, err));
+    // temporary float-pair tables: their allocations are the ones added to P->owned here
+    const size_t mark = P->owned.size();
+    TabTable tmp;
+    S2W_TRY(make_tab(P, *t, &tmp, st, err));
+    if (launch_tc_pack(*t, *tab, tmp, Mc, mlo, fp16, st) != cudaSuccess) {
+      err = "tensor-core table packing failed to launch";
       return S2W_ECUDA;
     }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      err = "tensor-core table build failed";
+      return S2W_ECUDA;
+    }
+    for (size_t i = mark; i < P->owned.size(); ++i) cudaFree(P->owned[i]);
+    P->owned.resize(mark);
     cache[key] = tab;
     t->tc = tab;
+  }
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tc_b_hi, err));
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tc_b_lo, err));
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * sc_max, 1), &P->tc_scale, err));
+  return S2W_OK;
+}
+
+// Float-pair tables of one transform (offsets, allocation, the build and fold kernels).
+s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStream_t st, std::string& err) {
+  const GridTables& g = P->grids[t.grid];
+  const int L = t.L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
+  tab->Lp = ((L + 63) / 64) * 64;
+  tab->Lk = ((L + 31) / 32) * 32;
+  std::vector<int64_t> oi((size_t)Mc * t.nact, 0), of((size_t)Mc * t.nact, 0);
+  std::vector<int> kp((size_t)Mc * t.nact, 0);
+  int64_t ri = 0, rf = 0;
+  for (int mi = 0; mi < Mc; ++mi)
+    for (int ni = 0; ni < t.nact; ++ni) {
+      const size_t idx = (size_t)mi * t.nact + ni;
+      const int l0 = std::max(std::abs(mlo + mi), std::abs(t.nvals_h[ni]));
+      oi[idx] = ri;
+      of[idx] = rf;
+      if (l0 >= L) continue;
+      const int l0a = l0 & ~7, k = ((L - l0a + 31) / 32) * 32;
+      kp[idx] = k;
+      ri += (int64_t)k * tab->Lp;
+      rf += (int64_t)tab->Lk * k;
+      tab->kpmax = std::max(tab->kpmax, k);
+    }
+  tab->elems = std::max(ri, rf);
+  S2W_TRY(upload(P, oi, &tab->off_inv, st, err));
+  S2W_TRY(upload(P, of, &tab->off_fwd, st, err));
+  S2W_TRY(upload(P, kp, &tab->kp, st, err));
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ri, 1), &tab->inv, err));
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(rf, 1), &tab->fwd, err));
+  if (tab->kpmax > 0 && launch_tab_build(g, t, *tab, Mc, mlo, st) != cudaSuccess) {
+    err = "Wigner-d table kernels failed to launch";
+    return S2W_ECUDA;
   }
   return S2W_OK;
 }
@@ -361,38 +407,9 @@ s2w_status build_tab_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
       t->tab = it->second;
       continue;
     }
-    const GridTables& g = P->grids[t->grid];
-    const int L = t->L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
     TabTable* tab = new TabTable();
     P->tab_tables.push_back(tab);
-    tab->Lp = ((L + 63) / 64) * 64;
-    tab->Lk = ((L + 31) / 32) * 32;
-    std::vector<int64_t> oi((size_t)Mc * t->nact, 0), of((size_t)Mc * t->nact, 0);
-    std::vector<int> kp((size_t)Mc * t->nact, 0);
-    int64_t ri = 0, rf = 0;
-    for (int mi = 0; mi < Mc; ++mi)
-      for (int ni = 0; ni < t->nact; ++ni) {
-        const size_t idx = (size_t)mi * t->nact + ni;
-        const int l0 = std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni]));
-        oi[idx] = ri;
-        of[idx] = rf;
-        if (l0 >= L) continue;
-        const int l0a = l0 & ~7, k = ((L - l0a + 31) / 32) * 32;
-        kp[idx] = k;
-        ri += (int64_t)k * tab->Lp;
-        rf += (int64_t)tab->Lk * k;
-        tab->kpmax = std::max(tab->kpmax, k);
-      }
-    tab->elems = std::max(ri, rf);
-    S2W_TRY(upload(P, oi, &tab->off_inv, st, err));
-    S2W_TRY(upload(P, of, &tab->off_fwd, st, err));
-    S2W_TRY(upload(P, kp, &tab->kp, st, err));
-    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ri, 1), &tab->inv, err));
-    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(rf, 1), &tab->fwd, err));
-    if (tab->kpmax > 0 && launch_tab_build(g, *t, *tab, Mc, mlo, st) != cudaSuccess) {
-      err = "Wigner-d table kernels failed to launch";
-      return S2W_ECUDA;
-    }
+    S2W_TRY(make_tab(P, *t, tab, st, err));
     cache[key] = tab;
     t->tab = tab;
   }

@@ -29,20 +29,21 @@ struct GridTables {
   float2* MR2 = nullptr;       // the same as float pairs
   double2* tw = nullptr;       // [n] exp(+2 pi i e / n)
   float4* tw4 = nullptr;       // [n] the same as float pairs (re_hi, re_lo, im_hi, im_lo)
-  // reduced-precision modes: quadrature matrices packed for the tensor cores
-  int Lb = 0;                  // L rounded up to 128
-  double qscale = 1.0;         // power-of-two scale of the packed quadrature entries
-  uint16_t* Q_hi = nullptr;    // [2][Lb/128][128 x Lb] core-matrix packed (fp16 hi or bf16)
-  uint16_t* Q_lo = nullptr;    // lo parts (the quadrature is a pair in both modes)
 };
 
-// Packed Wigner-d tiles of one transform for the tensor-core contractions (kernels_tc.cu).
+// Packed Wigner-d tables of one transform for the tensor-core contractions (kernels_tc.cu):
+// fp16 or bf16 hi/lo pairs in 128-row x 64-deep core-matrix chunks.  Tile (m, n) starts at
+// l0a = max(|m|,|n|) rounded down to 8.
 struct TcTable {
-  int Lb = 0, klmax = 0;
-  int64_t* off = nullptr;      // device [Mc * nact] element offset of tile (m, n)
-  int* kl = nullptr;           // device [Mc * nact] padded l extent (multiple of 128; 0 if empty)
+  int Lb = 0;                  // beta rows of the inverse tables (L rounded up to 128)
+  int Lk = 0;                  // beta' reduction extent of the forward tables (L rounded up to 64)
+  int klf_max = 0;             // largest forward row extent
+  int64_t* off_i = nullptr;    // device [Mc * nact] element offset of inverse tile (m, n)
+  int64_t* off_f = nullptr;    // forward tile offsets
+  int* kli = nullptr;          // device [Mc * nact] inverse l extent (multiple of 64; 0 if empty)
+  int* klf = nullptr;          // forward l row extent (multiple of 128; 0 if empty)
   uint16_t *inv_hi = nullptr, *inv_lo = nullptr, *fwd_hi = nullptr, *fwd_lo = nullptr;
-  int64_t elems = 0;
+  int64_t op_i = 0, op_f = 0;  // prepared-operand elements per 16-map chunk (inverse, forward)
 };
 
 // Precomputed Wigner-d tables of one transform for the float64-accurate table contractions
@@ -110,6 +111,8 @@ struct s2w_plan {
 
   bool tensor = false;                 // reduced-precision modes (S2W_FP32_SPLIT, S2W_BF16)
   std::vector<s2w::TcTable*> tc_tables;  // owned
+  uint16_t *tc_b_hi = nullptr, *tc_b_lo = nullptr;   // prepared tensor-core operands (hi, lo)
+  float* tc_scale = nullptr;                         // their power-of-two scales
   int cur_batch = 0;                   // > 0: maps per launch for an internal caller (ball transforms)
   bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
   std::vector<s2w::TabTable*> tab_tables;  // owned
@@ -187,15 +190,13 @@ cudaError_t launch_quad_adjoint(const s2w_plan* P, const GridTables& g, const Tr
 cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st);
 
 // Tensor-core reduced-precision path (kernels_tc.cu).
-cudaError_t launch_tc_build(const GridTables& g, const TransformSpec& t, const TcTable& tab, int Mc, int mlo,
-                            bool split, cudaStream_t st);
-cudaError_t launch_tc_build_quad(const GridTables& g, bool split, cudaStream_t st);
+struct TabTable;
+cudaError_t launch_tc_pack(const TransformSpec& t, const TcTable& tab, const TabTable& src, int Mc, int mlo, bool fp16,
+                           cudaStream_t st);
 cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
                               ColumnArgs out, cudaStream_t st);
 cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
                               CoefArgs out, cudaStream_t st);
-size_t tc_inv_smem(bool split, int klmax);
-size_t tc_fwd_smem(bool split, int Lb);
 
 // Float64-accurate table contractions (kernels_tab.cu): build (recursion + folded quadrature)
 // and the two contractions; same contracts as launch_wigner_inverse / launch_wigner_forward.
