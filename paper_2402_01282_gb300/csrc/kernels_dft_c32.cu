@@ -294,16 +294,33 @@ __device__ void stage2_sym(const float4* tmp, float4* AB, const float4* tw, int 
     }
     Acc cr{x0.x, x0.y}, ci{x0.z, x0.w}, sr{0.f, 0.f}, si{0.f, 0.f};
     const int step = (n1 * kk) % n;
-    int e = step;
-    for (int j = 0; j < h2; ++j) {
-      const float4 a = ab[2 * j], b = ab[2 * j + 1];
-      const float4 w = tw[e];
-      racc<PLAIN>(cr, a.x, a.y, w.x, w.y);
-      racc<PLAIN>(ci, a.z, a.w, w.x, w.y);
-      racc<PLAIN>(sr, b.x, b.y, w.z, w.w);
-      racc<PLAIN>(si, b.z, b.w, w.z, w.w);
-      e += step;
-      if (e >= n) e -= n;
+    if (PLAIN) {
+      // float32 arithmetic: the twiddles cos, sin(2 pi j kk/n2) by the rotation recurrence
+      // (error ~j 2^-24, far below the reduced modes' budgets) instead of a table load per j
+      const float4 w1 = tw[step];
+      float wr = w1.x, wi = w1.z;
+      for (int j = 0; j < h2; ++j) {
+        const float4 a = ab[2 * j], b = ab[2 * j + 1];
+        cr.s = fmaf(a.x, wr, cr.s);
+        ci.s = fmaf(a.z, wr, ci.s);
+        sr.s = fmaf(b.x, wi, sr.s);
+        si.s = fmaf(b.z, wi, si.s);
+        const float t = fmaf(wr, w1.x, -wi * w1.z);
+        wi = fmaf(wr, w1.z, wi * w1.x);
+        wr = t;
+      }
+    } else {
+      int e = step;
+      for (int j = 0; j < h2; ++j) {
+        const float4 a = ab[2 * j], b = ab[2 * j + 1];
+        const float4 w = tw[e];
+        racc<PLAIN>(cr, a.x, a.y, w.x, w.y);
+        racc<PLAIN>(ci, a.z, a.w, w.x, w.y);
+        racc<PLAIN>(sr, b.x, b.y, w.z, w.w);
+        racc<PLAIN>(si, b.z, b.w, w.z, w.w);
+        e += step;
+        if (e >= n) e -= n;
+      }
     }
     const float sg = (float)SIGN;
     store(k1 + n1 * kk, comb<PLAIN>(cr, -sg, si), comb<PLAIN>(ci, sg, sr));

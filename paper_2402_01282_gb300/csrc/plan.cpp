@@ -395,11 +395,13 @@ s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStre
 }
 
 // Float64-accurate precomputed tables (precompute = 1) for the SHT, the scaling function and
-// every wavelet scale; specs with the same (L, n values) share one table.
-s2w_status build_tab_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+// (with_wavelets) every wavelet scale; specs with the same (L, n values) share one table.  The
+// reduced modes use them for the SHT and the scaling function, which stay float64-accurate.
+s2w_status build_tab_tables(s2w_plan* P, cudaStream_t st, std::string& err, bool with_wavelets) {
   std::map<std::pair<int, std::vector<int>>, TabTable*> cache;
   std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
-  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+  if (with_wavelets)
+    for (TransformSpec& t : P->wav_t) specs.push_back(&t);
   for (TransformSpec* t : specs) {
     auto key = std::make_pair(t->L, t->nvals_h);
     auto it = cache.find(key);
@@ -530,7 +532,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   }
 
   if (P->tensor) S2W_TRY(build_tc_tables(P, st, err));
-  if (P->precompute) S2W_TRY(build_tab_tables(P, st, err));
+  if (P->precompute || P->tensor) S2W_TRY(build_tab_tables(P, st, err, !P->tensor));
 
   // workspaces
   const int64_t B = p.batch;
