@@ -45,9 +45,10 @@ PEAKS = {
 }
 PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64"]
 # DRAM bytes (read + write) per launch of a kernel, mean over one step's launches, from one ncu
-# capture of the kernel as it is built now (profiles/k_wig_fwd_traffic_L256_N8_B16_fp64.md).
+# capture of the kernel as it is built now (profiles/*_traffic_*.md).
 # An entry is dropped whenever its kernel changes; a missing entry reports null.
-TRAFFIC_BYTES = {("fp64", "wigner_forward"): 368.88e6 / 9 + 0.54e6 / 9}
+TRAFFIC_BYTES = {("fp64", "wigner_forward"): 368.88e6 / 9 + 0.54e6 / 9,   # k_wig_fwd, on-the-fly mode
+                 ("fp64_table", "wigner_forward"): 209.0e6}   # k_tab_fwd (k_tab_fwd_traffic_..._fp64_table.md)
 
 
 def dist_init():
