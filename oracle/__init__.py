@@ -9,13 +9,16 @@ matrix), while this oracle follows the Fourier-space route of McEwen-Wiaux
 sampling: Wigner-d functions expanded as trigonometric polynomials in beta,
 azimuthal and polar integrals done as direct DFT sums, and the colatitude
 integral done exactly by convolving with the Fourier weights of sin(theta) on
-[0, pi].
+[0, pi].  On Driscoll-Healy sampling the colatitude integral is instead the DH
+quadrature (weights from the moment conditions), applied to the same Fourier-space
+Wigner-d functions.
 
 Everything is float64 / complex128, unblocked and unfused, so that each step can
 be read against the paper:
 
 * ``wigner``    Wigner-d functions as trigonometric polynomials (Sec. 2.2, Eq. 47).
-* ``sampling``  McEwen-Wiaux grids on S^2 and SO(3) and the sin-weight integrals.
+* ``sampling``  McEwen-Wiaux grids on S^2 and SO(3) and the sin-weight integrals; the
+                Driscoll-Healy grids and their colatitude weights.
 * ``harmonic``  spin spherical-harmonic transform (Sec. 2.1, Eqs. 2-3) and Wigner
                 transform (Sec. 2.2, Eqs. 4-5).
 * ``filters``   scale-discretised tiling and dictionary (App. A, Eqs. A2-A10).

@@ -10,21 +10,23 @@ its conjugate transpose.  Complex plans are complex-linear, so unit vectors of t
 basis suffice; real plans (spin 0, real maps) give real matrices.  The cost is one transform
 per input sample: tiny band-limits only.
 
-Vectors are flattened in the library's layout: a map as [L][2L-1]; the wavelet side as the
-scales j = J0..J concatenated, each [2N_j-1][L_j][2L_j-1], followed by nothing else; the
-scaling map separately as [L_Phi][2L_Phi-1].
+Vectors are flattened in the library's layout: a map as [R][2L-1]; the wavelet side as the
+scales j = J0..J concatenated, each [2N_j-1][R_j][2L_j-1], followed by nothing else; the
+scaling map separately as [R_Phi][2L_Phi-1].  R is the ring count of the sampling ``samp``
+(L for MW, 2L for DH) at each band-limit.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import filters, wavelet
+from . import filters, sampling, wavelet
 
 
-def _shapes(L: int, N: int, lam: float, J0: int):
-    scales = [(2 * Nj - 1, Lj, 2 * Lj - 1) for (_, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0)]
+def _shapes(L: int, N: int, lam: float, J0: int, samp: str = "mw"):
+    scales = [(2 * Nj - 1, sampling.rings(Lj, samp), 2 * Lj - 1)
+              for (_, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0)]
     LP = filters.scaling_bandlimit(L, lam, J0)
-    return scales, (LP, 2 * LP - 1)
+    return scales, (sampling.rings(LP, samp), 2 * LP - 1)
 
 
 def _flatten(wavs, wphi, real: bool):
@@ -32,8 +34,8 @@ def _flatten(wavs, wphi, real: bool):
     return v.real.copy() if real else v.astype(np.complex128)
 
 
-def _split(v: np.ndarray, L: int, N: int, lam: float, J0: int):
-    scales, sphi = _shapes(L, N, lam, J0)
+def _split(v: np.ndarray, L: int, N: int, lam: float, J0: int, samp: str = "mw"):
+    scales, sphi = _shapes(L, N, lam, J0, samp)
     wavs, o = [], 0
     for s in scales:
         n = int(np.prod(s))
@@ -42,49 +44,52 @@ def _split(v: np.ndarray, L: int, N: int, lam: float, J0: int):
     return wavs, v[o:o + sphi[0] * sphi[1]].reshape(sphi)
 
 
-def analysis_matrix(L: int, N: int, lam: float, J0: int, spin: int = 0, reality: bool = False) -> np.ndarray:
+def analysis_matrix(L: int, N: int, lam: float, J0: int, spin: int = 0, reality: bool = False,
+                    samp: str = "mw") -> np.ndarray:
     """Matrix of f -> (W^j for all j, W^Phi) (Algorithm 1 analysis), columns = unit maps."""
     real = reality and spin == 0
-    n_in = L * (2 * L - 1)
+    R = sampling.rings(L, samp)
+    n_in = R * (2 * L - 1)
     cols = []
     for k in range(n_in):
         e = np.zeros(n_in, dtype=np.float64 if real else np.complex128)
         e[k] = 1.0
-        wavs, wphi = wavelet.analysis(e.reshape(L, 2 * L - 1), L, N, lam, J0, spin, reality=real)
+        wavs, wphi = wavelet.analysis(e.reshape(R, 2 * L - 1), L, N, lam, J0, spin, reality=real, samp=samp)
         cols.append(_flatten(wavs, wphi, real))
     return np.stack(cols, axis=1)
 
 
-def synthesis_matrix(L: int, N: int, lam: float, J0: int, spin: int = 0, reality: bool = False) -> np.ndarray:
+def synthesis_matrix(L: int, N: int, lam: float, J0: int, spin: int = 0, reality: bool = False,
+                     samp: str = "mw") -> np.ndarray:
     """Matrix of (W^j for all j, W^Phi) -> f (Eq. 42), columns = unit coefficient arrays."""
     real = reality and spin == 0
-    scales, sphi = _shapes(L, N, lam, J0)
+    scales, sphi = _shapes(L, N, lam, J0, samp)
     n_in = sum(int(np.prod(s)) for s in scales) + sphi[0] * sphi[1]
     cols = []
     for k in range(n_in):
         e = np.zeros(n_in, dtype=np.float64 if real else np.complex128)
         e[k] = 1.0
-        wavs, wphi = _split(e, L, N, lam, J0)
-        f = wavelet.synthesis(wavs, wphi, L, N, lam, J0, spin, reality=real)
+        wavs, wphi = _split(e, L, N, lam, J0, samp)
+        f = wavelet.synthesis(wavs, wphi, L, N, lam, J0, spin, reality=real, samp=samp)
         f = np.asarray(f)
         cols.append(f.real.ravel().copy() if real else f.ravel().astype(np.complex128))
     return np.stack(cols, axis=1)
 
 
 def analysis_adjoint(gwavs, gphi, L: int, N: int, lam: float, J0: int, spin: int = 0, reality: bool = False,
-                     matrix: np.ndarray | None = None) -> np.ndarray:
-    """A^H (gwavs, gphi) as a [L][2L-1] map; `matrix` may pass a cached analysis_matrix."""
+                     matrix: np.ndarray | None = None, samp: str = "mw") -> np.ndarray:
+    """A^H (gwavs, gphi) as a [R][2L-1] map; `matrix` may pass a cached analysis_matrix."""
     real = reality and spin == 0
-    A = analysis_matrix(L, N, lam, J0, spin, reality) if matrix is None else matrix
+    A = analysis_matrix(L, N, lam, J0, spin, reality, samp) if matrix is None else matrix
     y = _flatten(gwavs, gphi, real)
-    return (A.conj().T @ y).reshape(L, 2 * L - 1)
+    return (A.conj().T @ y).reshape(sampling.rings(L, samp), 2 * L - 1)
 
 
 def synthesis_adjoint(gf, L: int, N: int, lam: float, J0: int, spin: int = 0, reality: bool = False,
-                      matrix: np.ndarray | None = None):
-    """S^H gf as (list of [2N_j-1][L_j][2L_j-1] arrays, [L_Phi][2L_Phi-1] array)."""
+                      matrix: np.ndarray | None = None, samp: str = "mw"):
+    """S^H gf as (list of [2N_j-1][R_j][2L_j-1] arrays, [R_Phi][2L_Phi-1] array)."""
     real = reality and spin == 0
-    S = synthesis_matrix(L, N, lam, J0, spin, reality) if matrix is None else matrix
+    S = synthesis_matrix(L, N, lam, J0, spin, reality, samp) if matrix is None else matrix
     y = np.asarray(gf).ravel()
     y = y.real.copy() if real else y.astype(np.complex128)
-    return _split(S.conj().T @ y, L, N, lam, J0)
+    return _split(S.conj().T @ y, L, N, lam, J0, samp)

@@ -29,7 +29,7 @@ import math
 
 import numpy as np
 
-from . import filters, harmonic, laguerre
+from . import filters, harmonic, laguerre, sampling
 
 
 def radial_bandlimits(P: int, nu: float, J0r: int):
@@ -59,11 +59,11 @@ def _embed(Lsmall: int, Lbig: int):
 
 
 def analysis(f: np.ndarray, L: int, N: int, P: int, lam: float, nu: float, J0: int, J0r: int,
-             tau: float = 1.0, reality: bool = True):
-    """Returns ({(j, j'): W^{jj'}}, W^Phi)."""
-    flmp = laguerre.spherical_laguerre_forward(f, L, P, tau)
+             tau: float = 1.0, reality: bool = True, samp: str = "mw"):
+    """Returns ({(j, j'): W^{jj'}}, W^Phi); angular grids of the sampling ``samp``."""
+    flmp = laguerre.spherical_laguerre_forward(f, L, P, tau, samp=samp)
     phi = scaling_filter(L, P, lam, nu, J0, J0r)
-    wphi = laguerre.spherical_laguerre_inverse(flmp * phi[:, :, None], L, P, tau)
+    wphi = laguerre.spherical_laguerre_inverse(flmp * phi[:, :, None], L, P, tau, samp=samp)
     wavs = {}
     for (j, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0):
         psi = filters.wavelet_filter(L, N, lam, j)
@@ -71,7 +71,8 @@ def analysis(f: np.ndarray, L: int, N: int, P: int, lam: float, nu: float, J0: i
         for (jr, Pj) in radial_bandlimits(P, nu, J0r):
             kap = radial_kappa(P, nu, jr)
             _, _, K = laguerre.quadrature(Pj, tau)
-            out = np.zeros((Pj, 2 * Nj - 1, Lj, 2 * Lj - 1), dtype=np.float64 if reality else np.complex128)
+            out = np.zeros((Pj, 2 * Nj - 1, sampling.rings(Lj, samp), 2 * Lj - 1),
+                           dtype=np.float64 if reality else np.complex128)
             for i in range(Pj):
                 # radial inverse of kappa^{j'}(p) f_lmp at node r_i of the P_j' rule
                 g = sum(K[i, p] * kap[p] * flmp[p] for p in range(Pj))
@@ -79,17 +80,17 @@ def analysis(f: np.ndarray, L: int, N: int, P: int, lam: float, nu: float, J0: i
                 for l in range(Lj):
                     for n in range(-(Nj - 1), Nj):
                         coef[n + Nj - 1, l] = (8 * math.pi ** 2 / (2 * l + 1)) * g[l, sl] * np.conj(psi[l, n + N - 1])
-                w = harmonic.wigner_inverse(coef, Lj, Nj)
+                w = harmonic.wigner_inverse(coef, Lj, Nj, samp)
                 out[i] = w.real if reality else w
             wavs[(j, jr)] = out
     return wavs, (wphi.real.copy() if reality else wphi)
 
 
 def synthesis(wavs, wphi: np.ndarray, L: int, N: int, P: int, lam: float, nu: float, J0: int, J0r: int,
-              tau: float = 1.0, reality: bool = True) -> np.ndarray:
+              tau: float = 1.0, reality: bool = True, samp: str = "mw") -> np.ndarray:
     """Inverse of ``analysis``."""
     phi = scaling_filter(L, P, lam, nu, J0, J0r)
-    flmp = laguerre.spherical_laguerre_forward(wphi, L, P, tau) * phi[:, :, None]
+    flmp = laguerre.spherical_laguerre_forward(wphi, L, P, tau, samp=samp) * phi[:, :, None]
     for (j, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0):
         psi = filters.wavelet_filter(L, N, lam, j)
         sl = _embed(Lj, L)
@@ -98,12 +99,12 @@ def synthesis(wavs, wphi: np.ndarray, L: int, N: int, P: int, lam: float, nu: fl
             _, om, K = laguerre.quadrature(Pj, tau)
             W = wavs[(j, jr)]
             for i in range(Pj):
-                coef = harmonic.wigner_forward(W[i], Lj, Nj)
+                coef = harmonic.wigner_forward(W[i], Lj, Nj, samp)
                 acc = np.zeros((L, 2 * L - 1), dtype=np.complex128)
                 for l in range(Lj):
                     for n in range(-(Nj - 1), Nj):
                         acc[l, sl] += coef[n + Nj - 1, l] * psi[l, n + N - 1]
                 for p in range(Pj):
                     flmp[p] += kap[p] * om[i] * K[i, p] * acc
-    f = laguerre.spherical_laguerre_inverse(flmp, L, P, tau)
+    f = laguerre.spherical_laguerre_inverse(flmp, L, P, tau, samp=samp)
     return f.real.copy() if reality else f

@@ -1,4 +1,4 @@
-"""Spin spherical-harmonic and Wigner transforms on MW sampling (oracle; test infrastructure only).
+"""Spin spherical-harmonic and Wigner transforms on MW and DH sampling (oracle; test infrastructure only).
 
 Definitions followed
 --------------------
@@ -21,6 +21,14 @@ column G(theta) against d^l_mn(theta) sin(theta) is done exactly by
       with the closed-form weights w of ``sampling.sin_weight``,
   (4) contracting with the Fourier coefficients of d^l_mn (``wigner.fourier_coeffs``).
 All DFTs are direct O(n^2) sums written as matrix products.
+
+Driscoll-Healy sampling (``samp="dh"``; the grid and weights of ``sampling``): the
+inverse transforms evaluate the same Fourier series at the 2L DH rings, and the forward
+transforms replace steps (1)-(3) by
+  I(k) = sum_t w_t G(theta_t) exp(i k theta_t),
+so that step (4), which is shared, yields sum_t w_t G(theta_t) d^l_mn(theta_t): the DH
+quadrature of the colatitude integral, exact whenever G d^l_mn is a cosine series of
+degree <= 2L-1 (every band-limited column).
 """
 from __future__ import annotations
 
@@ -53,8 +61,20 @@ def _colatitude_integrals(G: np.ndarray, L: int, parity: np.ndarray) -> np.ndarr
     return Wk @ Ghat
 
 
-def sht_inverse(flm: np.ndarray, L: int, spin: int = 0) -> np.ndarray:
-    """Inverse spin SHT (Eq. 3).  flm [L, 2L-1] -> f [L theta, 2L-1 phi] (complex)."""
+def _dh_integrals(G: np.ndarray, L: int) -> np.ndarray:
+    """I[k, col] = sum_t w_t G_col(theta_t) exp(i k theta_t), |k| <= L-1, on the 2L DH rings."""
+    th = sampling.thetas_dh(L)
+    w = sampling.dh_weights(L)
+    k = _mrange(L)
+    return np.exp(1j * np.outer(k, th)) @ (w[:, None] * G)
+
+
+def _integrals(G, L, parity, samp):
+    return _colatitude_integrals(G, L, parity) if samp == "mw" else _dh_integrals(G, L)
+
+
+def sht_inverse(flm: np.ndarray, L: int, spin: int = 0, samp: str = "mw") -> np.ndarray:
+    """Inverse spin SHT (Eq. 3).  flm [L, 2L-1] -> f [R theta, 2L-1 phi] (complex), R rings."""
     ms = _mrange(L)
     Cmk = np.zeros((2 * L - 1, 2 * L - 1), dtype=np.complex128)   # [m, k]
     for l in range(abs(spin), L):
@@ -62,19 +82,19 @@ def sht_inverse(flm: np.ndarray, L: int, spin: int = 0) -> np.ndarray:
         norm = (-1.0) ** spin * np.sqrt((2 * l + 1) / (4 * np.pi))
         sl = slice(L - 1 - l, L + l)
         Cmk[sl, sl] += norm * flm[l, sl][:, None] * Cl
-    th = sampling.thetas(L)
+    th = sampling.thetas_for(L, samp)
     G = Cmk @ np.exp(1j * np.outer(ms, th))                        # [m, t]
     E = np.exp(1j * np.outer(ms, sampling.phis(L)))                 # [m, p]
     return G.T @ E
 
 
-def sht_forward(f: np.ndarray, L: int, spin: int = 0) -> np.ndarray:
-    """Forward spin SHT (Eq. 2) of MW samples f [L, 2L-1] -> flm [L, 2L-1]."""
+def sht_forward(f: np.ndarray, L: int, spin: int = 0, samp: str = "mw") -> np.ndarray:
+    """Forward spin SHT (Eq. 2) of samples f [R, 2L-1] -> flm [L, 2L-1]."""
     ms = _mrange(L)
     E = np.exp(-1j * np.outer(sampling.phis(L), ms))                # [p, m]
     G = (2 * np.pi / (2 * L - 1)) * (np.asarray(f, dtype=np.complex128) @ E)   # [t, m]
     parity = (-1.0) ** ((ms + spin) % 2)
-    I = _colatitude_integrals(G, L, parity)                         # [k, m]
+    I = _integrals(G, L, parity, samp)                              # [k, m]
     flm = np.zeros((L, 2 * L - 1), dtype=np.complex128)
     for l in range(abs(spin), L):
         Cl = wigner.fourier_coeffs(l, [-spin])[:, 0, :]             # [m, k]
@@ -84,8 +104,8 @@ def sht_forward(f: np.ndarray, L: int, spin: int = 0) -> np.ndarray:
     return flm
 
 
-def wigner_inverse(flmn: np.ndarray, L: int, N: int) -> np.ndarray:
-    """Inverse Wigner transform (Eq. 5).  flmn [2N-1, L, 2L-1] -> f [2N-1 gamma, L beta, 2L-1 alpha]."""
+def wigner_inverse(flmn: np.ndarray, L: int, N: int, samp: str = "mw") -> np.ndarray:
+    """Inverse Wigner transform (Eq. 5).  flmn [2N-1, L, 2L-1] -> f [2N-1 gamma, R beta, 2L-1 alpha]."""
     ms = _mrange(L)
     ns = np.arange(-(N - 1), N)
     Cnmk = np.zeros((2 * N - 1, 2 * L - 1, 2 * L - 1), dtype=np.complex128)   # [n, m, k]
@@ -94,7 +114,7 @@ def wigner_inverse(flmn: np.ndarray, L: int, N: int) -> np.ndarray:
         sl = slice(L - 1 - l, L + l)
         coef = (2 * l + 1) / (8 * np.pi ** 2) * flmn[:, l, sl]       # [n, m]
         Cnmk[:, sl, sl] += np.transpose(Cl, (1, 0, 2)) * coef[:, :, None]
-    betas = sampling.thetas(L)
+    betas = sampling.thetas_for(L, samp)
     G = Cnmk @ np.exp(1j * np.outer(ms, betas))                      # [n, m, b]
     Ea = np.exp(1j * np.outer(ms, sampling.phis(L)))                  # [m, a]
     Eg = np.exp(1j * np.outer(ns, sampling.gammas(N)))               # [n, g]
@@ -102,8 +122,8 @@ def wigner_inverse(flmn: np.ndarray, L: int, N: int) -> np.ndarray:
     return np.einsum('nba,ng->gba', H, Eg)                           # gamma sum
 
 
-def wigner_forward(f: np.ndarray, L: int, N: int) -> np.ndarray:
-    """Forward Wigner transform (Eq. 4) of MW SO(3) samples f [2N-1, L, 2L-1] -> flmn."""
+def wigner_forward(f: np.ndarray, L: int, N: int, samp: str = "mw") -> np.ndarray:
+    """Forward Wigner transform (Eq. 4) of SO(3) samples f [2N-1, R, 2L-1] -> flmn."""
     ms = _mrange(L)
     ns = np.arange(-(N - 1), N)
     Ea = np.exp(-1j * np.outer(sampling.phis(L), ms))                # [a, m]
@@ -113,8 +133,9 @@ def wigner_forward(f: np.ndarray, L: int, N: int) -> np.ndarray:
     G = np.einsum('gbm,gn->nbm', G, Eg)
     G *= (2 * np.pi / (2 * L - 1)) * (2 * np.pi / (2 * N - 1))      # [n, b, m]
     parity = (-1.0) ** ((ms[None, :] + ns[:, None]) % 2)              # [n, m]
-    Gcols = np.transpose(G, (1, 0, 2)).reshape(L, -1)
-    I = _colatitude_integrals(Gcols, L, parity.reshape(-1))
+    R = G.shape[1]
+    Gcols = np.transpose(G, (1, 0, 2)).reshape(R, -1)
+    I = _integrals(Gcols, L, parity.reshape(-1), samp)
     I = I.reshape(2 * L - 1, 2 * N - 1, 2 * L - 1)                  # [k, n, m]
     flmn = np.zeros((2 * N - 1, L, 2 * L - 1), dtype=np.complex128)
     for l in range(L):

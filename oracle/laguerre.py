@@ -78,16 +78,16 @@ def radial_inverse(f_p: np.ndarray, P: int, tau: float = 1.0) -> np.ndarray:
 
 
 def spherical_laguerre_forward(f: np.ndarray, L: int, P: int, tau: float = 1.0,
-                               spin: int = 0) -> np.ndarray:
-    """Z (Eq. 10): samples f[i, t, p] on (r_i, MW grid) -> f_lmp as [P, L, 2L-1]."""
+                               spin: int = 0, samp: str = "mw") -> np.ndarray:
+    """Z (Eq. 10): samples f[i, t, p] on (r_i, MW or DH grid) -> f_lmp as [P, L, 2L-1]."""
     from . import harmonic
-    flm_r = np.stack([harmonic.sht_forward(f[i], L, spin) for i in range(P)])
+    flm_r = np.stack([harmonic.sht_forward(f[i], L, spin, samp) for i in range(P)])
     return radial_forward(flm_r, P, tau)
 
 
 def spherical_laguerre_inverse(flmp: np.ndarray, L: int, P: int, tau: float = 1.0,
-                               spin: int = 0) -> np.ndarray:
-    """Z^-1 (Eq. 11): f_lmp [P, L, 2L-1] -> samples [P nodes, L, 2L-1] (complex)."""
+                               spin: int = 0, samp: str = "mw") -> np.ndarray:
+    """Z^-1 (Eq. 11): f_lmp [P, L, 2L-1] -> samples [P nodes, R rings, 2L-1] (complex)."""
     from . import harmonic
     flm_r = radial_inverse(flmp, P, tau)
-    return np.stack([harmonic.sht_inverse(flm_r[i], L, spin) for i in range(P)])
+    return np.stack([harmonic.sht_inverse(flm_r[i], L, spin, samp) for i in range(P)])

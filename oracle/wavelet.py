@@ -24,16 +24,18 @@ def _embed_slice(Lsmall: int, Lbig: int):
 
 
 def analysis(f: np.ndarray, L: int, N: int, lam: float, J0: int, spin: int = 0,
-             reality: bool = False):
-    """Returns ([W^j as [2N_j-1, L_j, 2L_j-1] for j = J0..J], W^Phi as [L_Phi, 2L_Phi-1])."""
-    flm = harmonic.sht_forward(f, L, spin)
+             reality: bool = False, samp: str = "mw"):
+    """Returns ([W^j as [2N_j-1, R_j, 2L_j-1] for j = J0..J], W^Phi as [R_Phi, 2L_Phi-1]).
+
+    R is the ring count of the sampling (``samp``: "mw" or "dh") at each band-limit."""
+    flm = harmonic.sht_forward(f, L, spin, samp)
     LP = filters.scaling_bandlimit(L, lam, J0)
     phi = filters.scaling_filter(L, lam, J0, spin)
     wphi_lm = np.zeros((LP, 2 * LP - 1), dtype=np.complex128)
     sl = _embed_slice(LP, L)
     for l in range(LP):
         wphi_lm[l] = math.sqrt(4 * math.pi / (2 * l + 1)) * phi[l] * flm[l, sl]
-    wphi = harmonic.sht_inverse(wphi_lm, LP, 0)
+    wphi = harmonic.sht_inverse(wphi_lm, LP, 0, samp)
     wavs = []
     for (j, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0):
         psi = filters.wavelet_filter(L, N, lam, j, spin)
@@ -43,31 +45,31 @@ def analysis(f: np.ndarray, L: int, N: int, lam: float, J0: int, spin: int = 0,
             for n in range(-(Nj - 1), Nj):
                 coef[n + Nj - 1, l] = (8 * math.pi ** 2 / (2 * l + 1)) * flm[l, slj] * \
                     np.conj(psi[l, n + N - 1])
-        w = harmonic.wigner_inverse(coef, Lj, Nj)
+        w = harmonic.wigner_inverse(coef, Lj, Nj, samp)
         wavs.append(w.real.copy() if reality else w)
     return wavs, (wphi.real.copy() if reality else wphi)
 
 
 def synthesis(wavs, wphi: np.ndarray, L: int, N: int, lam: float, J0: int, spin: int = 0,
-              reality: bool = False) -> np.ndarray:
+              reality: bool = False, samp: str = "mw") -> np.ndarray:
     """Inverse of ``analysis`` (Eq. 42)."""
     flm = np.zeros((L, 2 * L - 1), dtype=np.complex128)
     LP = filters.scaling_bandlimit(L, lam, J0)
     phi = filters.scaling_filter(L, lam, J0, spin)
-    wphi_lm = harmonic.sht_forward(wphi, LP, 0)
+    wphi_lm = harmonic.sht_forward(wphi, LP, 0, samp)
     sl = _embed_slice(LP, L)
     for l in range(LP):
         flm[l, sl] += math.sqrt(4 * math.pi / (2 * l + 1)) * phi[l] * wphi_lm[l]
     for (j, Lj, Nj), w in zip(filters.scale_bandlimits(L, N, lam, J0), wavs):
         psi = filters.wavelet_filter(L, N, lam, j, spin)
-        coef = harmonic.wigner_forward(w, Lj, Nj)
+        coef = harmonic.wigner_forward(w, Lj, Nj, samp)
         slj = _embed_slice(Lj, L)
         for l in range(Lj):
             acc = np.zeros(2 * Lj - 1, dtype=np.complex128)
             for n in range(-(Nj - 1), Nj):
                 acc += coef[n + Nj - 1, l] * psi[l, n + N - 1]
             flm[l, slj] += acc
-    f = harmonic.sht_inverse(flm, L, spin)
+    f = harmonic.sht_inverse(flm, L, spin, samp)
     return f.real.copy() if reality else f
 
 
