@@ -4,7 +4,8 @@
  * The library computes the scale-discretised directional wavelet transform on the
  * sphere (Sec. 3.1 and Algorithm 1 of "Differentiable and accelerated directional
  * wavelet transforms on the sphere and ball", Price et al. 2024) on McEwen-Wiaux
- * (MW) sampling, together with the harmonic transforms it is built from: the spin
+ * (MW) or Driscoll-Healy (DH) sampling (the transforms are sampling agnostic, Sec. 1),
+ * together with the harmonic transforms it is built from: the spin
  * spherical-harmonic transform Y (Sec. 2.1, Eqs. 2-3) and the Wigner transform D
  * (Sec. 2.2, Eqs. 4-5), and the Fourier-Laguerre radial transform of the ball
  * (Sec. 2.3, Eqs. 6-8).
@@ -22,11 +23,15 @@
  *             pixel arrays (double); otherwise pixel arrays are complex,
  *             interleaved (re, im) pairs of double.  Harmonic-space arrays are
  *             always complex interleaved.
+ * Sampling    R(L) colatitude rings by 2L-1 longitudes phi_p = 2 pi p/(2L-1) at band-limit L:
+ *             MW  R = L rings theta_t = pi(2t+1)/(2L-1), t < L (the last is the south pole);
+ *             DH  R = 2L rings theta_t = pi(2t+1)/(4L), t < 2L (no pole sampled).
+ *             On SO(3) beta takes the theta rings and alpha the phi samples.
  * Layouts     (row-major, batch outermost; `b` = batch index)
- *   map       [b][L theta][2L-1 phi], theta_t = pi(2t+1)/(2L-1), phi_p = 2 pi p/(2L-1)
- *   wav       scales j = J0..J concatenated; scale j is [b][2N_j-1 gamma][L_j beta][2L_j-1 alpha]
- *             with gamma_g = 2 pi g/(2N_j-1) and alpha, beta on the MW grid at L_j
- *   scal      [b][L_Phi][2L_Phi-1] (MW grid at the scaling band-limit L_Phi)
+ *   map       [b][R(L) theta][2L-1 phi]
+ *   wav       scales j = J0..J concatenated; scale j is [b][2N_j-1 gamma][R(L_j) beta][2L_j-1 alpha]
+ *             with gamma_g = 2 pi g/(2N_j-1) and alpha, beta on the grid at L_j
+ *   scal      [b][R(L_Phi)][2L_Phi-1] (the grid at the scaling band-limit L_Phi)
  *   flm       [b][L][Mc] with Mc = L (m = 0..L-1) for real plans and Mc = 2L-1
  *             (index m + L - 1) otherwise; real signals obey f_{l,-m} = (-1)^m conj f_lm
  *   flmn      [b][2N_j-1][L_j][Mc_j], n index n + N_j - 1, m indexed as for flm at L_j
@@ -68,6 +73,14 @@ typedef enum {
  *                  support L <= 256 (S2W_EUNSUPPORTED above). */
 typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3 } s2w_precision;
 
+/* S2W_SAMPLING_MW  McEwen-Wiaux: L rings; the forward transforms' colatitude integral is
+ *                  exact through the periodic extension of each column (a dense quadrature
+ *                  matrix per parity of m + n).
+ * S2W_SAMPLING_DH  Driscoll-Healy: 2L midpoint rings; the colatitude integral is the
+ *                  weighted ring sum with the weights w_t that integrate cos(k theta) sin(theta)
+ *                  exactly for k < 2L (Fejer's first rule in x = cos theta).  L <= 512. */
+typedef enum { S2W_SAMPLING_MW = 0, S2W_SAMPLING_DH = 1 } s2w_sampling;
+
 /* Problem statement of the sphere transform (Algorithm 1; Sec. 3.3; App. A).
  *   L        angular band-limit, harmonic degrees l < L            (2 <= L <= 1024)
  *   N        azimuthal band-limit of the wavelets, |n| < N          (1 <= N <= L)
@@ -79,10 +92,12 @@ typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE =
  *   precompute 0 (Wigner-d functions by recursion inside the kernels)
  *   lambda   dilation factor lambda > 1 (Eq. A2); scale j uses band-limit
  *            L_j = min(ceil(lambda^(j+1)), L) and N_j = min(N, L_j), j = J0..J with J
- *            the smallest integer such that lambda^J >= L; L_Phi = min(ceil(lambda^J0), L). */
+ *            the smallest integer such that lambda^J >= L; L_Phi = min(ceil(lambda^J0), L).
+ *   sampling s2w_sampling (0 = MW, the default of a zeroed struct) */
 typedef struct {
   int L, N, J0, spin, reality, batch, precision, precompute;
   double lambda;
+  int sampling;
 } s2w_params;
 
 typedef struct s2w_plan s2w_plan;
@@ -162,13 +177,15 @@ s2w_status s2w_wigner_inverse(const s2w_plan* plan, int scale, const void* flmn,
  * forward transform f_p = sum_i omega_i K_p(r_i) f(r_i) (Eq. 7) is exact for band-limited
  * signals; the inverse is f(r_i) = sum_p K_p(r_i) f_p (Eq. 8).
  * Layouts (b = batch index): radial samples of harmonic coefficients f_r [b][P node][L][Mc] and
- * Fourier-Laguerre coefficients f_p [b][P][L][Mc], complex; ball pixels [b][P node][L][2L-1]
- * (real when reality = 1, else complex).  The plan owns a workspace of batch*P*L*Mc complex. */
+ * Fourier-Laguerre coefficients f_p [b][P][L][Mc], complex; ball pixels [b][P node][R(L)][2L-1]
+ * on the angular sampling `sampling` (real when reality = 1, else complex).  The plan owns a
+ * workspace of batch*P*L*Mc complex. */
 typedef struct {
   int L;          /* angular band-limit (2 <= L <= 1024) */
   int P;          /* radial band-limit (2 <= P <= 256) */
   int spin, reality, batch, precision;   /* as in s2w_params (precision S2W_FP64 or S2W_FP64_NATIVE) */
   double tau;     /* Laguerre scale tau > 0 */
+  int sampling;   /* angular sampling, s2w_sampling */
 } s2w_ball_params;
 
 typedef struct s2w_ball_plan s2w_ball_plan;
@@ -192,21 +209,22 @@ s2w_status s2w_ball_sl_inverse(const s2w_ball_plan* plan, const void* flmp, void
  * Wavelets Psi^{jj'}_lnp = sqrt((2l+1)/(8 pi^2)) kappa^j(l) kappa^{j'}(p) zeta_ln (App. A.4) for
  * angular scales j = J0..J (as in s2w_params) and radial scales j' = J0r..J', J' the smallest
  * integer with nu^J' >= P, kappa^{j'}(p) = kappa_nu(p / nu^j').  Multiresolution (Sec. 3.3):
- * scale (j, j') is sampled on the MW SO(3) grid at (L_j, N_j) and on the P_j'-node
+ * scale (j, j') is sampled on the SO(3) grid of the sampling at (L_j, N_j) and on the P_j'-node
  * Gauss-Laguerre rule, P_j' = min(ceil(nu^(j'+1)), P), r'_i = tau x'_i.  Scaling function:
  * |Phi_l0p|^2 (4 pi/(2l+1)) = A + B - A B with A = k_lambda(l/lambda^J0), B = k_nu(p/nu^J0r)
  * (the reading of App. A.4 that satisfies the admissibility condition of Sec. 3.2); the
- * scaling coefficients W^Phi are sampled at full resolution (P nodes, MW grid at L).
+ * scaling coefficients W^Phi are sampled at full resolution (P nodes, the grid at L).
  * Spin 0 only (S2W_EUNSUPPORTED otherwise); real fields when reality = 1.
- * Layouts: field f and scaling coefficients [batch][P node][L][2L-1]; wavelet coefficients
+ * Layouts: field f and scaling coefficients [batch][P node][R(L)][2L-1]; wavelet coefficients
  * wav: one block per scale k in the order of s2w_ball_wav_query_layout (j outer, j' inner),
- * block k = [batch][P_j' node][2N_j-1 gamma][L_j beta][2L_j-1 alpha], starting at element
+ * block k = [batch][P_j' node][2N_j-1 gamma][R(L_j) beta][2L_j-1 alpha], starting at element
  * wav_offsets[k] (offsets over the WHOLE batch, unlike s2w_query_layout).
  * The plan holds a sphere wavelet plan over batch*P node maps and two workspaces of
  * batch*P*L*Mc complex.  Same stream, allocation and error conventions as s2w_forward. */
 typedef struct {
   int L, N, P, J0, J0r, spin, reality, batch, precision, precompute;   /* precision/precompute as s2w_params */
   double lambda, nu, tau;
+  int sampling;   /* angular sampling, s2w_sampling */
 } s2w_ball_wav_params;
 
 typedef struct s2w_ball_wav_plan s2w_ball_wav_plan;
@@ -240,7 +258,7 @@ s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
  * running.  The paper has no counterpart: it is a deployment variant of the Eq. 3 transform.
  * Its m-column scratch is a fixed 16 MiB device array inside the library (held by every GPU
  * that loads it, until exit): the call allocates nothing and returns S2W_EINVAL when
- * batch * L * Mc exceeds 1,048,576 complex elements (e.g. 16 real maps at L = 256).  The first
+ * batch * R(L) * Mc exceeds 1,048,576 complex elements (e.g. 16 real MW maps at L = 256).  The first
  * call on a device looks the array's device address up (make it before any stream capture).
  * All calls share the array; calls whose work overlaps on the GPU race on it.  Same arguments,
  * layouts and results as s2w_sht_inverse. */

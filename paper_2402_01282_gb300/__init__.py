@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libs2w.so")
 _lib = None
 
 S2W_FP64, S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_NATIVE = 0, 1, 2, 3
+S2W_SAMPLING_MW, S2W_SAMPLING_DH = 0, 1
 STATUS = {0: "S2W_OK", 1: "S2W_EINVAL", 2: "S2W_ENOMEM", 3: "S2W_ECUDA", 4: "S2W_ETIMEOUT",
           5: "S2W_EUNSUPPORTED", 6: "S2W_ENONFINITE"}
 
@@ -43,20 +44,28 @@ class S2WError(RuntimeError):
 
 class BallParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("P", ctypes.c_int), ("spin", ctypes.c_int), ("reality", ctypes.c_int),
-                ("batch", ctypes.c_int), ("precision", ctypes.c_int), ("tau", ctypes.c_double)]
+                ("batch", ctypes.c_int), ("precision", ctypes.c_int), ("tau", ctypes.c_double),
+                ("sampling", ctypes.c_int)]
 
 
 class BallWavParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("N", ctypes.c_int), ("P", ctypes.c_int), ("J0", ctypes.c_int),
                 ("J0r", ctypes.c_int), ("spin", ctypes.c_int), ("reality", ctypes.c_int), ("batch", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precompute", ctypes.c_int), ("lam", ctypes.c_double),
-                ("nu", ctypes.c_double), ("tau", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("tau", ctypes.c_double), ("sampling", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("N", ctypes.c_int), ("J0", ctypes.c_int), ("spin", ctypes.c_int),
                 ("reality", ctypes.c_int), ("batch", ctypes.c_int), ("precision", ctypes.c_int),
-                ("precompute", ctypes.c_int), ("lam", ctypes.c_double)]
+                ("precompute", ctypes.c_int), ("lam", ctypes.c_double), ("sampling", ctypes.c_int)]
+
+
+def rings(L: int, sampling: int = 0) -> int:
+    """Colatitude rings of the grid at band-limit L: L (S2W_SAMPLING_MW) or 2L (S2W_SAMPLING_DH)."""
+    if sampling not in (S2W_SAMPLING_MW, S2W_SAMPLING_DH):
+        raise ValueError(f"unknown sampling {sampling}")
+    return 2 * L if sampling == S2W_SAMPLING_DH else L
 
 
 def load(path: str = LIB_PATH):
@@ -142,14 +151,17 @@ class Plan:
 
     Parameters follow the paper's statement of the problem: band-limits L and N,
     dilation ``lam`` (lambda), lowest scale J0, spin, reality of the signal and the
-    number of maps per call.
+    number of maps per call; ``sampling`` picks the grid (S2W_SAMPLING_MW or
+    S2W_SAMPLING_DH).
     """
 
     def __init__(self, L: int, N: int, lam: float = 2.0, J0: int = 0, spin: int = 0,
                  reality: bool = False, batch: int = 1, precision: int = S2W_FP64, stream=None,
-                 precompute: int = 0):
+                 precompute: int = 0, sampling: int = 0):
         lib = load()
-        self.params = Params(L, N, J0, spin, int(reality), batch, precision, int(precompute), float(lam))
+        self.params = Params(L, N, J0, spin, int(reality), batch, precision, int(precompute), float(lam),
+                             int(sampling))
+        self.sampling = int(sampling)
         h = ctypes.c_void_p()
         _check(lib.s2w_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
         self._h = h
@@ -170,6 +182,7 @@ class Plan:
         self.wav_offsets = list(offs)
         self.Lj, self.Nj = list(Lj), list(Nj)
         self.Mc = L if self.real else 2 * L - 1
+        self.R, self.R_phi = rings(L, self.sampling), rings(self.L_phi, self.sampling)
 
     # ------------------------------------------------------------------ buffers
     @property
@@ -179,7 +192,7 @@ class Plan:
 
     def empty_map(self, device="cuda"):
         import torch
-        return torch.empty((self.batch, self.L, 2 * self.L - 1), dtype=self.dtype, device=device)
+        return torch.empty((self.batch, self.R, 2 * self.L - 1), dtype=self.dtype, device=device)
 
     def empty_wav(self, device="cuda"):
         import torch
@@ -187,14 +200,14 @@ class Plan:
 
     def empty_scal(self, device="cuda"):
         import torch
-        return torch.empty((self.batch, self.L_phi, 2 * self.L_phi - 1), dtype=self.dtype, device=device)
+        return torch.empty((self.batch, self.R_phi, 2 * self.L_phi - 1), dtype=self.dtype, device=device)
 
     def empty_flm(self, device="cuda"):
         import torch
         return torch.empty((self.batch, self.L, self.Mc), dtype=torch.complex128, device=device)
 
     def scale_shape(self, s: int):
-        return (2 * self.Nj[s] - 1, self.Lj[s], 2 * self.Lj[s] - 1)
+        return (2 * self.Nj[s] - 1, rings(self.Lj[s], self.sampling), 2 * self.Lj[s] - 1)
 
     def empty_flmn(self, s: int, device="cuda"):
         import torch
@@ -203,7 +216,7 @@ class Plan:
         return torch.empty((self.batch, 2 * Nj - 1, Lj, Mcj), dtype=torch.complex128, device=device)
 
     def scale_view(self, wav, s: int):
-        """View of scale index s of a [batch, wav_elems] tensor as [batch, 2N_j-1, L_j, 2L_j-1]."""
+        """View of scale index s of a [batch, wav_elems] tensor as [batch, 2N_j-1, R(L_j), 2L_j-1]."""
         a, b = self.wav_offsets[s], self.wav_offsets[s + 1]
         return wav[:, a:b].view(self.batch, *self.scale_shape(s))
 
@@ -295,9 +308,10 @@ class BallPlan:
     ball signals with angular band-limit L and radial band-limit P."""
 
     def __init__(self, L: int, P: int, tau: float = 1.0, spin: int = 0, reality: bool = False,
-                 batch: int = 1, precision: int = S2W_FP64, stream=None):
+                 batch: int = 1, precision: int = S2W_FP64, stream=None, sampling: int = 0):
         lib = load()
-        self.params = BallParams(L, P, spin, int(reality), batch, precision, float(tau))
+        self.params = BallParams(L, P, spin, int(reality), batch, precision, float(tau), int(sampling))
+        self.sampling, self.R = int(sampling), rings(L, int(sampling))
         h = ctypes.c_void_p()
         _check(lib.s2w_ball_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
         self._h = h
@@ -319,7 +333,7 @@ class BallPlan:
     def empty_pixels(self, device="cuda"):
         import torch
         dt = torch.float64 if self.real else torch.complex128
-        return torch.empty((self.batch, self.P, self.L, 2 * self.L - 1), dtype=dt, device=device)
+        return torch.empty((self.batch, self.P, self.R, 2 * self.L - 1), dtype=dt, device=device)
 
     def laguerre_forward(self, f_r, f_p, stream=None):
         _check(_lib.s2w_laguerre_forward(self._h, _ptr(f_r, False, "f_r"), _ptr(f_p, False, "f_p"),
@@ -393,10 +407,11 @@ class BallWavPlan:
 
     def __init__(self, L: int, N: int, P: int, lam: float = 2.0, nu: float = 2.0, J0: int = 0, J0r: int = 0,
                  tau: float = 1.0, reality: bool = True, batch: int = 1, precision: int = S2W_FP64,
-                 precompute: int = 0, stream=None):
+                 precompute: int = 0, stream=None, sampling: int = 0):
         lib = load()
         self.params = BallWavParams(L, N, P, J0, J0r, 0, int(reality), batch, precision, int(precompute),
-                                    float(lam), float(nu), float(tau))
+                                    float(lam), float(nu), float(tau), int(sampling))
+        self.sampling, self.R = int(sampling), rings(L, int(sampling))
         h = ctypes.c_void_p()
         _check(lib.s2w_ball_wav_plan_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
         self._h = h
@@ -423,16 +438,17 @@ class BallWavPlan:
 
     def empty_field(self, device="cuda"):
         import torch
-        return torch.empty((self.batch, self.P, self.L, 2 * self.L - 1), dtype=self.dtype, device=device)
+        return torch.empty((self.batch, self.P, self.R, 2 * self.L - 1), dtype=self.dtype, device=device)
 
     def empty_wav(self, device="cuda"):
         import torch
         return torch.empty((self.wav_elems,), dtype=self.dtype, device=device)
 
     def scale_view(self, wav, k: int):
-        """Block k of the wavelet coefficients as [batch, P_j', 2N_j-1, L_j, 2L_j-1]."""
+        """Block k of the wavelet coefficients as [batch, P_j', 2N_j-1, R(L_j), 2L_j-1]."""
         a, b = self.wav_offsets[k], self.wav_offsets[k + 1]
-        return wav[a:b].view(self.batch, self.Pj[k], 2 * self.Nj[k] - 1, self.Lj[k], 2 * self.Lj[k] - 1)
+        return wav[a:b].view(self.batch, self.Pj[k], 2 * self.Nj[k] - 1, rings(self.Lj[k], self.sampling),
+                             2 * self.Lj[k] - 1)
 
     def forward(self, f, wav, scal, stream=None):
         _check(_lib.s2w_ball_forward(self._h, _ptr(f, self.real, "f"), _ptr(wav, self.real, "wav"),

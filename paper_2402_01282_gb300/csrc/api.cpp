@@ -62,6 +62,7 @@ ColumnArgs cols(const s2w_plan* P, int nact, int L) {
   c.B = batch_of(P);
   c.nact = nact;
   c.L = L;
+  c.nr = rings_of(P->p.sampling, L);
   c.Mc = Mc_at(P, L);
   c.mlo = mlo_at(P, L);
   return c;
@@ -73,20 +74,20 @@ const char* kKindNames[K_NKINDS] = {"dft_forward", "dft_inverse", "wigner_invers
                                     "quadrature_adjoint"};
 
 double contraction_terms(const s2w_plan* P, const TransformSpec& t) {
-  const int L = t.L, mlo = mlo_at(P, L), Mc = Mc_at(P, L);
+  const int L = t.L, mlo = mlo_at(P, L), Mc = Mc_at(P, L), nr = rings_of(P->p.sampling, L);
   double T = 0.0;
   for (int mi = 0; mi < Mc; ++mi)
     for (int n : t.nvals_h) {
       const int l0 = std::max(std::abs(mlo + mi), std::abs(n));
-      if (l0 < L) T += double(L) * double(L - l0);
+      if (l0 < L) T += double(nr) * double(L - l0);
     }
   return T;
 }
 
 double dft_flops(const s2w_plan* P, const TransformSpec& t) {
-  const double n = 2.0 * t.L - 1.0, B = batch_of(P), Ng = 2.0 * t.N - 1.0;
+  const double n = 2.0 * t.L - 1.0, B = batch_of(P), Ng = 2.0 * t.N - 1.0, nr = rings_of(P->p.sampling, t.L);
   const double ring = (P->real ? 2.5 : 5.0) * n * std::log2(n);
-  return B * Ng * t.L * ring + 8.0 * B * t.L * Mc_at(P, t.L) * t.nact * Ng;
+  return B * Ng * nr * ring + 8.0 * B * nr * Mc_at(P, t.L) * t.nact * Ng;
 }
 
 // algorithmic flops per contraction term: the recursion step (5, unless the d values come
@@ -197,8 +198,9 @@ s2w_status adj_fwd_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, v
     S2W_CUDA(launch_wigner_inverse(P, g, ta, in, c, st), "adjoint of the forward contraction");
   }
   {
+    const double nr = rings_of(P->p.sampling, t.L);
     TraceScope ts(P, st, K_QUAD_ADJ,
-                  P->trace_on ? 4.0 * batch_of(P) * t.nact * (double)Mc_at(P, t.L) * t.L * t.L : 0.0);
+                  P->trace_on ? (g.wdiag ? 2.0 : 4.0 * t.L) * batch_of(P) * t.nact * (double)Mc_at(P, t.L) * nr : 0.0);
     S2W_CUDA(launch_quad_adjoint(P, g, ta, c, st), "transposed colatitude quadrature");
   }
   {
@@ -436,7 +438,8 @@ s2w_status s2w_wigner_forward(const s2w_plan* cP, int scale, const void* f, void
   CoefArgs out = raw_args(P, scale, flmn);
   S2W_CUDA(launch_zero(flmn, out.s_b * P->p.batch * (int64_t)sizeof(double2), st), "zero flmn");
   const int Lj = P->Lj[scale], Nj = P->Nj[scale];
-  return fwd_transform(P, P->raw_t[scale], f, (int64_t)(2 * Nj - 1) * Lj * (2 * Lj - 1), out, st);
+  return fwd_transform(P, P->raw_t[scale], f, (int64_t)(2 * Nj - 1) * rings_of(P->p.sampling, Lj) * (2 * Lj - 1),
+                       out, st);
 }
 
 s2w_status s2w_wigner_inverse(const s2w_plan* cP, int scale, const void* flmn, void* f, void* stream) {
@@ -450,7 +453,7 @@ s2w_status s2w_wigner_inverse(const s2w_plan* cP, int scale, const void* flmn, v
   P->last_stream = st;
   const int Lj = P->Lj[scale], Nj = P->Nj[scale];
   return inv_transform(P, P->raw_t[scale], raw_args(P, scale, flmn), f,
-                       (int64_t)(2 * Nj - 1) * Lj * (2 * Lj - 1), st);
+                       (int64_t)(2 * Nj - 1) * rings_of(P->p.sampling, Lj) * (2 * Lj - 1), st);
 }
 
 s2w_status s2w_check(const s2w_plan* P) {

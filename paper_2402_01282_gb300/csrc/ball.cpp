@@ -208,6 +208,7 @@ s2w_status s2w_ball_plan_create(const s2w_ball_params* prm, void* stream, s2w_ba
   sp.precision = p.precision;
   sp.precompute = 0;
   sp.lambda = 2.0;
+  sp.sampling = p.sampling;
   s2w_status s = s2w_plan_create(&sp, stream, &B->sphere);   // validates L, spin, reality
   if (s != S2W_OK) {
     delete B;

@@ -126,7 +126,7 @@ struct Ctx {
   int64_t scale_pix(int k) const {   // elements of one node map of wavelet scale k
     const int s = W->sc_s[k];
     const int Lj = W->sph->Lj[s], Nj = W->sph->Nj[s];
-    return (int64_t)(2 * Nj - 1) * Lj * (2 * Lj - 1);
+    return (int64_t)(2 * Nj - 1) * rings_of(W->p.sampling, Lj) * (2 * Lj - 1);
   }
   char* wav_at(void* wav, int k) const { return static_cast<char*>(wav) + W->wav_off[k] * elem(); }
 };
@@ -162,6 +162,7 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
   sp.precision = p.precision;
   sp.precompute = p.precompute;
   sp.lambda = p.lambda;
+  sp.sampling = p.sampling;
   s2w_status s = s2w_plan_create(&sp, stream, &W->sph);   // validates L, N, lambda, J0
   if (s != S2W_OK) {
     delete W;
@@ -170,7 +171,7 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
   cudaStream_t st = (cudaStream_t)stream;
   const int P = p.P, L = p.L;
   W->Mc = p.reality ? L : 2 * L - 1;
-  W->field_elems = (int64_t)P * L * (2 * L - 1);
+  W->field_elems = (int64_t)P * rings_of(p.sampling, L) * (2 * L - 1);
   for (int j = p.J0r; j <= Jr; ++j) {
     W->jr.push_back(j);
     W->Pj.push_back(std::min(tiling::ceil_pow(p.nu, j + 1), P));
@@ -182,7 +183,7 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
       W->sc_r.push_back((int)r);
       const int Lj = W->sph->Lj[s_], Nj = W->sph->Nj[s_];
       W->wav_off.push_back(W->wav_off.back() +
-                           (int64_t)p.batch * W->Pj[r] * (2 * Nj - 1) * Lj * (2 * Lj - 1));
+                           (int64_t)p.batch * W->Pj[r] * (2 * Nj - 1) * rings_of(p.sampling, Lj) * (2 * Lj - 1));
     }
   W->wav_elems = W->wav_off.back();
 

@@ -92,8 +92,8 @@ struct DftcArgs {
   const void* pix_in;
   void* pix_out;
   int64_t pix_sb;
-  double2* G;           // [B][nact][L][Mc] float64 columns
-  int B, nact, Ng, L, Mc, mlo, n, n1, n2;
+  double2* G;           // [B][nact][nr][Mc] float64 columns
+  int B, nact, Ng, L, nr, Mc, mlo, n, n1, n2;
   const float4* tw;     // [n] exp(+2 pi i e/n) as pairs
   const float4* gph;    // [nact][Ng] exp(+i n gamma_g) as pairs
   const int* nvals;     // [nact] the n values carried
@@ -109,7 +109,7 @@ __global__ void k_dftc_fwd(DftcArgs a) {
   float4* tmp = x + n;
   float4* H = tmp + n;   // [Ng][Mc]
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
-  const int64_t ring = (int64_t)a.L * n;
+  const int64_t ring = (int64_t)a.nr * n;
   for (int g = 0; g < a.Ng; ++g) {
     __syncthreads();
     const int64_t base = (int64_t)b * a.pix_sb + (int64_t)g * ring + (int64_t)t * n;
@@ -133,7 +133,7 @@ __global__ void k_dftc_fwd(DftcArgs a) {
     const int ni = idx / a.Mc, mi = idx - ni * a.Mc;
     Acc re{0.f, 0.f}, im{0.f, 0.f};
     for (int g = 0; g < a.Ng; ++g) cmac<-1, PLAIN>(re, im, H[g * a.Mc + mi], a.gph[ni * a.Ng + g]);
-    a.G[(((int64_t)b * a.nact + ni) * a.L + t) * a.Mc + mi] =
+    a.G[(((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc + mi] =
         make_double2(to_double(re) * a.scale, to_double(im) * a.scale);
   }
 }
@@ -149,9 +149,9 @@ __global__ void k_dftc_inv(DftcArgs a) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   for (int idx = threadIdx.x; idx < a.nact * a.Mc; idx += blockDim.x) {
     const int ni = idx / a.Mc, mi = idx - ni * a.Mc;
-    Gs[idx] = split(a.G[(((int64_t)b * a.nact + ni) * a.L + t) * a.Mc + mi]);
+    Gs[idx] = split(a.G[(((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc + mi]);
   }
-  const int64_t ring = (int64_t)a.L * n;
+  const int64_t ring = (int64_t)a.nr * n;
   for (int g = 0; g < a.Ng; ++g) {
     __syncthreads();
     for (int mi = threadIdx.x; mi < a.Mc; mi += blockDim.x) {
@@ -379,7 +379,7 @@ __global__ void k_dftg_fwd(DftcArgs a) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   __syncthreads();
   const int nj = njs, Ng = a.Ng, hg = (Ng - 1) / 2;
-  const int64_t ring = (int64_t)L * n;
+  const int64_t ring = (int64_t)a.nr * n;
   const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
   // H_j(alpha) = sum_g W(alpha, gamma_g) exp(-i n_j gamma_g)
   for (int j0 = 0; j0 < nj; j0 += kJobChunk) {
@@ -421,8 +421,8 @@ __global__ void k_dftg_fwd(DftcArgs a) {
     stage1_sym<-1, PLAIN>(HZ + j * n, tmp, tw, n, a.n1, a.n2);
     __syncthreads();
     const int ni = jn[j], pi = jp[j];
-    double2* Gn = a.G + (((int64_t)b * a.nact + ni) * L + t) * a.Mc;
-    double2* Gp = (pi >= 0) ? a.G + (((int64_t)b * a.nact + pi) * L + t) * a.Mc : nullptr;
+    double2* Gn = a.G + (((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc;
+    double2* Gp = (pi >= 0) ? a.G + (((int64_t)b * a.nact + pi) * a.nr + t) * a.Mc : nullptr;
     const double sc = a.scale;
     const int mlo = a.mlo;
     stage2_sym<-1, PLAIN>(tmp, AB, tw, n, a.n1, a.n2, [&](int k, Acc re, Acc im) {
@@ -461,8 +461,8 @@ __global__ void k_dftg_inv(DftcArgs a) {
   const int nj = njs;
   for (int j = 0; j < nj; ++j) {
     const int ni = jn[j], pi = jp[j];
-    const double2* Gn = a.G + (((int64_t)b * a.nact + ni) * L + t) * a.Mc;
-    const double2* Gp = a.G + (((int64_t)b * a.nact + (pi >= 0 ? pi : ni)) * L + t) * a.Mc;
+    const double2* Gn = a.G + (((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc;
+    const double2* Gp = a.G + (((int64_t)b * a.nact + (pi >= 0 ? pi : ni)) * a.nr + t) * a.Mc;
     __syncthreads();
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       double2 v;
@@ -492,7 +492,7 @@ __global__ void k_dftg_inv(DftcArgs a) {
   // P = sum_j Z_j cos, Q = sum_j Z_j sin.  Real signals: the n, -n pair contributes 2 Re, the
   // n = 0 job Re.
   const int Ng = a.Ng, hg = (Ng - 1) / 2;
-  const int64_t ring = (int64_t)L * n;
+  const int64_t ring = (int64_t)a.nr * n;
   const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
   for (int al = threadIdx.x; al < n; al += blockDim.x) {
     for (int g = 0; g <= hg; ++g) {
@@ -531,6 +531,7 @@ DftcArgs make_args(const GridTables& g, const TransformSpec& t, ColumnArgs c) {
   a.nact = c.nact;
   a.Ng = 2 * t.N - 1;
   a.L = c.L;
+  a.nr = c.nr;
   a.Mc = c.Mc;
   a.mlo = c.mlo;
   a.n = g.n;
@@ -578,7 +579,7 @@ cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, con
   a.pix_out = nullptr;
   a.pix_sb = pix_sb;
   a.scale = (2.0 * 3.14159265358979323846 / g.n) * t.gscale;
-  dim3 grid(c.L, c.B);
+  dim3 grid(c.nr, c.B);
   if (use_dftg(g, t, real, true)) {
     const size_t sm = dftg_smem(g, t, real, true);
     const int th = t.dft_threads_fwd;
@@ -597,7 +598,7 @@ cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, Col
   a.pix_in = nullptr;
   a.pix_out = pix;
   a.pix_sb = pix_sb;
-  dim3 grid(c.L, c.B);
+  dim3 grid(c.nr, c.B);
   if (use_dftg(g, t, real, false)) {
     const size_t sm = dftg_smem(g, t, real, false);
     const int th = t.dft_threads_inv;

@@ -9,6 +9,8 @@
 //                            against the weighted columns, products fused in the epilogue.
 #include <math.h>
 
+#include <algorithm>
+
 #include "comp32.cuh"
 #include "s2w_internal.h"
 #include "wigner_rec.cuh"
@@ -75,8 +77,8 @@ struct DftArgs {
   const void* pix_in;
   void* pix_out;
   int64_t pix_sb;       // elements between maps
-  double2* G;           // [B][nact][L][Mc]
-  int B, nact, Ng, L, Mc, mlo, n, n1, n2;
+  double2* G;           // [B][nact][nr][Mc]
+  int B, nact, Ng, L, nr, Mc, mlo, n, n1, n2;
   const double2* tw;
   const double2* gph;   // [nact][Ng] exp(+i n gamma_g)
   double scale;
@@ -92,7 +94,7 @@ __global__ void k_dft_fwd(DftArgs a) {
   double2* tmp = x + n;          // [n]
   double2* H = tmp + n;          // [Ng][Mc]
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
-  const int64_t ring = (int64_t)a.L * n;
+  const int64_t ring = (int64_t)a.nr * n;
   for (int g = 0; g < a.Ng; ++g) {
     __syncthreads();
     const int64_t base = (int64_t)b * a.pix_sb + (int64_t)g * ring + (int64_t)t * n;
@@ -119,7 +121,7 @@ __global__ void k_dft_fwd(DftArgs a) {
       re = fma(h.x, p.x, fma(h.y, p.y, re));
       im = fma(h.y, p.x, fma(-h.x, p.y, im));
     }
-    a.G[(((int64_t)b * a.nact + ni) * a.L + t) * a.Mc + mi] = make_double2(re * a.scale, im * a.scale);
+    a.G[(((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc + mi] = make_double2(re * a.scale, im * a.scale);
   }
 }
 
@@ -135,9 +137,9 @@ __global__ void k_dft_inv(DftArgs a) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   for (int idx = threadIdx.x; idx < a.nact * a.Mc; idx += blockDim.x) {
     const int ni = idx / a.Mc, mi = idx - ni * a.Mc;
-    Gs[idx] = a.G[(((int64_t)b * a.nact + ni) * a.L + t) * a.Mc + mi];
+    Gs[idx] = a.G[(((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc + mi];
   }
-  const int64_t ring = (int64_t)a.L * n;
+  const int64_t ring = (int64_t)a.nr * n;
   for (int g = 0; g < a.Ng; ++g) {
     __syncthreads();
     for (int mi = threadIdx.x; mi < a.Mc; mi += blockDim.x) {
@@ -177,8 +179,8 @@ struct WigInvArgs {
   const double2* mult;   // [L][nact]
   const int* nvals;
   int nact;
-  double2* G;            // [B][nact][L][Mc]
-  int B, L, Mc, mlo;
+  double2* G;            // [B][nact][nr][Mc]
+  int B, L, nr, Mc, mlo;
   RecTables T;
 };
 
@@ -195,11 +197,11 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
   float4* F4 = reinterpret_cast<float4*>(Fs);
   const int mi = blockIdx.x, ni = blockIdx.y;
   const int m = a.mlo + mi, nn = a.nvals[ni];
-  const int L = a.L;
+  const int L = a.L, nr = a.nr;
   const int b = blockIdx.z * blockDim.x + threadIdx.x;
   const int l0 = max(abs(m), abs(nn));
-  const double wb = (b < L) ? a.T.wpole[b] : 0.0;
-  const double* cK = (2 * (2 * b + 1) < a.T.n) ? cKn : cKs;
+  const double wb = (b < nr) ? a.T.wpole[b] : 0.0;
+  const double* cK = (2 * (2 * b + 1) < a.T.den) ? cKn : cKs;
   for (int map0 = 0; map0 < a.B; map0 += MB) {
     double2 acc[C32 ? 1 : MB];
     Acc ar[C32 ? MB : 1], ai[C32 ? MB : 1];
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
     }
     double v = 0.0, vp = 0.0;
     int q = 0;
-    if (b < L && l0 < L) wigner_seed(a.T, b, l0, m, nn, v, q);
+    if (b < nr && l0 < L) wigner_seed(a.T, b, l0, m, nn, v, q);
     for (int ls = l0; ls < L; ls += kInvLT) {
       const int cnt = min(kInvLT, L - ls);
       __syncthreads();
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
       }
       for (int i = threadIdx.x; i < cnt; i += blockDim.x) rec_coeffs(ls + i, m, nn, cA[i], cKn[i], cKs[i], cC[i]);
       __syncthreads();
-      if (b < L) {
+      if (b < nr) {
         for (int i = 0; i < cnt; ++i) {
           if (q == 0) {
             if (C32) {
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
         }
       }
     }
-    if (b < L) {
+    if (b < nr) {
 #pragma unroll
       for (int k = 0; k < MB; ++k) {
         const int bm = map0 + k;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
           double2 r;
           if (C32) r = make_double2(to_double(ar[k]), to_double(ai[k]));
           else r = acc[C32 ? 0 : k];
-          a.G[(((int64_t)bm * a.nact + ni) * L + b) * a.Mc + mi] = r;
+          a.G[(((int64_t)bm * a.nact + ni) * nr + b) * a.Mc + mi] = r;
         }
       }
     }
@@ -275,16 +277,17 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
 }
 
 struct WigFwdArgs {
-  const double2* G;      // [B][nact][L][Mc]
-  int B, L, Mc, mlo;
+  const double2* G;      // [B][nact][nr][Mc]
+  int B, L, nr, Mc, mlo;
   const int* nvals;
   int nact;
   const double2* mult;   // [L][nact]
   double2* out;
   int64_t s_b, s_n, s_l;
   int mlo_out;
-  const double* MT;      // [2][L][L]
+  const double* MT;      // MW: [2][L][L]
   const float2* MT2;     // the same as float pairs (compensated quadrature)
+  const double* wdiag;   // DH: [nr] ring weights (MT unused)
   int quad;              // 0: skip the quadrature (adjoint of the inverse contraction)
   RecTables T;
 };
@@ -292,14 +295,15 @@ struct WigFwdArgs {
 // C32: the quadrature M^{par} G and the contraction over beta run in compensated float32
 // pairs (comp32.cuh); the weighted columns stay as pairs in shared memory and each recursion
 // value is split with integer operations.  Without C32 every step is native float64.  The
-// Wigner-d recursion is float64 either way.
+// Wigner-d recursion is float64 either way.  On DH sampling the quadrature is diagonal and is
+// applied in float64 as the columns are loaded.
 template <int MB, int LT, bool C32>
 __global__ void k_wig_fwd(WigFwdArgs a) {
   extern __shared__ double smd[];
-  const int L = a.L;
-  double2* Gs = (double2*)smd;                 // [L][MB]
-  double* Ds = (double*)(Gs + (size_t)L * MB); // [LT][L]
-  double* cA = Ds + (size_t)LT * L;
+  const int L = a.L, nr = a.nr;
+  double2* Gs = (double2*)smd;                  // [nr][MB]
+  double* Ds = (double*)(Gs + (size_t)nr * MB); // [LT][nr]
+  double* cA = Ds + (size_t)LT * nr;
   double* cKn = cA + LT;
   double* cKs = cKn + LT;
   double* cC = cKs + LT;
@@ -310,20 +314,25 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
   if (l0 >= L) return;
   const int par = (m + nn) & 1;
   const double* MT = a.MT + (size_t)par * L * L;
-  const double wb = (t < L) ? a.T.wpole[t] : 0.0;
-  const double* cK = (2 * (2 * t + 1) < a.T.n) ? cKn : cKs;
+  const double wb = (t < nr) ? a.T.wpole[t] : 0.0;
+  const double* cK = (2 * (2 * t + 1) < a.T.den) ? cKn : cKs;
+  const bool diag = a.quad && a.wdiag != nullptr;
   for (int map0 = 0; map0 < a.B; map0 += MB) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < L * MB; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nr * MB; idx += blockDim.x) {
       const int tt = idx / MB, mp = idx - tt * MB, bm = map0 + mp;
-      const double2 gv = (bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * L + tt) * a.Mc + mi] : make_double2(0.0, 0.0);
+      double2 gv = (bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * nr + tt) * a.Mc + mi] : make_double2(0.0, 0.0);
+      if (diag) {
+        const double w = a.wdiag[tt];
+        gv = make_double2(gv.x * w, gv.y * w);
+      }
       if (C32) reinterpret_cast<float4*>(Gs)[idx] = split(gv);
       else Gs[idx] = gv;
     }
     __syncthreads();
-    // colatitude quadrature: Gs <- M^{par} Gs
-    if (!a.quad) {
-      // columns enter the beta sum as they are
+    // colatitude quadrature (MW): Gs <- M^{par} Gs
+    if (!a.quad || diag) {
+      // columns enter the beta sum as they are (or were weighted on load)
     } else if (C32) {
       const float2* MT2 = a.MT2 + (size_t)par * L * L;
       const float4* G4 = reinterpret_cast<const float4*>(Gs);
@@ -370,16 +379,16 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
     }
     double v = 0.0, vp = 0.0;
     int q = 0;
-    if (t < L) wigner_seed(a.T, t, l0, m, nn, v, q);
+    if (t < nr) wigner_seed(a.T, t, l0, m, nn, v, q);
     for (int ls = l0; ls < L; ls += LT) {
       const int cnt = min(LT, L - ls);
       __syncthreads();
       for (int i = threadIdx.x; i < cnt; i += blockDim.x) rec_coeffs(ls + i, m, nn, cA[i], cKn[i], cKs[i], cC[i]);
       __syncthreads();
-      if (t < L) {
+      if (t < nr) {
         for (int i = 0; i < cnt; ++i) {
-          if (C32) reinterpret_cast<float2*>(Ds)[i * L + t] = (q == 0) ? split1_bits(v) : make_float2(0.f, 0.f);
-          else Ds[i * L + t] = (q == 0) ? v : 0.0;
+          if (C32) reinterpret_cast<float2*>(Ds)[i * nr + t] = (q == 0) ? split1_bits(v) : make_float2(0.f, 0.f);
+          else Ds[i * nr + t] = (q == 0) ? v : 0.0;
           const double x = fma(cA[i], wb, cK[i]);
           const double vn = fma(x, v, -cC[i] * vp);
           vp = v;
@@ -396,10 +405,10 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
         const int i = idx / MB, mp = idx - i * MB, bm = map0 + mp, l = ls + i;
         double re = 0.0, im = 0.0;
         if (C32) {
-          const float2* drow = reinterpret_cast<const float2*>(Ds) + (size_t)i * L;
+          const float2* drow = reinterpret_cast<const float2*>(Ds) + (size_t)i * nr;
           const float4* G4 = reinterpret_cast<const float4*>(Gs);
           Acc ar{0.f, 0.f}, ai{0.f, 0.f};
-          for (int bb = 0; bb < L; ++bb) {
+          for (int bb = 0; bb < nr; ++bb) {
             const float2 d = drow[bb];
             const float4 gv = G4[bb * MB + mp];
             acc_add(ar, gv.x, gv.y, d.x, d.y);
@@ -408,8 +417,8 @@ __global__ void k_wig_fwd(WigFwdArgs a) {
           re = to_double(ar);
           im = to_double(ai);
         } else {
-          const double* drow = Ds + (size_t)i * L;
-          for (int bb = 0; bb < L; ++bb) {
+          const double* drow = Ds + (size_t)i * nr;
+          for (int bb = 0; bb < nr; ++bb) {
             const double d = drow[bb];
             const double2 gv = Gs[bb * MB + mp];
             re = fma(d, gv.x, re);
@@ -498,6 +507,15 @@ __global__ void k_quad_adj(QuadAdjArgs a) {
   }
 }
 
+// DH: the quadrature is the diagonal of ring weights, its own transpose: G[.][t][.] *= w[t].
+__global__ void k_ring_scale(double2* G, int64_t total, int nr, int Mc, const double* w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = w[(i / Mc) % nr];
+    const double2 v = G[i];
+    G[i] = make_double2(v.x * s, v.y * s);
+  }
+}
+
 RecTables rec_tables(const GridTables& g) {
   RecTables T;
   T.wpole = g.wpole;
@@ -507,6 +525,7 @@ RecTables rec_tables(const GridTables& g) {
   T.spow_e = g.spow_e;
   T.sqrtC = g.sqrtC;
   T.n = g.n;
+  T.den = g.den;
   return T;
 }
 
@@ -518,7 +537,7 @@ int pick_mb(int B, int cap) {
 
 template <int MB>
 cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, bool c32, cudaStream_t st) {
-  dim3 grid(a.Mc, nact, (a.L + kInvThreads - 1) / kInvThreads);
+  dim3 grid(a.Mc, nact, (a.nr + kInvThreads - 1) / kInvThreads);
   if (c32) k_wig_inv<MB, true><<<grid, kInvThreads, 0, st>>>(a);
   else k_wig_inv<MB, false><<<grid, kInvThreads, 0, st>>>(a);
   return cudaGetLastError();
@@ -526,8 +545,8 @@ cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, bool c32, cudaStream_t 
 
 template <int MB, int LT, bool C32>
 cudaError_t launch_fwd_k(const WigFwdArgs& a, int nact, cudaStream_t st) {
-  const int threads = ((a.L + 31) / 32) * 32;
-  const size_t smem = (size_t)a.L * MB * sizeof(double2) + (size_t)LT * a.L * sizeof(double) + 4 * LT * sizeof(double);
+  const int threads = ((a.nr + 31) / 32) * 32;
+  const size_t smem = (size_t)a.nr * MB * sizeof(double2) + (size_t)LT * a.nr * sizeof(double) + 4 * LT * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_wig_fwd<MB, LT, C32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.Mc, nact);
@@ -553,6 +572,7 @@ static DftArgs dft_args(const GridTables& g, const TransformSpec& t, ColumnArgs 
   a.nact = c.nact;
   a.Ng = 2 * t.N - 1;
   a.L = c.L;
+  a.nr = c.nr;
   a.Mc = c.Mc;
   a.mlo = c.mlo;
   a.n = g.n;
@@ -573,7 +593,7 @@ cudaError_t launch_dft_forward(const s2w_plan* P, const GridTables& g, const Tra
   a.pix_sb = pix_sb;
   a.scale = (2.0 * 3.14159265358979323846 / g.n) * t.gscale;
   const size_t smem = (size_t)(3 * g.n + a.Ng * c.Mc) * sizeof(double2);
-  dim3 grid(c.L, c.B);
+  dim3 grid(c.nr, c.B);
   cudaError_t e;
   if (real) {
     e = cudaFuncSetAttribute(k_dft_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -595,7 +615,7 @@ cudaError_t launch_dft_inverse(const s2w_plan* P, const GridTables& g, const Tra
   a.pix_out = pix;
   a.pix_sb = pix_sb;
   const size_t smem = (size_t)(3 * g.n + c.nact * c.Mc) * sizeof(double2);
-  dim3 grid(c.L, c.B);
+  dim3 grid(c.nr, c.B);
   cudaError_t e;
   if (real) {
     e = cudaFuncSetAttribute(k_dft_inv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -623,6 +643,7 @@ cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const 
   a.G = out.G;
   a.B = out.B;
   a.L = out.L;
+  a.nr = out.nr;
   a.Mc = out.Mc;
   a.mlo = out.mlo;
   a.T = rec_tables(g);
@@ -642,6 +663,7 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
   a.G = in.G;
   a.B = in.B;
   a.L = in.L;
+  a.nr = in.nr;
   a.Mc = in.Mc;
   a.mlo = in.mlo;
   a.nvals = t.nvals;
@@ -654,11 +676,13 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
   a.mlo_out = out.mlo;
   a.MT = g.MT;
   a.MT2 = g.MT2;
+  a.wdiag = g.wdiag;
   a.T = rec_tables(g);
   const bool c32 = !P->native64;
   // Compensated blocks use 16-row recursion tiles so that two blocks fit on an SM (one
-  // block's float64 recursion phase overlaps the other's float32 contraction phase).
-  if (in.L <= 256) {
+  // block's float64 recursion phase overlaps the other's float32 contraction phase).  Shapes
+  // follow the ring count (one thread per ring; shared memory grows with it).
+  if (in.nr <= 256) {
     if (c32) {
       switch (pick_mb(in.B, 16)) {
         case 1: return launch_fwd_mb<1, 16>(a, t.nact, c32, st);
@@ -675,7 +699,7 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
       case 8: return launch_fwd_mb<8, 32>(a, t.nact, c32, st);
       default: return launch_fwd_mb<16, 32>(a, t.nact, c32, st);
     }
-  } else if (in.L <= 512) {
+  } else if (in.nr <= 512) {
     switch (pick_mb(in.B, 8)) {
       case 1: return launch_fwd_mb<1, 32>(a, t.nact, c32, st);
       case 2: return launch_fwd_mb<2, 32>(a, t.nact, c32, st);
@@ -693,6 +717,12 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
 
 cudaError_t launch_quad_adjoint(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
                                 cudaStream_t st) {
+  if (g.wdiag != nullptr) {
+    const int64_t total = (int64_t)c.B * c.nact * c.nr * c.Mc;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    k_ring_scale<<<blocks, 256, 0, st>>>(c.G, total, c.nr, c.Mc, g.wdiag);
+    return cudaGetLastError();
+  }
   QuadAdjArgs a;
   a.G = c.G;
   a.B = c.B;

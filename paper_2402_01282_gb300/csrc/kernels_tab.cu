@@ -4,10 +4,11 @@
 // (hi + lo, ~48 bits); the contractions are compensated-float32 GEMMs (comp32.cuh).
 //
 //  * k_tab_build   T_inv[(m,n)][l - l0a][beta] (l0a = max(|m|,|n|) rounded down to a multiple of 8) = d^l_mn(beta_b): one thread per beta runs the
-//                  recursion over l (wigner_rec.cuh), zero outside l0 <= l < L, beta < L.
+//                  recursion over l (wigner_rec.cuh), zero outside l0 <= l < L, beta < nr (rings).
 //  * k_tab_fold    T_fwd[(m,n)][beta'][l - l0a] = sum_beta M^{par(m+n)}[beta][beta'] d^l_mn(beta):
 //                  the colatitude quadrature of the forward transforms folded into the table
-//                  (F_l = sum_beta d^l (M G)(beta) = sum_beta' (M^T d^l)(beta') G(beta')), float64.
+//                  (F_l = sum_beta d^l (M G)(beta) = sum_beta' (M^T d^l)(beta') G(beta')), float64;
+//                  on DH sampling M is the diagonal of ring weights, T_fwd = w(beta') d^l_mn(beta').
 //  * k_tab_inv     G[b][n][beta][m] = sum_l T_inv[l][beta] (mult_inv f)(b, l, m)
 //  * k_tab_fwd     out(b, l, m) += mult_fwd[l][n] sum_beta' T_fwd[beta'][l] G[b][n][beta'][m]
 // Both GEMM kernels: one block per (64-row tile, m, n), 128 threads, a 4 x 4 micro-tile per
@@ -34,7 +35,7 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
 struct TabBuildArgs {
   RecTables T;
   const int* nvals;
-  int nact, L, Mc, mlo, Lp;
+  int nact, L, nr, Mc, mlo, Lp;
   const int64_t* off_inv;
   const int* kp;
   float2* inv;
@@ -51,12 +52,12 @@ __global__ void k_tab_build(TabBuildArgs a) {
   float2* out = a.inv + a.off_inv[idx] + b;
   for (int ll = 0; ll < l0 - l0a; ++ll) out[(int64_t)ll * a.Lp] = make_float2(0.f, 0.f);
   for (int ll = L - l0a; ll < kp; ++ll) out[(int64_t)ll * a.Lp] = make_float2(0.f, 0.f);
-  if (b >= L) {
+  if (b >= a.nr) {
     for (int ll = l0 - l0a; ll < L - l0a; ++ll) out[(int64_t)ll * a.Lp] = make_float2(0.f, 0.f);
     return;
   }
   const double wb = a.T.wpole[b];
-  const bool north = 2 * (2 * b + 1) < a.T.n;
+  const bool north = 2 * (2 * b + 1) < a.T.den;
   double v = 0.0, vp = 0.0;
   int q = 0;
   wigner_seed(a.T, b, l0, m, nn, v, q);
@@ -78,13 +79,14 @@ __global__ void k_tab_build(TabBuildArgs a) {
 
 struct TabFoldArgs {
   const int* nvals;
-  int nact, L, Mc, mlo, Lp, Lk;
+  int nact, L, nr, Mc, mlo, Lp, Lk;
   const int64_t* off_inv;
   const int64_t* off_fwd;
   const int* kp;
   const float2* inv;
   float2* fwd;
-  const double* MR;   // [2][L][L] row-major M[par][t][t']
+  const double* MR;      // MW: [2][L][L] row-major M[par][t][t']
+  const double* wdiag;   // DH: [nr] ring weights (MR unused)
 };
 
 constexpr int kFoldL = 32, kFoldB = 64, kFoldThreads = 256;
@@ -97,11 +99,25 @@ __global__ void __launch_bounds__(kFoldThreads) k_tab_fold(TabFoldArgs a) {
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
   if (lc * kFoldL >= kp) return;
   const int m = a.mlo + mi, nn = a.nvals[ni], L = a.L;
-  const int par = (m + nn) & 1;
-  const double* M = a.MR + (size_t)par * L * L;
   const float2* Tin = a.inv + a.off_inv[idx];
   float2* Tout = a.fwd + a.off_fwd[idx];
   const int bp = bt * kFoldThreads + threadIdx.x;
+  if (a.wdiag != nullptr) {   // DH: T_fwd[beta'][l] = w(beta') d^l(beta')
+    if (bp < a.Lk) {
+      const double w = (bp < a.nr) ? a.wdiag[bp] : 0.0;
+      for (int j = 0; j < kFoldL; ++j) {
+        float2 r = make_float2(0.f, 0.f);
+        if (bp < a.nr) {
+          const float2 p = Tin[(int64_t)(lc * kFoldL + j) * a.Lp + bp];
+          r = split1(((double)p.x + (double)p.y) * w);
+        }
+        Tout[(int64_t)bp * kp + lc * kFoldL + j] = r;
+      }
+    }
+    return;
+  }
+  const int par = (m + nn) & 1;
+  const double* M = a.MR + (size_t)par * L * L;
   double acc[kFoldL];
 #pragma unroll
   for (int j = 0; j < kFoldL; ++j) acc[j] = 0.0;
@@ -200,7 +216,7 @@ struct TabInvArgs {
   int Lp;
   const float2* tab;
   double2* G;
-  int B, L, Mc, mlo;
+  int B, L, nr, Mc, mlo;
 };
 
 // Double-buffered: the table tile of chunk c+1 is copied asynchronously and its data
@@ -209,15 +225,15 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
   __shared__ __align__(16) float4 As[2][kK][kRows / 2];   // [k][row] pairs
   __shared__ __align__(16) float4 Bs[2][kK][kMaps];       // [k][map] (re_hi, re_lo, im_hi, im_lo)
   const int rt = blockIdx.x, mi = blockIdx.y, ni = blockIdx.z;
-  const int L = a.L, row0 = rt * kRows;
-  if (row0 >= L) return;
+  const int L = a.L, nr = a.nr, row0 = rt * kRows;
+  if (row0 >= nr) return;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
   const int nch = kp == 0 ? 0 : (L - l0a + kK - 1) / kK;
   const float2* T = a.tab + a.off[idx];
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
-  const bool warp_live = row0 + 16 * (tid >> 5) < L;   // a warp owns 16 rows beta
+  const bool warp_live = row0 + 16 * (tid >> 5) < nr;   // a warp owns 16 rows beta
   auto load_b = [&](int c, int map0, double2 (&f)[kBPer]) {
 #pragma unroll
     for (int q = 0; q < kBPer; ++q) {
@@ -267,13 +283,13 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int beta = row0 + 4 * ty + r;
-      if (beta >= L) continue;
+      if (beta >= nr) continue;
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int bm = map0 + 2 * tx + p;
         if (bm < a.B) {
           const double x = to_double(acc[r][2 * p]), y = to_double(acc[r][2 * p + 1]);
-          a.G[(((int64_t)bm * a.nact + ni) * L + beta) * a.Mc + mi] =
+          a.G[(((int64_t)bm * a.nact + ni) * nr + beta) * a.Mc + mi] =
               make_double2(fma(x, a.phase.x, -y * a.phase.y), fma(x, a.phase.y, y * a.phase.x));
         }
       }
@@ -283,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_tab_inv(TabInvArgs a) {
 
 struct TabFwdArgs {
   const double2* G;
-  int B, L, Mc, mlo;
+  int B, L, nr, Mc, mlo;
   const int* nvals;
   int nact;
   const double2* mult;
@@ -303,9 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
   const int idx = mi * a.nact + ni, kp = a.kp[idx];
   const int row0 = rt * kRows;
   if (row0 >= kp) return;
-  const int L = a.L, m = a.mlo + mi, nn = a.nvals[ni];
+  const int L = a.L, nr = a.nr, m = a.mlo + mi, nn = a.nvals[ni];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
-  const int nch = (L + kK - 1) / kK;
+  const int nch = (nr + kK - 1) / kK;   // reduction over the rings beta'
   const float2* T = a.tab + a.off[idx];
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
   // a warp owns 16 rows l; it skips the products when none of them lies in [l0, L)
@@ -316,8 +332,8 @@ __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
     for (int q = 0; q < kBPer; ++q) {
       const int i = tid + q * kThreads, k = i / kMaps, mp = i - k * kMaps;
       const int beta = c * kK + k, bm = map0 + mp;
-      f[q] = (beta < L && bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * L + beta) * a.Mc + mi]
-                                    : make_double2(0.0, 0.0);
+      f[q] = (beta < nr && bm < a.B) ? a.G[(((int64_t)bm * a.nact + ni) * nr + beta) * a.Mc + mi]
+                                     : make_double2(0.0, 0.0);
     }
   };
   for (int map0 = 0; map0 < a.B; map0 += kMaps) {
@@ -345,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_tab_fwd(TabFwdArgs a) {
       }
       __syncthreads();
       if (warp_live) {
-        const int kend = min(kK, L - c * kK);
+        const int kend = min(kK, nr - c * kK);
 #pragma unroll 4
         for (int k = 0; k < kend; ++k) mac_tile(acc, As[buf][k], Bs[buf][k], ty, tx);
       }
@@ -379,6 +395,7 @@ RecTables rec_tables_tab(const GridTables& g) {
   T.spow_e = g.spow_e;
   T.sqrtC = g.sqrtC;
   T.n = g.n;
+  T.den = g.den;
   return T;
 }
 
@@ -391,6 +408,7 @@ cudaError_t launch_tab_build(const GridTables& g, const TransformSpec& t, const 
   a.nvals = t.nvals;
   a.nact = t.nact;
   a.L = t.L;
+  a.nr = g.nr;
   a.Mc = Mc;
   a.mlo = mlo;
   a.Lp = tab.Lp;
@@ -405,6 +423,7 @@ cudaError_t launch_tab_build(const GridTables& g, const TransformSpec& t, const 
   f.nvals = t.nvals;
   f.nact = t.nact;
   f.L = t.L;
+  f.nr = g.nr;
   f.Mc = Mc;
   f.mlo = mlo;
   f.Lp = tab.Lp;
@@ -415,6 +434,7 @@ cudaError_t launch_tab_build(const GridTables& g, const TransformSpec& t, const 
   f.inv = tab.inv;
   f.fwd = tab.fwd;
   f.MR = g.MR;
+  f.wdiag = g.wdiag;
   dim3 fgrid((tab.kpmax / kFoldL) * ((tab.Lk + kFoldThreads - 1) / kFoldThreads), Mc, t.nact);
   k_tab_fold<<<fgrid, kFoldThreads, 0, st>>>(f);
   return cudaGetLastError();
@@ -441,6 +461,7 @@ cudaError_t launch_tab_inverse(const GridTables& g, const TransformSpec& t, Coef
   a.G = out.G;
   a.B = out.B;
   a.L = out.L;
+  a.nr = out.nr;
   a.Mc = out.Mc;
   a.mlo = out.mlo;
   dim3 grid(tab.Lp / kRows, out.Mc, t.nact);
@@ -456,6 +477,7 @@ cudaError_t launch_tab_forward(const GridTables& g, const TransformSpec& t, Colu
   a.G = in.G;
   a.B = in.B;
   a.L = in.L;
+  a.nr = in.nr;
   a.Mc = in.Mc;
   a.mlo = in.mlo;
   a.nvals = t.nvals;

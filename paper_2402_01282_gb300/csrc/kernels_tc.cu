@@ -107,7 +107,7 @@ __device__ __forceinline__ float pow2_scale_f(float mx) {
 // ------------------------------------------------------------------ table packing
 struct PackArgs {
   const int* nvals;
-  int nact, L, Mc, mlo;
+  int nact, L, nr, Mc, mlo;
   const int64_t *toff_i, *toff_f;   // float-pair tables (kernels_tab.cu layout)
   const int* tkp;
   int tLp, tLk;
@@ -133,7 +133,7 @@ __global__ void k_tc_pack(PackArgs a) {
   for (int64_t e = threadIdx.x; e < (int64_t)a.Lb * kli; e += blockDim.x) {
     const int beta = (int)(e / kli), ll = (int)(e - (int64_t)beta * kli), l = l0a + ll;
     double v = 0.0;
-    if (beta < L && l >= l0 && l < L && ll < kp) {
+    if (beta < a.nr && l >= l0 && l < L && ll < kp) {
       const float2 p = Ti[(int64_t)ll * a.tLp + beta];
       v = ((double)p.x + (double)p.y) * kInvScale;
     }
@@ -144,7 +144,7 @@ __global__ void k_tc_pack(PackArgs a) {
   for (int64_t e = threadIdx.x; e < (int64_t)klf * a.Lk; e += blockDim.x) {
     const int ll = (int)(e / a.Lk), bp = (int)(e - (int64_t)ll * a.Lk), l = l0a + ll;
     double v = 0.0;
-    if (bp < L && l >= l0 && l < L && ll < kp) {
+    if (bp < a.nr && l >= l0 && l < L && ll < kp) {
       const float2 p = Tf[(int64_t)bp * kp + ll];
       v = ((double)p.x + (double)p.y) * kFwdScale;
     }
@@ -156,7 +156,7 @@ __global__ void k_tc_pack(PackArgs a) {
 // ------------------------------------------------------------------ operand preparation
 struct PrepArgs {
   const int* nvals;
-  int nact, L, Mc, mlo, B;
+  int nact, L, nr, Mc, mlo, B;
   const int* kl;          // inverse: K extent per tile (0 = empty); forward: row extent (0 = empty)
   const int64_t* off_i;   // inverse table offsets (operand offset = off_i / Lb * 32)
   int Lb, Lk;
@@ -176,8 +176,8 @@ __device__ __forceinline__ float prep_value(const PrepArgs& a, int mi, int ni, i
   const int bm = map0 + (j >> 1);
   if (bm >= a.B) return 0.f;
   if (FWD) {
-    if (k >= a.L) return 0.f;
-    const double2 g = a.G[(((int64_t)bm * a.nact + ni) * a.L + k) * a.Mc + mi];
+    if (k >= a.nr) return 0.f;
+    const double2 g = a.G[(((int64_t)bm * a.nact + ni) * a.nr + k) * a.Mc + mi];
     return to_f((j & 1) ? g.y : g.x);
   }
   const int l = l0a + k;
@@ -224,7 +224,7 @@ struct GemmArgs {
   const float* scale;
   int64_t qstride;
   const int* nvals;
-  int nact, L, Lb, Lk, Mc, mlo, B;
+  int nact, L, nr, Lb, Lk, Mc, mlo, B;
   double2* G;             // inverse output
   const double2* mult;    // forward multiplier
   double2* out;           // forward output (accumulated)
@@ -240,14 +240,14 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
   __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
   __shared__ uint32_t tbase;
   const int rt = blockIdx.x, mi = blockIdx.y, ni = blockIdx.z, idx = mi * a.nact + ni;
-  const int kl = a.kl[idx], L = a.L;
+  const int kl = a.kl[idx], L = a.L, nr = a.nr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
   if (!FWD && kl == 0) {   // l0 >= L: this (m, n) column of every map is zero
     for (int e = tid; e < a.B * 128; e += kTcThreads) {
       const int b = e >> 7, beta = rt * 128 + (e & 127);
-      if (beta < L) a.G[(((int64_t)b * a.nact + ni) * L + beta) * a.Mc + mi] = make_double2(0.0, 0.0);
+      if (beta < nr) a.G[(((int64_t)b * a.nact + ni) * nr + beta) * a.Mc + mi] = make_double2(0.0, 0.0);
     }
     return;
   }
@@ -327,12 +327,12 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
     const float un = 1.f / (sc * (float)(FWD ? kFwdScale : kInvScale));   // a power of two
     const int row = rt * 128 + warp * 32 + lane;
     if (!FWD) {
-      if (row < L) {
+      if (row < nr) {
 #pragma unroll
         for (int p = 0; p < kTcN / 2; ++p) {
           const int bm = map0 + p;
           if (bm < a.B)
-            a.G[(((int64_t)bm * a.nact + ni) * L + row) * a.Mc + mi] = make_double2(f2d(v[2 * p] * un), f2d(v[2 * p + 1] * un));
+            a.G[(((int64_t)bm * a.nact + ni) * nr + row) * a.Mc + mi] = make_double2(f2d(v[2 * p] * un), f2d(v[2 * p + 1] * un));
         }
       }
     } else {
@@ -360,11 +360,12 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
 
 constexpr size_t kGemmSmem = 2 * (2 * kTileElems + 2 * kOpElems) * sizeof(uint16_t);   // 80 KB
 
-PrepArgs prep_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab, int Mc, int mlo, int B) {
+PrepArgs prep_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab, int nr, int Mc, int mlo, int B) {
   PrepArgs a{};
   a.nvals = t.nvals;
   a.nact = t.nact;
   a.L = t.L;
+  a.nr = nr;
   a.Mc = Mc;
   a.mlo = mlo;
   a.B = B;
@@ -377,8 +378,10 @@ PrepArgs prep_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab
   return a;
 }
 
-GemmArgs gemm_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab, int Mc, int mlo, int B, bool fp16) {
+GemmArgs gemm_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab, int nr, int Mc, int mlo, int B,
+                   bool fp16) {
   GemmArgs a{};
+  a.nr = nr;
   a.off_i = tab.off_i;
   a.B_hi = P->tc_b_hi;
   a.B_lo = P->tc_b_lo;
@@ -398,12 +401,13 @@ GemmArgs gemm_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab
 
 }  // namespace
 
-cudaError_t launch_tc_pack(const TransformSpec& t, const TcTable& tab, const TabTable& src, int Mc, int mlo, bool fp16,
-                           cudaStream_t st) {
+cudaError_t launch_tc_pack(const TransformSpec& t, const TcTable& tab, const TabTable& src, int nr, int Mc, int mlo,
+                           bool fp16, cudaStream_t st) {
   PackArgs a;
   a.nvals = t.nvals;
   a.nact = t.nact;
   a.L = t.L;
+  a.nr = nr;
   a.Mc = Mc;
   a.mlo = mlo;
   a.toff_i = src.off_inv;
@@ -435,7 +439,7 @@ cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const Tran
   const TcTable& tab = *t.tc;
   const bool fp16 = P->p.precision == S2W_FP32_SPLIT;
   const int nq = (out.B + kTcN / 2 - 1) / (kTcN / 2);
-  PrepArgs pa = prep_args(P, t, tab, out.Mc, out.mlo, out.B);
+  PrepArgs pa = prep_args(P, t, tab, out.nr, out.Mc, out.mlo, out.B);
   pa.kl = tab.kli;
   pa.coef = in.coef;
   pa.s_b = in.s_b;
@@ -449,7 +453,7 @@ cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const Tran
   else k_tcp<false, false><<<pg, 256, 0, st>>>(pa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  GemmArgs a = gemm_args(P, t, tab, out.Mc, out.mlo, out.B, fp16);
+  GemmArgs a = gemm_args(P, t, tab, out.nr, out.Mc, out.mlo, out.B, fp16);
   a.A_hi = tab.inv_hi;
   a.A_lo = tab.inv_lo;
   a.off = tab.off_i;
@@ -469,7 +473,7 @@ cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const Tran
   const TcTable& tab = *t.tc;
   const bool fp16 = P->p.precision == S2W_FP32_SPLIT;
   const int nq = (in.B + kTcN / 2 - 1) / (kTcN / 2);
-  PrepArgs pa = prep_args(P, t, tab, in.Mc, in.mlo, in.B);
+  PrepArgs pa = prep_args(P, t, tab, in.nr, in.Mc, in.mlo, in.B);
   pa.kl = tab.klf;
   pa.G = in.G;
   pa.qstride = tab.op_f;
@@ -478,7 +482,7 @@ cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const Tran
   else k_tcp<true, false><<<pg, 256, 0, st>>>(pa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  GemmArgs a = gemm_args(P, t, tab, in.Mc, in.mlo, in.B, fp16);
+  GemmArgs a = gemm_args(P, t, tab, in.nr, in.Mc, in.mlo, in.B, fp16);
   a.A_hi = tab.fwd_hi;
   a.A_lo = tab.fwd_lo;
   a.off = tab.off_f;

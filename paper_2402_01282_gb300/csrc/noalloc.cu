@@ -24,7 +24,7 @@
 
 namespace {
 
-// 16 MiB: B * L * Mc complex float64 columns, enough for 16 real maps at L = 256.
+// 16 MiB: B * rings * Mc complex float64 columns, enough for 16 real MW maps at L = 256.
 constexpr long long kStaticColsElems = 1 << 20;
 static __device__ __align__(256) double2 g_static_cols[kStaticColsElems];
 
@@ -41,9 +41,9 @@ extern "C" s2w_status s2w_sht_inverse_static(const s2w_plan* cP, const void* flm
   if (flm == nullptr || f == nullptr) return record_error(S2W_EINVAL, "flm or f is NULL");
   if ((reinterpret_cast<uintptr_t>(flm) % 16) != 0 || (reinterpret_cast<uintptr_t>(f) % (P->real ? 8 : 16)) != 0)
     return record_error(S2W_EINVAL, "flm or f is misaligned");
-  const long long need = (long long)P->p.batch * P->p.L * P->Mc;
+  const long long need = (long long)P->p.batch * P->nr * P->Mc;
   if (need > kStaticColsElems)
-    return record_error(S2W_EINVAL, "s2w_sht_inverse_static: batch * L * Mc = " + std::to_string(need) +
+    return record_error(S2W_EINVAL, "s2w_sht_inverse_static: batch * rings * Mc = " + std::to_string(need) +
                                         " column elements exceeds the fixed scratch of " +
                                         std::to_string(kStaticColsElems) + " (16 MiB)");
   int dev = 0;
@@ -77,6 +77,7 @@ extern "C" s2w_status s2w_sht_inverse_static(const s2w_plan* cP, const void* flm
   c.B = P->p.batch;
   c.nact = t.nact;
   c.L = t.L;
+  c.nr = P->nr;
   c.Mc = P->Mc;
   c.mlo = P->mlo;
   e = launch_wigner_inverse(P, g, t, in, c, st);

@@ -1,7 +1,8 @@
 // Host-side construction of a transform plan: parameter validation, the wavelet
 // dictionary (App. A), multiresolution band-limits (Sec. 3.3), and the float64
-// tables the kernels read (MW grids, Wigner-d seed powers, the colatitude
-// quadrature matrices and DFT twiddles).  Everything here runs once per plan.
+// tables the kernels read (MW or DH grids, Wigner-d seed powers, the colatitude
+// quadrature: MW matrices or DH ring weights, and DFT twiddles).  Everything here runs
+// once per plan.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -125,28 +126,55 @@ void factorise(int n, int& n1, int& n2) {
     }
 }
 
+// Driscoll-Healy ring weights on the 2L midpoint rings theta_t = pi (2t+1)/(4L):
+//   w_t = (2/L) sin(theta_t) sum_{k<L} sin((2k+1) theta_t)/(2k+1),
+// the unique weights that integrate cos(j theta) sin(theta) over [0, pi] exactly for j < 2L
+// (the Driscoll-Healy quadrature; Fejer's first rule in x = cos theta).  Every sine has an
+// integer multiple of pi/(4L) as argument, reduced exactly before evaluation.
+std::vector<double> dh_weights(int L) {
+  const long den = 4L * L;   // angles pi a/den
+  auto sin_pi = [&](long a) {
+    a %= 2 * den;
+    if (a < 0) a += 2 * den;
+    const double sg = (a >= den) ? -1.0 : 1.0;
+    if (a >= den) a -= den;
+    if (2 * a > den) a = den - a;   // sin(pi - x) = sin x
+    return sg * std::sin(kPi * double(a) / double(den));
+  };
+  std::vector<double> w(2 * L);
+  for (int t = 0; t < 2 * L; ++t) {
+    long double acc = 0.0L;
+    for (int k = 0; k < L; ++k) acc += (long double)sin_pi((long)(2 * k + 1) * (2 * t + 1)) / (long double)(2 * k + 1);
+    w[t] = (double)((2.0L / (long double)L) * (long double)sin_pi(2 * t + 1) * acc);
+  }
+  return w;
+}
+
 s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::string& err) {
+  const bool dh = P->p.sampling == S2W_SAMPLING_DH;
   g.L = L;
   g.n = 2 * L - 1;
+  g.nr = rings_of(P->p.sampling, L);
+  g.den = dh ? 4 * L : g.n;
   factorise(g.n, g.n1, g.n2);
-  const int n = g.n;
-  std::vector<double> wpole(L), cm((size_t)L * n), sm((size_t)L * n), sc((size_t)L * n, 0.0);
-  std::vector<int> ce((size_t)L * n), se((size_t)L * n);
-  for (int b = 0; b < L; ++b) {
-    // half angle beta_b/2 = pi num/(2n); the smaller of sin and cos is evaluated through an
+  const int n = g.n, nr = g.nr, den = g.den;
+  std::vector<double> wpole(nr), cm((size_t)nr * n), sm((size_t)nr * n), sc((size_t)L * n, 0.0);
+  std::vector<int> ce((size_t)nr * n), se((size_t)nr * n);
+  for (int b = 0; b < nr; ++b) {
+    // half angle beta_b/2 = pi num/(2 den); the smaller of sin and cos is evaluated through an
     // exact complementary argument so both keep full relative precision near the poles.
-    const long num = 2 * b + 1, cnum = n - num;   // pi/2 - beta_b/2 = pi cnum/(2n)
+    const long num = 2 * b + 1, cnum = den - num;   // pi/2 - beta_b/2 = pi cnum/(2 den)
     double ch, sh;
-    if (2 * num <= n) {
-      sh = std::sin(0.5 * kPi * double(num) / double(n));
-      ch = std::cos(0.5 * kPi * double(num) / double(n));
+    if (2 * num <= den) {
+      sh = std::sin(0.5 * kPi * double(num) / double(den));
+      ch = std::cos(0.5 * kPi * double(num) / double(den));
     } else {
-      ch = (cnum == 0) ? 0.0 : std::sin(0.5 * kPi * double(cnum) / double(n));
-      sh = (cnum == 0) ? 1.0 : std::cos(0.5 * kPi * double(cnum) / double(n));
+      ch = (cnum == 0) ? 0.0 : std::sin(0.5 * kPi * double(cnum) / double(den));
+      sh = (cnum == 0) ? 1.0 : std::cos(0.5 * kPi * double(cnum) / double(den));
     }
     // recursion weight: -(1 - cos beta) = -2 sin^2(beta/2) on the northern half,
     // (1 + cos beta) = 2 cos^2(beta/2) on the southern half (see rec_coeffs).
-    wpole[b] = (2 * num < n) ? -2.0 * sh * sh : 2.0 * ch * ch;
+    wpole[b] = (2 * num < den) ? -2.0 * sh * sh : 2.0 * ch * ch;
     // powers as (mantissa in [0.5,1), exponent); zero base gives exact zeros.
     double vm = 0.5, sv = 0.5;
     int ve = 1, svx = 1;
@@ -170,12 +198,6 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
       sc[(size_t)l * n + k] = v;
     }
   }
-  std::vector<double> MT((size_t)2 * L * L), M;
-  for (int par = 0; par < 2; ++par) {
-    quad_matrix(L, par == 0 ? 1 : -1, M);
-    for (int t = 0; t < L; ++t)
-      for (int tp = 0; tp < L; ++tp) MT[(size_t)par * L * L + (size_t)tp * L + t] = M[(size_t)t * L + tp];
-  }
   std::vector<double2> tw(n);
   std::vector<float4> tw4(n);
   for (int e = 0; e < n; ++e) {
@@ -189,21 +211,32 @@ s2w_status build_grid(s2w_plan* P, int L, cudaStream_t st, GridTables& g, std::s
   S2W_TRY(upload(P, sm, &g.spow_m, st, err));
   S2W_TRY(upload(P, se, &g.spow_e, st, err));
   S2W_TRY(upload(P, sc, &g.sqrtC, st, err));
-  std::vector<float2> MT2(MT.size()), MR2(MT.size());
-  std::vector<double> MR(MT.size());
-  for (int par = 0; par < 2; ++par)
-    for (int t = 0; t < L; ++t)
-      for (int tp = 0; tp < L; ++tp) MR[(size_t)par * L * L + (size_t)t * L + tp] = MT[(size_t)par * L * L + (size_t)tp * L + t];
-  for (size_t i = 0; i < MT.size(); ++i) {
-    float h = (float)MT[i];
-    MT2[i] = make_float2(h, (float)(MT[i] - (double)h));
-    h = (float)MR[i];
-    MR2[i] = make_float2(h, (float)(MR[i] - (double)h));
+  if (dh) {
+    S2W_TRY(upload(P, dh_weights(L), &g.wdiag, st, err));
+  } else {
+    std::vector<double> MT((size_t)2 * L * L), M;
+    for (int par = 0; par < 2; ++par) {
+      quad_matrix(L, par == 0 ? 1 : -1, M);
+      for (int t = 0; t < L; ++t)
+        for (int tp = 0; tp < L; ++tp) MT[(size_t)par * L * L + (size_t)tp * L + t] = M[(size_t)t * L + tp];
+    }
+    std::vector<float2> MT2(MT.size()), MR2(MT.size());
+    std::vector<double> MR(MT.size());
+    for (int par = 0; par < 2; ++par)
+      for (int t = 0; t < L; ++t)
+        for (int tp = 0; tp < L; ++tp)
+          MR[(size_t)par * L * L + (size_t)t * L + tp] = MT[(size_t)par * L * L + (size_t)tp * L + t];
+    for (size_t i = 0; i < MT.size(); ++i) {
+      float h = (float)MT[i];
+      MT2[i] = make_float2(h, (float)(MT[i] - (double)h));
+      h = (float)MR[i];
+      MR2[i] = make_float2(h, (float)(MR[i] - (double)h));
+    }
+    S2W_TRY(upload(P, MT, &g.MT, st, err));
+    S2W_TRY(upload(P, MT2, &g.MT2, st, err));
+    S2W_TRY(upload(P, MR, &g.MR, st, err));
+    S2W_TRY(upload(P, MR2, &g.MR2, st, err));
   }
-  S2W_TRY(upload(P, MT, &g.MT, st, err));
-  S2W_TRY(upload(P, MT2, &g.MT2, st, err));
-  S2W_TRY(upload(P, MR, &g.MR, st, err));
-  S2W_TRY(upload(P, MR2, &g.MR2, st, err));
   S2W_TRY(upload(P, tw, &g.tw, st, err));
   S2W_TRY(upload(P, tw4, &g.tw4, st, err));
   return S2W_OK;
@@ -303,10 +336,11 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
       continue;
     }
     const int L = t->L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
+    const int nr = rings_of(P->p.sampling, L);
     TcTable* tab = new TcTable();
     P->tc_tables.push_back(tab);
-    tab->Lb = ((L + 127) / 128) * 128;
-    tab->Lk = ((L + 63) / 64) * 64;
+    tab->Lb = ((nr + 127) / 128) * 128;
+    tab->Lk = ((nr + 63) / 64) * 64;
     std::vector<int64_t> oi((size_t)Mc * t->nact, 0), of((size_t)Mc * t->nact, 0);
     std::vector<int> ki((size_t)Mc * t->nact, 0), kf((size_t)Mc * t->nact, 0);
     int64_t ri = 0, rf = 0;
@@ -340,7 +374,7 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     const size_t mark = P->owned.size();
     TabTable tmp;
     S2W_TRY(make_tab(P, *t, &tmp, st, err));
-    if (launch_tc_pack(*t, *tab, tmp, Mc, mlo, fp16, st) != cudaSuccess) {
+    if (launch_tc_pack(*t, *tab, tmp, nr, Mc, mlo, fp16, st) != cudaSuccess) {
       err = "tensor-core table packing failed to launch";
       return S2W_ECUDA;
     }
@@ -363,8 +397,8 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
 s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStream_t st, std::string& err) {
   const GridTables& g = P->grids[t.grid];
   const int L = t.L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
-  tab->Lp = ((L + 63) / 64) * 64;
-  tab->Lk = ((L + 31) / 32) * 32;
+  tab->Lp = ((g.nr + 63) / 64) * 64;
+  tab->Lk = ((g.nr + 31) / 32) * 32;
   std::vector<int64_t> oi((size_t)Mc * t.nact, 0), of((size_t)Mc * t.nact, 0);
   std::vector<int> kp((size_t)Mc * t.nact, 0);
   int64_t ri = 0, rf = 0;
@@ -437,6 +471,11 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     return S2W_EUNSUPPORTED;
   }
   if (p.precompute != 0 && p.precompute != 1) { err = "precompute must be 0 or 1"; return S2W_EINVAL; }
+  if (p.sampling != S2W_SAMPLING_MW && p.sampling != S2W_SAMPLING_DH) { err = "unknown sampling"; return S2W_EINVAL; }
+  if (p.sampling == S2W_SAMPLING_DH && p.L > 512) {
+    err = "Driscoll-Healy sampling supports L <= 512 in this build (2L rings, one thread per ring)";
+    return S2W_EUNSUPPORTED;
+  }
   if (p.precompute == 1 && p.precision == S2W_FP64_NATIVE) {
     err = "the plain float64 path computes the Wigner-d functions on the fly (precompute = 0)";
     return S2W_EUNSUPPORTED;
@@ -461,11 +500,14 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     P->Lj.push_back(Lj);
     P->Nj.push_back(std::min(p.N, Lj));
   }
-  P->map_elems = (int64_t)p.L * (2 * p.L - 1);
-  P->scal_elems = (int64_t)P->L_phi * (2 * P->L_phi - 1);
+  const int smp = p.sampling;
+  P->nr = rings_of(smp, p.L);
+  P->map_elems = (int64_t)P->nr * (2 * p.L - 1);
+  P->scal_elems = (int64_t)rings_of(smp, P->L_phi) * (2 * P->L_phi - 1);
   P->wav_off.assign(1, 0);
   for (int s = 0; s < P->nscales; ++s)
-    P->wav_off.push_back(P->wav_off.back() + (int64_t)(2 * P->Nj[s] - 1) * P->Lj[s] * (2 * P->Lj[s] - 1));
+    P->wav_off.push_back(P->wav_off.back() +
+                         (int64_t)(2 * P->Nj[s] - 1) * rings_of(smp, P->Lj[s]) * (2 * P->Lj[s] - 1));
   P->wav_elems = P->wav_off.back();
 
   // grids for every distinct band-limit
@@ -536,10 +578,10 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
 
   // workspaces
   const int64_t B = p.batch;
-  int64_t gmax = B * (int64_t)L * P->Mc;
+  int64_t gmax = B * (int64_t)P->nr * P->Mc;
   for (int sc = 0; sc < P->nscales; ++sc) {
     int64_t Mcj = P->real ? P->Lj[sc] : 2 * P->Lj[sc] - 1;
-    gmax = std::max(gmax, B * (2 * P->Nj[sc] - 1) * (int64_t)P->Lj[sc] * Mcj);
+    gmax = std::max(gmax, B * (2 * P->Nj[sc] - 1) * (int64_t)rings_of(smp, P->Lj[sc]) * Mcj);
   }
   P->g_ws_elems = gmax;
   void* q = nullptr;

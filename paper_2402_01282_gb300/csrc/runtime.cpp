@@ -68,7 +68,8 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
   for (TransformSpec& t : P->wav_t) specs.push_back(&t);
   // pixel scratch for the largest transform (zeroed; the timing does not depend on the values)
   int64_t pix = 0;
-  for (TransformSpec* t : specs) pix = std::max<int64_t>(pix, (int64_t)(2 * t->N - 1) * t->L * (2 * t->L - 1));
+  for (TransformSpec* t : specs)
+    pix = std::max<int64_t>(pix, (int64_t)(2 * t->N - 1) * rings_of(P->p.sampling, t->L) * (2 * t->L - 1));
   void* buf = nullptr;
   const size_t eb = P->real ? sizeof(double) : sizeof(double2);
   if (cudaMalloc(&buf, (size_t)P->p.batch * pix * eb) != cudaSuccess) {
@@ -91,9 +92,10 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     c.B = P->p.batch;
     c.nact = t->nact;
     c.L = t->L;
+    c.nr = g.nr;
     c.Mc = P->real ? t->L : 2 * t->L - 1;
     c.mlo = P->real ? 0 : -(t->L - 1);
-    const int64_t pix_sb = (int64_t)(2 * t->N - 1) * t->L * (2 * t->L - 1);
+    const int64_t pix_sb = (int64_t)(2 * t->N - 1) * g.nr * (2 * t->L - 1);
     const bool plain = t->tc != nullptr;
     float best = 1e30f;
     int pick = t->dft_threads_fwd;

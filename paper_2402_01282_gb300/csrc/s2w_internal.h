@@ -11,22 +11,31 @@
 
 namespace s2w {
 
-// Tables for one MW band-limit L (shared by every transform run at that L).
-// Device pointers; rows are padded to the row lengths given.
+// Number of colatitude rings of the grid at band-limit L: L on McEwen-Wiaux sampling
+// (theta_t = pi (2t+1)/(2L-1)), 2L on Driscoll-Healy sampling (theta_t = pi (2t+1)/(4L)).
+inline int rings_of(int sampling, int L) { return sampling == S2W_SAMPLING_DH ? 2 * L : L; }
+
+// Tables for one band-limit L on the plan's sampling (shared by every transform run at that
+// L).  Device pointers; rows are padded to the row lengths given.
 struct GridTables {
-  int L = 0;            // band-limit (L beta/theta rings, n = 2L-1 azimuthal samples)
+  int L = 0;            // band-limit (n = 2L-1 azimuthal samples)
+  int nr = 0;           // colatitude rings: L (MW) or 2L (DH)
+  int den = 0;          // ring t sits at theta_t = pi (2t+1)/den: den = 2L-1 (MW) or 4L (DH)
   int n = 0;            // 2L-1
   int n1 = 1, n2 = 1;   // DFT factorisation n = n1 * n2 (n1 = 1 for primes)
-  double* wpole = nullptr;     // [L] -2 sin^2(beta_b/2) (beta < pi/2) or 2 cos^2(beta_b/2) (beta >= pi/2)
-  double* cpow_m = nullptr;    // [L][n] mantissa of cos(beta_b/2)^a, a = 0..n-1
-  int* cpow_e = nullptr;       // [L][n] binary exponent
-  double* spow_m = nullptr;    // [L][n] sin(beta_b/2)^a
+  double* wpole = nullptr;     // [nr] -2 sin^2(beta_b/2) (beta < pi/2) or 2 cos^2(beta_b/2) (beta >= pi/2)
+  double* cpow_m = nullptr;    // [nr][n] mantissa of cos(beta_b/2)^a, a = 0..n-1
+  int* cpow_e = nullptr;       // [nr][n] binary exponent
+  double* spow_m = nullptr;    // [nr][n] sin(beta_b/2)^a
   int* spow_e = nullptr;
   double* sqrtC = nullptr;     // [L][n] sqrt(binom(2l, k)), k = 0..2l
-  double* MT = nullptr;        // [2][L][L] quadrature matrices, transposed: MT[par][t'][t]
+  // colatitude quadrature of the forward transforms: MW has a dense matrix per parity of
+  // m + n, DH a diagonal (the ring weights), the same for both parities
+  double* MT = nullptr;        // MW: [2][L][L] quadrature matrices, transposed: MT[par][t'][t]
   float2* MT2 = nullptr;       // the same as float pairs (hi, lo)
-  double* MR = nullptr;        // [2][L][L] the same matrices row-major, MR[par][t][t'] (adjoints)
+  double* MR = nullptr;        // MW: [2][L][L] the same matrices row-major, MR[par][t][t'] (adjoints)
   float2* MR2 = nullptr;       // the same as float pairs
+  double* wdiag = nullptr;     // DH: [nr] ring weights (null on MW)
   double2* tw = nullptr;       // [n] exp(+2 pi i e / n)
   float4* tw4 = nullptr;       // [n] the same as float pairs (re_hi, re_lo, im_hi, im_lo)
 };
@@ -35,8 +44,8 @@ struct GridTables {
 // fp16 or bf16 hi/lo pairs in 128-row x 64-deep core-matrix chunks.  Tile (m, n) starts at
 // l0a = max(|m|,|n|) rounded down to 8.
 struct TcTable {
-  int Lb = 0;                  // beta rows of the inverse tables (L rounded up to 128)
-  int Lk = 0;                  // beta' reduction extent of the forward tables (L rounded up to 64)
+  int Lb = 0;                  // beta rows of the inverse tables (rings rounded up to 128)
+  int Lk = 0;                  // beta' reduction extent of the forward tables (rings rounded up to 64)
   int klf_max = 0;             // largest forward row extent
   int64_t* off_i = nullptr;    // device [Mc * nact] element offset of inverse tile (m, n)
   int64_t* off_f = nullptr;    // forward tile offsets
@@ -50,14 +59,14 @@ struct TcTable {
 // (kernels_tab.cu), float pairs.  Tile (m, n) covers l = l0a .. l0a + kp - 1 with
 // l0a = max(|m|,|n|) rounded down to a multiple of 8 and kp a multiple of 32.
 struct TabTable {
-  int Lp = 0;                  // beta rows of the inverse tiles (L rounded up to 64)
-  int Lk = 0;                  // beta' rows of the forward tiles (L rounded up to 32)
+  int Lp = 0;                  // beta rows of the inverse tiles (rings rounded up to 64)
+  int Lk = 0;                  // beta' rows of the forward tiles (rings rounded up to 32)
   int kpmax = 0;               // largest kp
   int64_t* off_inv = nullptr;  // device [Mc * nact] float2 offset of inverse tile (m, n): [kp][Lp]
   int64_t* off_fwd = nullptr;  // device [Mc * nact] offset of forward tile (m, n): [Lk][kp]
   int* kp = nullptr;           // device [Mc * nact] padded l extent (0 if l0 >= L)
   float2* inv = nullptr;       // d^l_mn(beta)
-  float2* fwd = nullptr;       // (M^{par(m+n)})^T d^l_mn, the quadrature folded in
+  float2* fwd = nullptr;       // (M^{par(m+n)})^T d^l_mn (MW) or w d^l_mn (DH), the quadrature folded in
   int64_t elems = 0;           // float2 elements of each of inv and fwd
 };
 
@@ -99,6 +108,7 @@ struct s2w_plan {
   int Mc = 0, mlo = 0;                 // m storage at L
   bool real = false;
   int nscales = 0, J = 0, L_phi = 1;
+  int nr = 0;                          // colatitude rings at L (rings_of(p.sampling, L))
   std::vector<int> scale_j, Lj, Nj;
   std::vector<int64_t> wav_off;        // per map, elements
   int64_t map_elems = 0, wav_elems = 0, scal_elems = 0;
@@ -117,7 +127,7 @@ struct s2w_plan {
   bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
   std::vector<s2w::TabTable*> tab_tables;  // owned
   double2* flm_ws = nullptr;           // [batch][L][Mc] harmonic workspace
-  double2* g_ws = nullptr;             // largest [batch][nact or 2N-1][L_j][Mc_j] column buffer
+  double2* g_ws = nullptr;             // largest [batch][nact or 2N-1][rings_j][Mc_j] column buffer
   int64_t g_ws_elems = 0;
   int* err_word = nullptr;             // device error word
   cudaStream_t last_stream = nullptr;
@@ -154,13 +164,13 @@ void free_plan(s2w_plan* plan);
 
 // Kernel launchers (kernels_fp64.cu).  All asynchronous on `st`.
 struct ColumnArgs {
-  // A column buffer G[b][nact][L][Mc] (complex) on the MW SO(3)/S2 grid at L.
+  // A column buffer G[b][nact][nr][Mc] (complex) on the SO(3)/S2 grid at L with nr rings.
   double2* G;
-  int B, nact, L, Mc, mlo;
+  int B, nact, L, nr, Mc, mlo;
 };
 
 // Pixel -> columns: azimuthal DFT (length 2L-1) and gamma DFT (length 2N-1), scaled by
-// (2pi/(2L-1)) (2pi/(2N-1)).  Pixel layout [b][2N-1][L][2L-1]; for the SHT N = 1.
+// (2pi/(2L-1)) (2pi/(2N-1)).  Pixel layout [b][2N-1][nr][2L-1]; for the SHT N = 1.
 // pix_sb = elements between consecutive maps of the pixel array.
 cudaError_t launch_dft_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
                                const void* pix, int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st);
@@ -178,12 +188,12 @@ struct CoefArgs {
 // G[b][n][beta][m] = sum_l coef(b,n,l,m) * mult_inv[l][n] * d^l_{m n}(beta)
 cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
                                   CoefArgs in, ColumnArgs out, cudaStream_t st);
-// out(b,n,l,m) += mult_fwd[l][n] * sum_beta (M^{par(m+n)} G)[beta] d^l_{m n}(beta)
-// (quad = false: the colatitude quadrature is skipped, G enters the sum as it is).
+// out(b,n,l,m) += mult_fwd[l][n] * sum_beta (M G)[beta] d^l_{m n}(beta), M the grid's colatitude
+// quadrature (quad = false: the quadrature is skipped, G enters the sum as it is).
 cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
                                   ColumnArgs in, CoefArgs out, cudaStream_t st, bool quad = true);
-// In place on every column of c: G[b][n][.][m] <- (M^{par(m+n)})^T G[b][n][.][m], the transposed
-// colatitude quadrature (adjoint of the forward transforms).
+// In place on every column of c: G[b][n][.][m] <- M^T G[b][n][.][m], the transposed colatitude
+// quadrature (adjoint of the forward transforms).
 cudaError_t launch_quad_adjoint(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
                                 cudaStream_t st);
 
@@ -191,8 +201,8 @@ cudaError_t launch_zero(void* p, int64_t bytes, cudaStream_t st);
 
 // Tensor-core reduced-precision path (kernels_tc.cu).
 struct TabTable;
-cudaError_t launch_tc_pack(const TransformSpec& t, const TcTable& tab, const TabTable& src, int Mc, int mlo, bool fp16,
-                           cudaStream_t st);
+cudaError_t launch_tc_pack(const TransformSpec& t, const TcTable& tab, const TabTable& src, int nr, int Mc, int mlo,
+                           bool fp16, cudaStream_t st);
 cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
                               ColumnArgs out, cudaStream_t st);
 cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,

@@ -17,7 +17,8 @@ struct RecTables {
   const double* spow_m;
   const int* spow_e;
   const double* sqrtC;
-  int n;  // row stride (2L-1)
+  int n;    // row stride (2L-1)
+  int den;  // ring b sits at beta_b = pi (2b+1)/den; it is on the northern half when 2 (2b+1) < den
 };
 
 // Values below 2^-100 of the true d^l_mn never reach the sums; while a column's value
