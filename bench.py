@@ -8,7 +8,8 @@ timing.  One step = analysis + synthesis (Algorithm 1) of the whole batch: the m
 the round trip per map, the paper's protocol (Sec. 4.4).  Default precision "fp64_table":
 float64 accuracy with precomputed Wigner-d tables built at plan creation (outside the timed
 region, like the paper's precomputed mode, Sec. 4.2); the other modes are timed on the same
-inputs under "other_modes".
+inputs under "other_modes", and the same maps sampled on Driscoll-Healy grids under
+"samplings".
 
 value  device time (CUDA events on the launching stream) of K steps, inputs resident in
        HBM, L2 flushed (256 MB write) between steps; max over ranks.
@@ -206,6 +207,32 @@ def run_ball(torch, s2w, stream, flush, steps, precision):
            "wavelet_coefficients_bytes": int(plan.wav_elems * 8)}
     plan.close()
     bp.close()
+    return out
+
+
+def run_sampling(torch, s2w, stream, flush, steps, flm, precision, autotune):
+    """The headline workload on Driscoll-Healy grids (2L rings): transforms per second of the
+    same 16 band-limited maps sampled on the DH grid, and the round-trip error."""
+    import numpy as np
+    plan = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[precision],
+                    precompute=PRECOMPUTE.get(precision, 0), sampling=s2w.S2W_SAMPLING_DH)
+    if autotune:
+        plan.autotune()
+    f = plan.empty_map()
+    plan.sht_inverse(torch.from_numpy(np.ascontiguousarray(flm)).cuda(), f)
+    wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
+    for _ in range(3):
+        plan.forward(f, wav, scal)
+        plan.inverse(wav, scal, f2)
+    ms = time_steps(torch, plan, f, wav, scal, f2, flush, stream, steps)
+    plan.check()
+    flm2 = plan.empty_flm()
+    plan.sht_forward(f2, flm2)
+    err = float(np.abs(flm2.cpu().numpy() - flm).max() / np.abs(flm).max())
+    out = {"dh": {"value": B * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
+                  "rings": plan.R, "precision": precision, "max_rel_err": err,
+                  "map_bytes": int(plan.map_elems * 8), "wavelet_coefficients_bytes": int(plan.wav_elems * 8)}}
+    plan.close()
     return out
 
 
@@ -427,6 +454,10 @@ def run_ours(args, world, rank, local):
     batching = None
     if not args.no_batching:
         batching = run_batching(torch, s2w, stream, flush, max(3, args.steps // 2), not args.no_autotune)
+    samplings = None
+    if not args.no_sampling:
+        samplings = run_sampling(torch, s2w, stream, flush, max(3, args.steps // 2), flm, args.precision,
+                                 not args.no_autotune)
     ball = None
     if not args.no_ball:
         ball = run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)
@@ -462,6 +493,7 @@ def run_ours(args, world, rank, local):
         "differentiation": diff,
         "ball": ball,
         "batching": batching,
+        "samplings": samplings,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
@@ -522,6 +554,7 @@ def main():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-study timing")
     ap.add_argument("--no-ball", action="store_true", help="skip the ball-study timing")
     ap.add_argument("--no-batching", action="store_true", help="skip the batching-study timing")
+    ap.add_argument("--no-sampling", action="store_true", help="skip the Driscoll-Healy timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     args = ap.parse_args()
     world, rank, local = dist_init()
