@@ -44,7 +44,7 @@ PEAKS = {
     "fp64_native": (FP64_PEAK_TFLOPS, "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (probe measured "
                     "1.196 TFLOP/s FP64 at 1987 MHz)"),
 }
-PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64"]
+PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64_tc"] = PEAKS["fp64"]
 # DRAM bytes (read + write) per launch of a kernel, mean over one step's launches, from one ncu
 # capture of the kernel as it is built now (profiles/*_traffic_*.md).
 # An entry is dropped whenever its kernel changes; a missing entry reports null.
@@ -150,7 +150,7 @@ def cpu_baseline_sample():
     return dt, err
 
 
-PRECISIONS = {"fp64": 0, "fp64_table": 0, "fp64_native": 3, "fp32_split": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "fp64_table": 0, "fp64_native": 3, "fp32_split": 1, "bf16": 2, "fp64_tc": 4}
 PRECOMPUTE = {"fp64_table": 1}
 PRECISION_DOC = {
     "fp64": "float64 accuracy: Wigner-d recursion in float64; l-contractions, DFTs and colatitude "
@@ -163,6 +163,9 @@ PRECISION_DOC = {
                   "(3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
     "bf16": "reduced: split-bf16, tcgen05 contractions on precomputed Wigner-d tiles, bf16 hi/lo tables "
             "and data (3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
+    "fp64_tc": "float64 accuracy on the tensor cores: precomputed Wigner-d tables and the data cut into "
+               "seven 7-bit integer slices (fp16), 28 slice products per K step summed exactly in float32 "
+               "TMEM accumulators (error-free splitting); compensated-float32 DFTs",
 }
 # Differentiation study: gradient of sum_j mean |W^j|^2 w.r.t. the pixels of 8 real maps at
 # L = 512, N = 4, lambda = 2, J0 = 3 (analysis + its hand-written adjoint per step).
@@ -432,7 +435,7 @@ def run_ours(args, world, rank, local):
     # the other precision modes on the same inputs, for comparison (not the headline)
     other = {}
     if not args.no_compare:
-        for name in ("fp64", "fp64_table", "fp64_native", "fp32_split", "bf16"):
+        for name in ("fp64", "fp64_table", "fp64_tc", "fp64_native", "fp32_split", "bf16"):
             if name == args.precision:
                 continue
             alt = s2w.Plan(L, N, LAM, J0, reality=True, batch=B, precision=PRECISIONS[name],

@@ -70,8 +70,14 @@ typedef enum {
  * S2W_BF16         split-bf16: the same with bf16 hi + lo pairs for the tables and the data
  *                  (three MMAs per K step, float32 accumulation; 1e-3 target).
  *                  Both reduced modes keep the spin SHT Y, Y^-1 float64-accurate and
- *                  support L <= 256 (S2W_EUNSUPPORTED above). */
-typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3 } s2w_precision;
+ *                  support L <= 256 (S2W_EUNSUPPORTED above).
+ * S2W_FP64_TC      float64 accuracy (1e-11 target) with every l-contraction on the tensor cores:
+ *                  precomputed Wigner-d tables and the data cut into seven 7-bit integer slices
+ *                  (fp16), the slice products exact and their float32 sums exact (Ozaki's
+ *                  error-free splitting); DFTs in compensated float32 pairs.  The tables are
+ *                  always precomputed (precompute is ignored).  L <= 512 and at most 512 rings
+ *                  (S2W_EUNSUPPORTED above). */
+typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3, S2W_FP64_TC = 4 } s2w_precision;
 
 /* S2W_SAMPLING_MW  McEwen-Wiaux: L rings; the forward transforms' colatitude integral is
  *                  exact through the periodic extension of each column (a dense quadrature

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libs2w.so")
 _lib = None
 
-S2W_FP64, S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_NATIVE = 0, 1, 2, 3
+S2W_FP64, S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_NATIVE, S2W_FP64_TC = 0, 1, 2, 3, 4
 S2W_SAMPLING_MW, S2W_SAMPLING_DH = 0, 1
 STATUS = {0: "S2W_OK", 1: "S2W_EINVAL", 2: "S2W_ENOMEM", 3: "S2W_ECUDA", 4: "S2W_ETIMEOUT",
           5: "S2W_EUNSUPPORTED", 6: "S2W_ENONFINITE"}

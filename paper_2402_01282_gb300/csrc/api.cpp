@@ -93,7 +93,7 @@ double dft_flops(const s2w_plan* P, const TransformSpec& t) {
 // algorithmic flops per contraction term: the recursion step (5, unless the d values come
 // from precomputed tables) plus a complex-times-real multiply-add (4) per map
 double term_flops(const s2w_plan* P, const TransformSpec& t) {
-  return (t.tab || t.tc ? 0.0 : 5.0) + 4.0 * batch_of(P);
+  return (t.tab || t.tc || t.tcx ? 0.0 : 5.0) + 4.0 * batch_of(P);
 }
 
 struct TraceScope {
@@ -127,7 +127,8 @@ s2w_status fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, i
   }
   {
     TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * term_flops(P, t) : 0.0);
-    S2W_CUDA(t.tc    ? launch_tc_forward(P, g, t, c, out, st)
+    S2W_CUDA(t.tcx   ? launch_tcx_forward(P, g, t, c, out, st)
+             : t.tc  ? launch_tc_forward(P, g, t, c, out, st)
              : t.tab ? launch_tab_forward(g, t, c, out, st)
                      : launch_wigner_forward(P, g, t, c, out, st),
              "forward contraction");
@@ -142,7 +143,8 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
   ColumnArgs c = cols(P, t.nact, t.L);
   {
     TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * term_flops(P, t) : 0.0);
-    S2W_CUDA(t.tc    ? launch_tc_inverse(P, g, t, in, c, st)
+    S2W_CUDA(t.tcx   ? launch_tcx_inverse(P, g, t, in, c, st)
+             : t.tc  ? launch_tc_inverse(P, g, t, in, c, st)
              : (t.tab && t.minv_factored) ? launch_tab_inverse(g, t, in, c, st)
                      : launch_wigner_inverse(P, g, t, in, c, st),
              "inverse contraction");
@@ -170,6 +172,7 @@ s2w_status adj_inv_transform(s2w_plan* P, const TransformSpec& t, const void* pi
   ta.mult_fwd = t.adj_fwd;
   ta.tc = nullptr;
   ta.tab = nullptr;
+  ta.tcx = nullptr;
   {
     TraceScope ts(P, st, K_DFT_FWD, P->trace_on ? dft_flops(P, t) : 0.0);
     S2W_CUDA(P->native64 ? launch_dft_forward(P, g, ta, pix, pix_sb, P->real, c, st)
@@ -193,6 +196,7 @@ s2w_status adj_fwd_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, v
   ta.mult_inv = t.adj_inv;
   ta.tc = nullptr;
   ta.tab = nullptr;
+  ta.tcx = nullptr;
   {
     TraceScope ts(P, st, K_WIG_INV, P->trace_on ? contraction_terms(P, t) * (5.0 + 4.0 * batch_of(P)) : 0.0);
     S2W_CUDA(launch_wigner_inverse(P, g, ta, in, c, st), "adjoint of the forward contraction");

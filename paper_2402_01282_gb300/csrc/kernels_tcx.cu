@@ -1,0 +1,582 @@
+// Float64-accurate l-contractions on the 5th-generation tensor cores (S2W_FP64_TC) by exact
+// integer slicing of both operands (the error-free splitting of Ozaki, Ogita, Oishi and Rump,
+// "Error-free transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012).
+//
+// Slicing.  Every value v of a table row or of a data column, whose row/column exponent e
+// bounds it (max |v| < 2^e), is rounded to the fixed-point integer X = round(v 2^(47 - e)),
+// |X| < 2^47, and X is written as seven balanced base-128 digits s_0..s_6 in [-64, 63]
+// (X = sum_i s_i 128^(6 - i), s_0 most significant).  Digits are exact in fp16 and the
+// product of two digits (|s t| <= 2^12) is exact in the MMA.
+//
+// Exact accumulation.  The pairs (i, i') of slices with i + i' = q (q = 0..6, 28 pairs) are
+// summed into one float32 TMEM accumulator D_q: over K <= 512 reduction terms one pair sums
+// to |.| <= 2^21 and at most seven pairs share an accumulator, so every partial sum is an
+// integer below 2^24 and float32 holds it exactly, whatever the order of the additions.  The
+// pairs with i + i' > 6 weigh at most 2^-49 of the leading pair and are dropped.  Then
+//   C[r][j] = 2^(e_r + f_j - 10) sum_{q=0..6} 2^(-7 q) D_q[r][j]
+// (e_r: table row exponent, f_j: data column exponent), summed from the smallest weight up in
+// compensated float32 and converted to float64: each output carries ~2^-45 of
+// max_k|A[r][k]| max_k|B[k][j]| per reduction term, the float64 accuracy class of the rest of
+// the path.
+//
+// The GEMMs are those of the reduced modes (one per (m, n), 128-row tiles, 32 columns = 16
+// maps x re/im): inverse rows beta, K = l (tables d^l_mn(beta)); forward rows l, K = beta'
+// (tables with the colatitude quadrature folded in).  Layouts, K chunks of 16, seven slices
+// contiguous per chunk (core matrices of 8 x 8 16-bit elements, K-major, no swizzle):
+//   table  (row tile t, chunk c, slice s): element (r, k) at
+//          ((t nkc + c) 7 + s) 2048 + ((r/8) 2 + k/8) 64 + (r%8) 8 + k%8
+//   data   (chunk c, slice s): element (j, k) at (c 7 + s) 512 + ((j/8) 2 + k/8) 64 + (j%8) 8 + k%8
+// k_tcx_gemm: one CTA of 128 threads per (row tile, m, n); thread 0 drives a three-stage
+// pipeline of bulk copies (35 KB per stage: 7 table slices + 7 data slices) and 28 MMAs per
+// chunk; 105 KB of shared memory and 256 TMEM columns per CTA let two CTAs share an SM; every
+// mbarrier wait is bounded and a timeout sets the plan's error word.
+#include <cuda_fp16.h>
+
+#include "comp32.cuh"
+#include "s2w_internal.h"
+#include "tc_sm100.cuh"
+
+namespace s2w {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kN = 32;                         // MMA N: 16 maps x (re, im)
+constexpr int kKc = 16;                        // K chunk (one MMA deep)
+constexpr int kSl = 7;                         // slices per value
+constexpr int kATile = 128 * kKc;              // elements of one table slice chunk
+constexpr int kBTile = kN * kKc;               // elements of one data slice chunk
+constexpr int kAChunk = kSl * kATile;          // 14336
+constexpr int kBChunk = kSl * kBTile;          // 3584
+constexpr int kStageElems = kAChunk + kBChunk;
+constexpr int kStages = 3;
+constexpr size_t kSmem = (size_t)kStages * kStageElems * sizeof(uint16_t);   // 107520 B
+constexpr uint32_t kWaitIter = 1u << 26;
+constexpr int kTmemCols = 256;                 // 7 accumulators x 32 columns
+
+__device__ __forceinline__ int core16(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+// biased float64 exponent of v (0 for zero and subnormals, which the slicing treats as zero)
+__device__ __forceinline__ int bexp(double v) {
+  return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF;
+}
+
+// row/column exponent from the largest biased exponent: max |v| < 2^e
+__device__ __forceinline__ int exp_of(int emax) { return emax > 0 ? emax - 1022 : 0; }
+
+// v -> seven balanced base-128 digits of round(v 2^(47 - e)) as fp16 bits (integer operations)
+__device__ __forceinline__ void slice7(double v, int e, uint16_t (&out)[kSl]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)(u >> 52) & 0x7FF;
+  long long X = 0;
+  if (E > 0) {
+    const int sh = 1028 + e - E;   // >= 6 when |v| < 2^e
+    if (sh < 63) {
+      const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      X = (long long)((M + (1ull << (sh - 1))) >> sh);
+      if (u >> 63) X = -X;
+    }
+  }
+#pragma unroll
+  for (int i = kSl - 1; i >= 0; --i) {
+    int r = (int)(X & 127);
+    if (r >= 64) r -= 128;
+    out[i] = __half_as_ushort(__int2half_rn(r));
+    X = (X - r) >> 7;
+  }
+}
+
+// 2^k x for a float64 x, by the exponent field (zero below the normal range)
+__device__ __forceinline__ double scale2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((unsigned long long)b >> 52) & 0x7FF;
+  if (E == 0) return 0.0;
+  const int En = E + k;
+  if (En <= 0) return 0.0;
+  if (En >= 2047) return __longlong_as_double((b & (long long)0x8000000000000000ull) | 0x7FF0000000000000ll);
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+
+__device__ __forceinline__ double neg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+// float -> float64 with integer operations (exact for normal floats; subnormals give 0)
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// a += x exactly as a pair (TwoSum into the high part, the error into the low part)
+__device__ __forceinline__ void two_sum_add(Acc& a, float x) {
+  const float s = __fadd_rn(a.s, x);
+  const float z = __fsub_rn(s, a.s);
+  const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, z)), __fsub_rn(x, z));
+  a.s = s;
+  a.c = __fadd_rn(a.c, t);
+}
+
+// ------------------------------------------------------------------ table packing (plan time)
+struct PackArgs {
+  const int* nvals;
+  int nact, L, nr, Mc, mlo;
+  const int64_t *toff_i, *toff_f;   // float-pair tables (kernels_tab.cu layout)
+  const int* tkp;
+  int tLp;
+  const float2 *tinv, *tfwd;
+  const int64_t *off_i, *off_f;
+  const int *kli, *klf;
+  int Lb, Lk, klf_max;
+  int *rexp_i, *rexp_f;
+  uint16_t *inv, *fwd;
+};
+
+// block (m, n), one thread per table row
+__global__ void k_tcx_pack(PackArgs a) {
+  const int mi = blockIdx.x, ni = blockIdx.y, idx = mi * a.nact + ni;
+  const int kli = a.kli[idx], klf = a.klf[idx];
+  if (kli == 0) return;
+  const int m = a.mlo + mi, nn = a.nvals[ni], L = a.L;
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int kp = a.tkp[idx];
+  const float2* Ti = a.tinv + a.toff_i[idx];   // [kp][tLp]
+  const float2* Tf = a.tfwd + a.toff_f[idx];   // [tLk][kp]
+  // inverse: rows beta, K = l - l0a
+  const int nkci = kli / kKc;
+  for (int r = threadIdx.x; r < a.Lb; r += blockDim.x) {
+    auto val = [&](int k) -> double {
+      const int l = l0a + k;
+      if (r >= a.nr || l < l0 || l >= L || k >= kp) return 0.0;
+      const float2 p = Ti[(int64_t)k * a.tLp + r];
+      return (double)p.x + (double)p.y;
+    };
+    int emax = 0;
+    for (int k = 0; k < kli; ++k) emax = max(emax, bexp(val(k)));
+    const int e = exp_of(emax);
+    a.rexp_i[(int64_t)idx * a.Lb + r] = e;
+    uint16_t d[kSl];
+    for (int k = 0; k < kli; ++k) {
+      slice7(val(k), e, d);
+      const int64_t o = a.off_i[idx] + ((int64_t)(r >> 7) * nkci + (k >> 4)) * kAChunk + core16(r & 127, k & 15);
+#pragma unroll
+      for (int s = 0; s < kSl; ++s) a.inv[o + (int64_t)s * kATile] = d[s];
+    }
+  }
+  // forward: rows l - l0a, K = beta'
+  const int nkcf = a.Lk / kKc;
+  for (int r = threadIdx.x; r < klf; r += blockDim.x) {
+    const int l = l0a + r;
+    auto val = [&](int k) -> double {
+      if (k >= a.nr || l < l0 || l >= L || r >= kp) return 0.0;
+      const float2 p = Tf[(int64_t)k * kp + r];
+      return (double)p.x + (double)p.y;
+    };
+    int emax = 0;
+    for (int k = 0; k < a.Lk; ++k) emax = max(emax, bexp(val(k)));
+    const int e = exp_of(emax);
+    a.rexp_f[(int64_t)idx * a.klf_max + r] = e;
+    uint16_t d[kSl];
+    for (int k = 0; k < a.Lk; ++k) {
+      slice7(val(k), e, d);
+      const int64_t o = a.off_f[idx] + ((int64_t)(r >> 7) * nkcf + (k >> 4)) * kAChunk + core16(r & 127, k & 15);
+#pragma unroll
+      for (int s = 0; s < kSl; ++s) a.fwd[o + (int64_t)s * kATile] = d[s];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ data slicing (every call)
+struct PrepArgs {
+  const int* nvals;
+  int nact, L, nr, Mc, mlo, B;
+  const int* kl;             // inverse: K extent (0 = empty); forward: row extent (0 = empty)
+  const int64_t* opoff_i;    // inverse: operand offset of (m, n) within a 16-map chunk
+  int Lk;
+  const double2* coef;       // inverse source
+  int64_t s_b, s_n, s_l;
+  int mlo_in;
+  const double* mult_r;      // inverse: real multiplier (factored) ...
+  const double2* mult;       // ... or the full complex one (mult_r == nullptr)
+  const double2* G;          // forward source: columns [B][nact][nr][Mc]
+  uint16_t* ops;             // destination slices
+  int* fexp;                 // [q][Mc * nact][32] column exponents
+  int64_t qstride;           // operand elements per 16-map chunk
+};
+
+template <bool FWD>
+__device__ __forceinline__ double prep_value(const PrepArgs& a, int mi, int ni, int m, int l0, int l0a, int j, int k,
+                                             int map0) {
+  const int bm = map0 + (j >> 1);
+  if (bm >= a.B) return 0.0;
+  if (FWD) {
+    if (k >= a.nr) return 0.0;
+    const double2 g = a.G[(((int64_t)bm * a.nact + ni) * a.nr + k) * a.Mc + mi];
+    return (j & 1) ? g.y : g.x;
+  }
+  const int l = l0a + k;
+  if (l < l0 || l >= a.L) return 0.0;
+  const double2 c = a.coef[(int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_in)];
+  if (a.mult_r != nullptr) {
+    const double r = a.mult_r[(int64_t)l * a.nact + ni];
+    return ((j & 1) ? c.y : c.x) * r;
+  }
+  const double2 u = a.mult[(int64_t)l * a.nact + ni];
+  return (j & 1) ? fma(c.x, u.y, c.y * u.x) : fma(c.x, u.x, -c.y * u.y);
+}
+
+// block (m, n, 16-map chunk), 256 threads: column exponents, then the seven slices
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_tcxp(PrepArgs a) {
+  __shared__ int colE[kN];
+  const int mi = blockIdx.x, ni = blockIdx.y, q = blockIdx.z, idx = mi * a.nact + ni;
+  const int kl = a.kl[idx];
+  if (kl == 0) return;
+  const int m = a.mlo + mi, nn = a.nvals[ni];
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int K = FWD ? a.Lk : kl;
+  const int map0 = q * (kN / 2);
+  if (threadIdx.x < kN) colE[threadIdx.x] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kN * K; e += blockDim.x) {
+    const int k = e / kN, j = e - k * kN;
+    const int E = bexp(prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0));
+    if (E > 0) atomicMax(&colE[j], E);
+  }
+  __syncthreads();
+  if (threadIdx.x < kN) a.fexp[((int64_t)q * a.Mc * a.nact + idx) * kN + threadIdx.x] = exp_of(colE[threadIdx.x]);
+  const int64_t base = (int64_t)q * a.qstride + (FWD ? (int64_t)idx * a.Lk * kN * kSl : a.opoff_i[idx]);
+  for (int e = threadIdx.x; e < kN * K; e += blockDim.x) {
+    const int k = e / kN, j = e - k * kN;
+    uint16_t d[kSl];
+    slice7(prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0), exp_of(colE[j]), d);
+    const int64_t o = base + (int64_t)(k >> 4) * kBChunk + ((j >> 3) * 2 + ((k & 15) >> 3)) * 64 + (j & 7) * 8 + (k & 7);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) a.ops[o + (int64_t)s * kBTile] = d[s];
+  }
+}
+
+// ------------------------------------------------------------------ GEMM
+struct GemmArgs {
+  const uint16_t* A;
+  const int64_t* off;       // table offsets (inverse off_i or forward off_f)
+  const int* kl;            // inverse: K extent; forward: row extent
+  const int* rexp;          // row exponents
+  int rstride;              // rows per (m, n) in rexp (Lb or klf_max)
+  const int64_t* opoff_i;   // inverse operand offsets
+  const uint16_t* ops;
+  const int* fexp;
+  int64_t qstride;
+  const int* nvals;
+  int nact, L, nr, Lk, Mc, mlo, B;
+  double2* G;               // inverse output
+  int phase_mode;           // inverse: 0 general, 1: +1, 2: -1, 3: +i, 4: -i
+  double2 phase;
+  const double2* mult;      // forward multiplier
+  double2* out;             // forward output (accumulated)
+  int64_t s_b, s_n, s_l;
+  int mlo_out;
+  uint32_t idesc;
+  int* err;
+};
+
+template <bool FWD>
+__global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar_ld[kStages], bar_mma[kStages];
+  __shared__ uint32_t tbase;
+  __shared__ int fexp_s[kN];
+  const int rt = blockIdx.x, mi = blockIdx.y, ni = blockIdx.z, idx = mi * a.nact + ni;
+  const int kl = a.kl[idx], L = a.L, nr = a.nr;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = a.mlo + mi, nn = a.nvals[ni];
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  if (!FWD && kl == 0) {   // l0 >= L: this (m, n) column of every map is zero
+    for (int e = tid; e < a.B * 128; e += kThreads) {
+      const int b = e >> 7, beta = rt * 128 + (e & 127);
+      if (beta < nr) a.G[(((int64_t)b * a.nact + ni) * nr + beta) * a.Mc + mi] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
+  if (FWD && rt * 128 >= kl) return;
+  const int K = FWD ? a.Lk : kl, nkc = K / kKc;
+  uint16_t* const stage0 = reinterpret_cast<uint16_t*>(smem);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&bar_ld[s], 1);
+      tc::mbar_init(&bar_mma[s], 1);
+    }
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tbase;
+  const int64_t aoff = a.off[idx] + (int64_t)rt * nkc * kAChunk;
+  const int64_t boff = FWD ? (int64_t)idx * a.Lk * kN * kSl : a.opoff_i[idx];
+  constexpr uint32_t stage_bytes = (uint32_t)kStageElems * 2u;
+  uint32_t ph_ld[kStages] = {0u, 0u, 0u}, ph_mma[kStages] = {0u, 0u, 0u};
+  const int row = rt * 128 + warp * 32 + lane;
+  const int e_r = a.rexp[(int64_t)idx * a.rstride + row];
+  bool ok = true;
+  for (int map0 = 0, q = 0; map0 < a.B && ok; map0 += kN / 2, ++q) {
+    if (tid < kN) fexp_s[tid] = a.fexp[((int64_t)q * a.Mc * a.nact + idx) * kN + tid];
+    if (tid == 0) {
+      const uint16_t* bq = a.ops + (int64_t)q * a.qstride + boff;
+      auto load = [&](int c, int s) {
+        uint16_t* S = stage0 + s * kStageElems;
+        tc::mbar_expect_tx(&bar_ld[s], stage_bytes);
+        tc::bulk_g2s(S, a.A + aoff + (int64_t)c * kAChunk, kAChunk * 2u, &bar_ld[s]);
+        tc::bulk_g2s(S + kAChunk, bq + (int64_t)c * kBChunk, kBChunk * 2u, &bar_ld[s]);
+      };
+      auto wait = [&](uint64_t* bar, uint32_t& ph) {
+        if (!ok) return;
+        if (!tc::mbar_wait(bar, ph, kWaitIter)) {
+          atomicExch(a.err, (int)S2W_ETIMEOUT);
+          ok = false;
+          return;
+        }
+        ph ^= 1u;
+      };
+      for (int c = 0; c < kStages - 1 && c < nkc; ++c) load(c, c);
+      for (int c = 0; c < nkc && ok; ++c) {
+        const int s = c % kStages;
+        wait(&bar_ld[s], ph_ld[s]);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t A0 = tc::smem_u32(stage0 + s * kStageElems), B0 = A0 + kAChunk * 2u;
+        for (int qq = 0; qq < kSl; ++qq)
+          for (int sa = 0; sa <= qq; ++sa) {
+            const int sb = qq - sa;
+            tc::mma_f16(tmem + (uint32_t)(32 * qq), tc::make_sdesc(A0 + (uint32_t)(sa * kATile * 2), 128, 256),
+                        tc::make_sdesc(B0 + (uint32_t)(sb * kBTile * 2), 128, 256), a.idesc,
+                        (c > 0 || sa > 0) ? 1u : 0u);
+          }
+        tc::mma_commit(&bar_mma[s]);
+        if (c + kStages - 1 < nkc) {
+          // the stage of chunk c + 2 last held chunk c - 1: its MMAs must be done
+          const int sn = (c + kStages - 1) % kStages;
+          if (c >= 1) wait(&bar_mma[sn], ph_mma[sn]);
+          if (!ok) break;
+          load(c + kStages - 1, sn);
+        }
+      }
+      // the MMAs still outstanding: chunks max(0, nkc - 3) .. nkc - 1 (every earlier chunk was
+      // waited for before its stage was reloaded)
+      for (int c = nkc > kStages ? nkc - kStages : 0; c < nkc && ok; ++c)
+        wait(&bar_mma[c % kStages], ph_mma[c % kStages]);
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    tc::fence_after_sync();
+    Acc acc[kN];
+#pragma unroll
+    for (int j = 0; j < kN; ++j) acc[j] = Acc{0.f, 0.f};
+    for (int qq = kSl - 1; qq >= 0; --qq) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * qq), v);
+      const float w = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
+#pragma unroll
+      for (int j = 0; j < kN; ++j) two_sum_add(acc[j], v[j] * w);
+    }
+    if (!FWD) {
+      if (row < nr) {
+#pragma unroll
+        for (int p = 0; p < kN / 2; ++p) {
+          const int bm = map0 + p;
+          if (bm >= a.B) break;
+          const int kr = e_r + fexp_s[2 * p] - 10, ki = e_r + fexp_s[2 * p + 1] - 10;
+          double x = scale2(f2d(acc[2 * p].s), kr) + scale2(f2d(acc[2 * p].c), kr);
+          double y = scale2(f2d(acc[2 * p + 1].s), ki) + scale2(f2d(acc[2 * p + 1].c), ki);
+          double2 r;
+          switch (a.phase_mode) {
+            case 1: r = make_double2(x, y); break;
+            case 2: r = make_double2(neg(x), neg(y)); break;
+            case 3: r = make_double2(neg(y), x); break;
+            case 4: r = make_double2(y, neg(x)); break;
+            default: r = make_double2(fma(x, a.phase.x, -y * a.phase.y), fma(x, a.phase.y, y * a.phase.x));
+          }
+          a.G[(((int64_t)bm * a.nact + ni) * nr + row) * a.Mc + mi] = r;
+        }
+      }
+    } else {
+      const int l = l0a + row;
+      if (l >= l0 && l < L) {
+        const double2 mu = a.mult[(int64_t)l * a.nact + ni];
+#pragma unroll
+        for (int p = 0; p < kN / 2; ++p) {
+          const int bm = map0 + p;
+          if (bm >= a.B) break;
+          const int kr = e_r + fexp_s[2 * p] - 10, ki = e_r + fexp_s[2 * p + 1] - 10;
+          const double x = scale2(f2d(acc[2 * p].s), kr) + scale2(f2d(acc[2 * p].c), kr);
+          const double y = scale2(f2d(acc[2 * p + 1].s), ki) + scale2(f2d(acc[2 * p + 1].c), ki);
+          double2* o = a.out + (int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_out);
+          atomicAdd(&o->x, fma(x, mu.x, -y * mu.y));
+          atomicAdd(&o->y, fma(x, mu.y, y * mu.x));
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();   // TMEM and fexp_s are rewritten by the next map chunk
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+int phase_mode(double2 ph) {
+  if (ph.y == 0.0 && ph.x == 1.0) return 1;
+  if (ph.y == 0.0 && ph.x == -1.0) return 2;
+  if (ph.x == 0.0 && ph.y == 1.0) return 3;
+  if (ph.x == 0.0 && ph.y == -1.0) return 4;
+  return 0;
+}
+
+}  // namespace
+
+cudaError_t launch_tcx_pack(const TransformSpec& t, const TcxTable& tab, const TabTable& src, int nr, int Mc, int mlo,
+                            cudaStream_t st) {
+  PackArgs a;
+  a.nvals = t.nvals;
+  a.nact = t.nact;
+  a.L = t.L;
+  a.nr = nr;
+  a.Mc = Mc;
+  a.mlo = mlo;
+  a.toff_i = src.off_inv;
+  a.toff_f = src.off_fwd;
+  a.tkp = src.kp;
+  a.tLp = src.Lp;
+  a.tinv = src.inv;
+  a.tfwd = src.fwd;
+  a.off_i = tab.off_i;
+  a.off_f = tab.off_f;
+  a.kli = tab.kli;
+  a.klf = tab.klf;
+  a.Lb = tab.Lb;
+  a.Lk = tab.Lk;
+  a.klf_max = tab.klf_max;
+  a.rexp_i = tab.rexp_i;
+  a.rexp_f = tab.rexp_f;
+  a.inv = tab.inv;
+  a.fwd = tab.fwd;
+  k_tcx_pack<<<dim3(Mc, t.nact), 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
+                               ColumnArgs out, cudaStream_t st) {
+  (void)g;
+  const TcxTable& tab = *t.tcx;
+  const int nq = (out.B + kN / 2 - 1) / (kN / 2);
+  PrepArgs pa{};
+  pa.nvals = t.nvals;
+  pa.nact = t.nact;
+  pa.L = t.L;
+  pa.nr = out.nr;
+  pa.Mc = out.Mc;
+  pa.mlo = out.mlo;
+  pa.B = out.B;
+  pa.kl = tab.kli;
+  pa.opoff_i = tab.opoff_i;
+  pa.Lk = tab.Lk;
+  pa.coef = in.coef;
+  pa.s_b = in.s_b;
+  pa.s_n = in.s_n;
+  pa.s_l = in.s_l;
+  pa.mlo_in = in.mlo;
+  pa.mult_r = t.minv_factored ? t.minv_r : nullptr;
+  pa.mult = t.mult_inv;
+  pa.ops = P->tcx_ops;
+  pa.fexp = P->tcx_fexp;
+  pa.qstride = tab.op_i;
+  k_tcxp<false><<<dim3(out.Mc, t.nact, nq), 256, 0, st>>>(pa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  GemmArgs a{};
+  a.A = tab.inv;
+  a.off = tab.off_i;
+  a.kl = tab.kli;
+  a.rexp = tab.rexp_i;
+  a.rstride = tab.Lb;
+  a.opoff_i = tab.opoff_i;
+  a.ops = P->tcx_ops;
+  a.fexp = P->tcx_fexp;
+  a.qstride = tab.op_i;
+  a.nvals = t.nvals;
+  a.nact = t.nact;
+  a.L = t.L;
+  a.nr = out.nr;
+  a.Lk = tab.Lk;
+  a.Mc = out.Mc;
+  a.mlo = out.mlo;
+  a.B = out.B;
+  a.G = out.G;
+  a.phase = t.minv_factored ? t.minv_phase : make_double2(1.0, 0.0);
+  a.phase_mode = phase_mode(a.phase);
+  a.idesc = tc::make_idesc(128, kN, 0, 0, 0);
+  a.err = P->err_word;
+  e = cudaFuncSetAttribute(k_tcx_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  k_tcx_gemm<false><<<dim3(tab.Lb / 128, out.Mc, t.nact), kThreads, kSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
+                               CoefArgs out, cudaStream_t st) {
+  (void)g;
+  const TcxTable& tab = *t.tcx;
+  const int nq = (in.B + kN / 2 - 1) / (kN / 2);
+  PrepArgs pa{};
+  pa.nvals = t.nvals;
+  pa.nact = t.nact;
+  pa.L = t.L;
+  pa.nr = in.nr;
+  pa.Mc = in.Mc;
+  pa.mlo = in.mlo;
+  pa.B = in.B;
+  pa.kl = tab.klf;
+  pa.Lk = tab.Lk;
+  pa.G = in.G;
+  pa.ops = P->tcx_ops;
+  pa.fexp = P->tcx_fexp;
+  pa.qstride = tab.op_f;
+  k_tcxp<true><<<dim3(in.Mc, t.nact, nq), 256, 0, st>>>(pa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  GemmArgs a{};
+  a.A = tab.fwd;
+  a.off = tab.off_f;
+  a.kl = tab.klf;
+  a.rexp = tab.rexp_f;
+  a.rstride = tab.klf_max;
+  a.ops = P->tcx_ops;
+  a.fexp = P->tcx_fexp;
+  a.qstride = tab.op_f;
+  a.nvals = t.nvals;
+  a.nact = t.nact;
+  a.L = t.L;
+  a.nr = in.nr;
+  a.Lk = tab.Lk;
+  a.Mc = in.Mc;
+  a.mlo = in.mlo;
+  a.B = in.B;
+  a.mult = t.mult_fwd;
+  a.out = const_cast<double2*>(out.coef);
+  a.s_b = out.s_b;
+  a.s_n = out.s_n;
+  a.s_l = out.s_l;
+  a.mlo_out = out.mlo;
+  a.idesc = tc::make_idesc(128, kN, 0, 0, 0);
+  a.err = P->err_word;
+  e = cudaFuncSetAttribute(k_tcx_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  if (tab.klf_max == 0) return cudaSuccess;
+  k_tcx_gemm<true><<<dim3(tab.klf_max / 128, in.Mc, t.nact), kThreads, kSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace s2w

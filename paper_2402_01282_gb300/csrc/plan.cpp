@@ -393,6 +393,82 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
   return S2W_OK;
 }
 
+// S2W_FP64_TC: sliced tables for every transform (the SHT, the scaling function and the
+// wavelet scales; specs with the same (L, n values) share one), packed from temporary
+// float-pair tables (make_tab) that are freed once packed; plus the data-slice workspace.
+s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+  std::map<std::pair<int, std::vector<int>>, TcxTable*> cache;
+  std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
+  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+  int64_t op_max = 0, fx_max = 0;
+  const int nq = (P->p.batch + 15) / 16;
+  for (TransformSpec* t : specs) {
+    auto key = std::make_pair(t->L, t->nvals_h);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      t->tcx = it->second;
+      continue;
+    }
+    const int L = t->L, Mc = P->real ? L : 2 * L - 1, mlo = P->real ? 0 : -(L - 1);
+    const int nr = rings_of(P->p.sampling, L);
+    TcxTable* tab = new TcxTable();
+    P->tcx_tables.push_back(tab);
+    tab->Lb = ((nr + 127) / 128) * 128;
+    tab->Lk = ((nr + 15) / 16) * 16;
+    const size_t nidx = (size_t)Mc * t->nact;
+    std::vector<int64_t> oi(nidx, 0), of(nidx, 0), oo(nidx, 0);
+    std::vector<int> ki(nidx, 0), kf(nidx, 0);
+    int64_t ri = 0, rf = 0, ro = 0;
+    for (int mi = 0; mi < Mc; ++mi)
+      for (int ni = 0; ni < t->nact; ++ni) {
+        const size_t idx = (size_t)mi * t->nact + ni;
+        const int l0 = std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni]));
+        oi[idx] = ri;
+        of[idx] = rf;
+        oo[idx] = ro;
+        if (l0 >= L) continue;
+        const int l0a = l0 & ~7;
+        ki[idx] = ((L - l0a + 15) / 16) * 16;
+        kf[idx] = ((L - l0a + 127) / 128) * 128;
+        ri += (int64_t)tab->Lb * ki[idx] * 7;
+        rf += (int64_t)kf[idx] * tab->Lk * 7;
+        ro += (int64_t)32 * 7 * ki[idx];
+        tab->klf_max = std::max(tab->klf_max, kf[idx]);
+      }
+    tab->op_i = ro;
+    tab->op_f = (int64_t)32 * 7 * tab->Lk * (int64_t)nidx;
+    op_max = std::max(op_max, std::max(tab->op_i, tab->op_f));
+    fx_max = std::max<int64_t>(fx_max, (int64_t)nidx * 32);
+    S2W_TRY(upload(P, oi, &tab->off_i, st, err));
+    S2W_TRY(upload(P, of, &tab->off_f, st, err));
+    S2W_TRY(upload(P, oo, &tab->opoff_i, st, err));
+    S2W_TRY(upload(P, ki, &tab->kli, st, err));
+    S2W_TRY(upload(P, kf, &tab->klf, st, err));
+    S2W_TRY(alloc_dev(P, std::max<size_t>(nidx * tab->Lb, 1), &tab->rexp_i, err));
+    S2W_TRY(alloc_dev(P, std::max<size_t>(nidx * (size_t)tab->klf_max, 1), &tab->rexp_f, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ri, 1), &tab->inv, err));
+    S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(rf, 1), &tab->fwd, err));
+    const size_t mark = P->owned.size();
+    TabTable tmp;
+    S2W_TRY(make_tab(P, *t, &tmp, st, err));
+    if (tmp.kpmax > 0 && launch_tcx_pack(*t, *tab, tmp, nr, Mc, mlo, st) != cudaSuccess) {
+      err = "sliced table packing failed to launch";
+      return S2W_ECUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      err = "sliced table build failed";
+      return S2W_ECUDA;
+    }
+    for (size_t i = mark; i < P->owned.size(); ++i) cudaFree(P->owned[i]);
+    P->owned.resize(mark);
+    cache[key] = tab;
+    t->tcx = tab;
+  }
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tcx_ops, err));
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * fx_max, 1), &P->tcx_fexp, err));
+  return S2W_OK;
+}
+
 // Float-pair tables of one transform (offsets, allocation, the build and fold kernels).
 s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStream_t st, std::string& err) {
   const GridTables& g = P->grids[t.grid];
@@ -462,7 +538,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   if (p.batch < 1) { err = "batch must be >= 1"; return S2W_EINVAL; }
   if (p.reality && p.spin != 0) { err = "reality requires spin 0"; return S2W_EINVAL; }
   if (p.precision != S2W_FP64 && p.precision != S2W_FP64_NATIVE && p.precision != S2W_FP32_SPLIT &&
-      p.precision != S2W_BF16) {
+      p.precision != S2W_BF16 && p.precision != S2W_FP64_TC) {
     err = "unknown precision mode";
     return S2W_EINVAL;
   }
@@ -476,6 +552,10 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     err = "Driscoll-Healy sampling supports L <= 512 in this build (2L rings, one thread per ring)";
     return S2W_EUNSUPPORTED;
   }
+  if (p.precision == S2W_FP64_TC && std::max(p.L, rings_of(p.sampling, p.L)) > 512) {
+    err = "the sliced tensor-core contractions need L and the ring count <= 512 (exact float32 sums)";
+    return S2W_EUNSUPPORTED;
+  }
   if (p.precompute == 1 && p.precision == S2W_FP64_NATIVE) {
     err = "the plain float64 path computes the Wigner-d functions on the fly (precompute = 0)";
     return S2W_EUNSUPPORTED;
@@ -487,6 +567,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   P->p = p;
   P->native64 = p.precision == S2W_FP64_NATIVE;
   P->tensor = p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16;
+  P->tcx = p.precision == S2W_FP64_TC;
   P->precompute = p.precompute == 1 && p.precision == S2W_FP64;
   P->real = p.reality != 0;
   P->Mc = P->real ? p.L : 2 * p.L - 1;
@@ -574,6 +655,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
   }
 
   if (P->tensor) S2W_TRY(build_tc_tables(P, st, err));
+  if (P->tcx) S2W_TRY(build_tcx_tables(P, st, err));
   if (P->precompute || P->tensor) S2W_TRY(build_tab_tables(P, st, err, !P->tensor));
 
   // workspaces
@@ -606,6 +688,8 @@ void free_plan(s2w_plan* P) {
   P->tc_tables.clear();
   for (TabTable* t : P->tab_tables) delete t;
   P->tab_tables.clear();
+  for (TcxTable* t : P->tcx_tables) delete t;
+  P->tcx_tables.clear();
 }
 
 }  // namespace s2w

@@ -113,7 +113,7 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
       if (ms < best) best = ms, pick = th;
     }
     t->dft_threads_inv = pick;
-    if (t->tc == nullptr && t->tab == nullptr) {
+    if (t->tc == nullptr && t->tab == nullptr && t->tcx == nullptr) {
       CoefArgs in;
       in.coef = P->flm_ws;
       in.s_b = (int64_t)P->p.L * P->Mc;

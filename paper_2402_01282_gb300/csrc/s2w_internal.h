@@ -70,6 +70,24 @@ struct TabTable {
   int64_t elems = 0;           // float2 elements of each of inv and fwd
 };
 
+// Sliced Wigner-d tables of one transform for the float64-accurate tensor-core contractions
+// (kernels_tcx.cu, S2W_FP64_TC): seven fp16 slices per entry, in 128-row x 16-deep chunks with the
+// slices of a chunk contiguous.  Tile (m, n) starts at l0a = max(|m|,|n|) rounded down to 8.
+struct TcxTable {
+  int Lb = 0;                  // beta rows of the inverse tables (rings rounded up to 128)
+  int Lk = 0;                  // beta' reduction extent of the forward tables (rings rounded up to 16)
+  int klf_max = 0;             // largest forward row extent
+  int64_t* off_i = nullptr;    // device [Mc * nact] element offset of inverse tile (m, n)
+  int64_t* off_f = nullptr;    // forward tile offsets
+  int64_t* opoff_i = nullptr;  // device [Mc * nact] offset of the inverse data slices of (m, n)
+  int* kli = nullptr;          // device [Mc * nact] inverse l extent (multiple of 16; 0 if empty)
+  int* klf = nullptr;          // forward l row extent (multiple of 128; 0 if empty)
+  int* rexp_i = nullptr;       // device [Mc * nact][Lb] row exponents of the inverse tables
+  int* rexp_f = nullptr;       // device [Mc * nact][klf_max] row exponents of the forward tables
+  uint16_t *inv = nullptr, *fwd = nullptr;
+  int64_t op_i = 0, op_f = 0;  // data-slice elements per 16-map chunk (inverse, forward)
+};
+
 // One Wigner / SHT transform instance: band-limit, the n values it carries and the
 // per-(l, n) multipliers that fuse the harmonic products into the contraction.
 struct TransformSpec {
@@ -93,6 +111,7 @@ struct TransformSpec {
   double2* adj_inv = nullptr;   // [L][nact] conj(mult_fwd) * (2 pi/(2L-1)) gscale
   const TcTable* tc = nullptr;  // reduced-precision modes: packed tiles (shared between specs)
   const TabTable* tab = nullptr;  // precompute = 1: float64-accurate tables (shared between specs)
+  const TcxTable* tcx = nullptr;  // S2W_FP64_TC: sliced tables (shared between specs)
   // launch shapes chosen by s2w_plan_autotune (defaults otherwise)
   int dft_threads_fwd = 256, dft_threads_inv = 256;   // threads per block of the DFT kernels
   int inv_mb = 16;                                     // maps per block of the inverse contraction
@@ -123,6 +142,10 @@ struct s2w_plan {
   std::vector<s2w::TcTable*> tc_tables;  // owned
   uint16_t *tc_b_hi = nullptr, *tc_b_lo = nullptr;   // prepared tensor-core operands (hi, lo)
   float* tc_scale = nullptr;                         // their power-of-two scales
+  bool tcx = false;                    // float64-accurate tensor-core contractions (S2W_FP64_TC)
+  std::vector<s2w::TcxTable*> tcx_tables;  // owned
+  uint16_t* tcx_ops = nullptr;         // data slices of the current contraction
+  int* tcx_fexp = nullptr;             // their column exponents
   int cur_batch = 0;                   // > 0: maps per launch for an internal caller (ball transforms)
   bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
   std::vector<s2w::TabTable*> tab_tables;  // owned
@@ -207,6 +230,16 @@ cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const Tran
                               ColumnArgs out, cudaStream_t st);
 cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
                               CoefArgs out, cudaStream_t st);
+
+// Float64-accurate tensor-core contractions by exact slicing (kernels_tcx.cu): table packing from
+// float-pair tables, and the two contractions (same contracts as launch_wigner_inverse/forward).
+struct TcxTable;
+cudaError_t launch_tcx_pack(const TransformSpec& t, const TcxTable& tab, const TabTable& src, int nr, int Mc, int mlo,
+                            cudaStream_t st);
+cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, CoefArgs in,
+                               ColumnArgs out, cudaStream_t st);
+cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs in,
+                               CoefArgs out, cudaStream_t st);
 
 // Float64-accurate table contractions (kernels_tab.cu): build (recursion + folded quadrature)
 // and the two contractions; same contracts as launch_wigner_inverse / launch_wigner_forward.

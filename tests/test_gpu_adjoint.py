@@ -23,7 +23,7 @@ from oracle import adjoint, harmonic, wavelet
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
-MODES = [0, 3, 1, 2]   # S2W_FP64, S2W_FP64_NATIVE, S2W_FP32_SPLIT, S2W_BF16
+MODES = [0, 3, 1, 2, 4]   # S2W_FP64, S2W_FP64_NATIVE, S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_TC
 CASES = [  # L, N, lam, J0, spin, real, B
     (8, 3, 2.0, 0, 0, True, 2),
     (8, 2, 2.0, 1, 2, False, 1),

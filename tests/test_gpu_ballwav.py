@@ -51,7 +51,7 @@ def fields(L, P, B, cfg):
     return np.stack(out)
 
 
-@pytest.mark.parametrize("mode", [(0, 0), (3, 0), (0, 1)])
+@pytest.mark.parametrize("mode", [(0, 0), (3, 0), (0, 1), (4, 0)])
 @pytest.mark.parametrize("L,N,P,nu,J0,J0r,B", CASES)
 def test_ball_analysis_parity(lib, L, N, P, nu, J0, J0r, B, mode):
     plan = lib.BallWavPlan(L, N, P, 2.0, nu, J0, J0r, batch=B, precision=mode[0], precompute=mode[1])

@@ -23,7 +23,7 @@ from oracle import adjoint, ballwav, harmonic, laguerre, wavelet
 pytestmark = pytest.mark.gpu
 DH = 1
 TOL = 1e-11
-MODES = [(0, 0), (3, 0), (0, 1)]
+MODES = [(0, 0), (3, 0), (0, 1), (4, 0)]
 REDUCED = {1: 1e-5, 2: 1e-3}
 
 
@@ -142,7 +142,7 @@ def _matrices(L, N, lam, J0, spin, real):
             adjoint.synthesis_matrix(L, N, lam, J0, spin, real, samp="dh"))
 
 
-@pytest.mark.parametrize("mode", [0, 3, 1, 2])
+@pytest.mark.parametrize("mode", [0, 3, 1, 2, 4])
 @pytest.mark.parametrize("L,N,lam,J0,spin,real,B", [(8, 3, 2.0, 0, 0, True, 2), (6, 2, 2.0, 1, 2, False, 1),
                                                     (7, 3, 1.7, 0, 0, True, 1)])
 def test_dh_adjoints(lib, L, N, lam, J0, spin, real, B, mode):
@@ -170,7 +170,7 @@ def test_dh_adjoints(lib, L, N, lam, J0, spin, real, B, mode):
         assert rel(sp[b], rp) < TOL
 
 
-@pytest.mark.parametrize("mode", [(0, 0), (0, 1)])
+@pytest.mark.parametrize("mode", [(0, 0), (0, 1), (4, 0)])
 def test_dh_ball_wavelet(lib, mode):
     L, N, P, nu, J0, J0r, B = 8, 2, 7, 2.0, 0, 0, 2
     plan = lib.BallWavPlan(L, N, P, 2.0, nu, J0, J0r, batch=B, precision=mode[0], precompute=mode[1], sampling=DH)

@@ -12,8 +12,9 @@ from oracle import filters, harmonic, wavelet
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
-MODES = [(0, 0), (3, 0), (0, 1)]   # (precision, precompute): S2W_FP64 on the fly, S2W_FP64_NATIVE,
-                                   # S2W_FP64 with precomputed quadrature-folded Wigner-d tables
+MODES = [(0, 0), (3, 0), (0, 1), (4, 0)]   # (precision, precompute): S2W_FP64 on the fly,
+                                           # S2W_FP64_NATIVE, S2W_FP64 with precomputed quadrature-folded
+                                           # Wigner-d tables, S2W_FP64_TC (sliced tables, tensor cores)
 
 
 def rel(a, b):
@@ -206,3 +207,29 @@ def test_full_size_steps_256(lib):
     plan.wigner_forward(s, to_dev(pix), out)
     assert rel(out.cpu().numpy()[0], harmonic.wigner_forward(pix[0], Lj, Nj)[:, :, Lj - 1:]) < TOL
     plan.check()
+
+
+@pytest.mark.parametrize("mode", [(0, 1), (4, 0)])
+def test_dynamic_range_and_map_chunks(lib, mode):
+    """20 maps (two 16-map chunks of the tensor-core operands) whose amplitudes span 30 orders
+    of magnitude: every map's wavelet maps and round trip against the oracle relative to that
+    map's own scale (the per-column exponents of the sliced operands)."""
+    L, N, lam, J0, B = 24, 3, 2.0, 1, 20
+    plan = lib.Plan(L, N, lam, J0, reality=True, batch=B, precision=mode[0], precompute=mode[1])
+    amp = [10.0 ** (-15 + 30 * b / (B - 1)) for b in range(B)]
+    flms = [amp[b] * synth.flm_random(L, synth.rng_for(507, b), reality=True) for b in range(B)]
+    f = np.stack([harmonic.sht_inverse(x, L).real for x in flms])
+    wav, scal = plan.empty_wav(), plan.empty_scal()
+    plan.forward(to_dev(f), wav, scal)
+    f2 = plan.empty_map()
+    plan.inverse(wav, scal, f2)
+    plan.check()
+    wv, sc, f2 = wav.cpu().numpy(), scal.cpu().numpy(), f2.cpu().numpy()
+    for b in (0, 7, 15, 16, 19):
+        W_ref, Wp_ref = wavelet.analysis(f[b], L, N, lam, J0, 0, True)
+        for s, w_ref in enumerate(W_ref):
+            got = wv[b, plan.wav_offsets[s]:plan.wav_offsets[s + 1]].reshape(plan.scale_shape(s))
+            assert rel(got, w_ref) < TOL, (b, s)
+        assert rel(sc[b], Wp_ref) < TOL
+    for b in range(B):
+        assert rel(f2[b], f[b]) < TOL, b
