@@ -6,7 +6,7 @@
 // Slicing.  Every value v of a table row or of a data column, whose row/column exponent e
 // bounds it (max |v| < 2^e), is rounded to the fixed-point integer X = round(v 2^(47 - e)),
 // |X| < 2^47, and X is written as seven balanced base-128 digits s_0..s_6 in [-64, 63]
-// (X = sum_i s_i 128^(6 - i), s_0 most significant).  Digits are exact in fp16 and the
+// (X = sum_i s_i 128^(6 - i), s_0 most significant).  Digits are exact in bf16 and the
 // product of two digits (|s t| <= 2^12) is exact in the MMA.
 //
 // Exact accumulation.  The pairs (i, i') of slices with i + i' = q (q = 0..6, 28 pairs) are
@@ -31,8 +31,6 @@
 // pipeline of bulk copies (35 KB per stage: 7 table slices + 7 data slices) and 28 MMAs per
 // chunk; 105 KB of shared memory and 256 TMEM columns per CTA let two CTAs share an SM; every
 // mbarrier wait is bounded and a timeout sets the plan's error word.
-#include <cuda_fp16.h>
-
 #include "comp32.cuh"
 #include "s2w_internal.h"
 #include "tc_sm100.cuh"
@@ -51,7 +49,7 @@ constexpr int kBChunk = kSl * kBTile;          // 3584
 constexpr int kStageElems = kAChunk + kBChunk;
 constexpr int kStages = 3;
 constexpr size_t kSmem = (size_t)kStages * kStageElems * sizeof(uint16_t);   // 107520 B
-constexpr uint32_t kWaitIter = 1u << 26;
+constexpr uint32_t kWaitIter = 1u << 20;   // bounded mbarrier polls (far above any legitimate wait)
 constexpr int kTmemCols = 256;                 // 7 accumulators x 32 columns
 
 __device__ __forceinline__ int core16(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
@@ -61,28 +59,58 @@ __device__ __forceinline__ int bexp(double v) {
   return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF;
 }
 
-// row/column exponent from the largest biased exponent: max |v| < 2^e
-__device__ __forceinline__ int exp_of(int emax) { return emax > 0 ? emax - 1022 : 0; }
-
-// v -> seven balanced base-128 digits of round(v 2^(47 - e)) as fp16 bits (integer operations)
-__device__ __forceinline__ void slice7(double v, int e, uint16_t (&out)[kSl]) {
+// round(v 2^(47 - e)) for |v| < 2^e, by integer operations on the float64 fields
+__device__ __forceinline__ long long fix47(double v, int e) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const int E = (int)(u >> 52) & 0x7FF;
-  long long X = 0;
-  if (E > 0) {
-    const int sh = 1028 + e - E;   // >= 6 when |v| < 2^e
-    if (sh < 63) {
-      const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      X = (long long)((M + (1ull << (sh - 1))) >> sh);
-      if (u >> 63) X = -X;
-    }
-  }
+  if (E == 0) return 0;
+  const int sh = 1028 + e - E;   // >= 6 when |v| < 2^e
+  if (sh >= 63) return 0;
+  const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const long long X = (long long)((M + (1ull << (sh - 1))) >> sh);
+  return (u >> 63) ? -X : X;
+}
+
+// round(c r 2^(47 - e)) for |c r| < 2^e: the 106-bit product of the significands by one
+// 64 x 64 high multiply (the bits below 2^53 of the product only decide exact ties)
+__device__ __forceinline__ long long fix47_prod(double c, double r, int e) {
+  const unsigned long long uc = (unsigned long long)__double_as_longlong(c);
+  const unsigned long long ur = (unsigned long long)__double_as_longlong(r);
+  const int Ec = (int)(uc >> 52) & 0x7FF, Er = (int)(ur >> 52) & 0x7FF;
+  if (Ec == 0 || Er == 0) return 0;
+  const int s2 = 2050 + e - Ec - Er;   // shift after the high multiply, >= 6 when |c r| < 2^e
+  if (s2 >= 63) return 0;
+  const unsigned long long Mc = (uc & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long Mr = (ur & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long H = __umul64hi(Mc << 11, Mr);   // floor(Mc Mr / 2^53)
+  const long long X = (long long)((H + (1ull << (s2 - 1))) >> s2);
+  return ((uc ^ ur) >> 63) ? -X : X;
+}
+
+// exponent bound of a value (max |v| < 2^e over values is the max of these), offset by 4096 so
+// that a zero column (all bounds 0) reads as e = 0
+constexpr int kEOff = 4096;
+__device__ __forceinline__ int ebound(double v) {
+  const int E = bexp(v);
+  return E > 0 ? E - 1022 + kEOff : 0;
+}
+__device__ __forceinline__ int ebound_prod(double c, double r) {   // |c r| < 2^(Ec - 1022) 2^(Er - 1022)
+  const int Ec = bexp(c), Er = bexp(r);
+  return (Ec > 0 && Er > 0) ? Ec + Er - 2044 + kEOff : 0;
+}
+__device__ __forceinline__ int e_from(int eb) { return eb > 0 ? eb - kEOff : 0; }
+
+// X (|X| < 2^48) -> seven balanced base-128 digits in [-64, 63], most significant first, as
+// the float32 bit patterns of the digit values: the balanced digits are the plain base-128
+// digits of X + 64 (128^7 - 1)/127, less 64; each float is exact, and its upper 16 bits are
+// the bfloat16 encoding of the same value.
+constexpr long long kDigitBias = 283691315109952ll;   // 64 (128^7 - 1)/127
+__device__ __forceinline__ void digits7(long long X, uint32_t (&f)[kSl]) {
+  const unsigned long long Y = (unsigned long long)(X + kDigitBias);
 #pragma unroll
-  for (int i = kSl - 1; i >= 0; --i) {
-    int r = (int)(X & 127);
-    if (r >= 64) r -= 128;
-    out[i] = __half_as_ushort(__int2half_rn(r));
-    X = (X - r) >> 7;
+  for (int i = 0; i < kSl; ++i) {
+    const unsigned int u = (unsigned int)(Y >> (7 * (kSl - 1 - i))) & 127u;
+    f[i] = __float_as_uint(__uint_as_float(0x4B000000u | u) - 8388672.0f);   // u - 64
   }
 }
 
@@ -154,16 +182,16 @@ __global__ void k_tcx_pack(PackArgs a) {
       const float2 p = Ti[(int64_t)k * a.tLp + r];
       return (double)p.x + (double)p.y;
     };
-    int emax = 0;
-    for (int k = 0; k < kli; ++k) emax = max(emax, bexp(val(k)));
-    const int e = exp_of(emax);
+    int eb = 0;
+    for (int k = 0; k < kli; ++k) eb = max(eb, ebound(val(k)));
+    const int e = e_from(eb);
     a.rexp_i[(int64_t)idx * a.Lb + r] = e;
-    uint16_t d[kSl];
+    uint32_t d[kSl];
     for (int k = 0; k < kli; ++k) {
-      slice7(val(k), e, d);
+      digits7(fix47(val(k), e), d);
       const int64_t o = a.off_i[idx] + ((int64_t)(r >> 7) * nkci + (k >> 4)) * kAChunk + core16(r & 127, k & 15);
 #pragma unroll
-      for (int s = 0; s < kSl; ++s) a.inv[o + (int64_t)s * kATile] = d[s];
+      for (int s = 0; s < kSl; ++s) a.inv[o + (int64_t)s * kATile] = (uint16_t)(d[s] >> 16);
     }
   }
   // forward: rows l - l0a, K = beta'
@@ -175,16 +203,16 @@ __global__ void k_tcx_pack(PackArgs a) {
       const float2 p = Tf[(int64_t)k * kp + r];
       return (double)p.x + (double)p.y;
     };
-    int emax = 0;
-    for (int k = 0; k < a.Lk; ++k) emax = max(emax, bexp(val(k)));
-    const int e = exp_of(emax);
+    int eb = 0;
+    for (int k = 0; k < a.Lk; ++k) eb = max(eb, ebound(val(k)));
+    const int e = e_from(eb);
     a.rexp_f[(int64_t)idx * a.klf_max + r] = e;
-    uint16_t d[kSl];
+    uint32_t d[kSl];
     for (int k = 0; k < a.Lk; ++k) {
-      slice7(val(k), e, d);
+      digits7(fix47(val(k), e), d);
       const int64_t o = a.off_f[idx] + ((int64_t)(r >> 7) * nkcf + (k >> 4)) * kAChunk + core16(r & 127, k & 15);
 #pragma unroll
-      for (int s = 0; s < kSl; ++s) a.fwd[o + (int64_t)s * kATile] = d[s];
+      for (int s = 0; s < kSl; ++s) a.fwd[o + (int64_t)s * kATile] = (uint16_t)(d[s] >> 16);
     }
   }
 }
@@ -207,55 +235,104 @@ struct PrepArgs {
   int64_t qstride;           // operand elements per 16-map chunk
 };
 
+// Source of the data operand at reduction index k of column (mi, ni) for map bm: the pair
+// (re, im) and, for the inverse with a factored multiplier, the real factor r (value = pair r);
+// otherwise r = 1 and the pair is the value.  Zero outside the data.
 template <bool FWD>
-__device__ __forceinline__ double prep_value(const PrepArgs& a, int mi, int ni, int m, int l0, int l0a, int j, int k,
-                                             int map0) {
-  const int bm = map0 + (j >> 1);
-  if (bm >= a.B) return 0.0;
+__device__ __forceinline__ double2 prep_pair(const PrepArgs& a, int mi, int ni, int m, int l0, int l0a, int bm,
+                                             int k, double& r) {
+  r = 1.0;
+  if (bm >= a.B) return make_double2(0.0, 0.0);
   if (FWD) {
-    if (k >= a.nr) return 0.0;
-    const double2 g = a.G[(((int64_t)bm * a.nact + ni) * a.nr + k) * a.Mc + mi];
-    return (j & 1) ? g.y : g.x;
+    if (k >= a.nr) return make_double2(0.0, 0.0);
+    return a.G[(((int64_t)bm * a.nact + ni) * a.nr + k) * a.Mc + mi];
   }
   const int l = l0a + k;
-  if (l < l0 || l >= a.L) return 0.0;
+  if (l < l0 || l >= a.L) return make_double2(0.0, 0.0);
   const double2 c = a.coef[(int64_t)bm * a.s_b + (int64_t)ni * a.s_n + (int64_t)l * a.s_l + (m - a.mlo_in)];
   if (a.mult_r != nullptr) {
-    const double r = a.mult_r[(int64_t)l * a.nact + ni];
-    return ((j & 1) ? c.y : c.x) * r;
+    r = a.mult_r[(int64_t)l * a.nact + ni];
+    return c;
   }
   const double2 u = a.mult[(int64_t)l * a.nact + ni];
-  return (j & 1) ? fma(c.x, u.y, c.y * u.x) : fma(c.x, u.x, -c.y * u.y);
+  return make_double2(fma(c.x, u.x, -c.y * u.y), fma(c.x, u.y, c.y * u.x));
 }
 
-// block (m, n, 16-map chunk), 256 threads: column exponents, then the seven slices
+// Block (8 consecutive m, n, 16-map chunk), 256 threads.  Work item (m, map, group of 8
+// reduction indices): the 8 m of a group read 128 contiguous bytes per (map, k), and the
+// slices of 8 consecutive k of one column form one 16-byte row of a core matrix (one vector
+// store per slice).  Pass 1: column exponent bounds (register maxima, one shared atomic per
+// column and thread; for a product c r the bound of |c| |r|); pass 2: the seven slices, the
+// product c r formed in the integer domain.
+constexpr int kPrepM = 8;
+
 template <bool FWD>
-__global__ void __launch_bounds__(256) k_tcxp(PrepArgs a) {
-  __shared__ int colE[kN];
-  const int mi = blockIdx.x, ni = blockIdx.y, q = blockIdx.z, idx = mi * a.nact + ni;
-  const int kl = a.kl[idx];
-  if (kl == 0) return;
+__global__ void __launch_bounds__(256, 2) k_tcxp(PrepArgs a) {
+  __shared__ int colE[kPrepM][kN];
+  const int mi0 = blockIdx.x * kPrepM, ni = blockIdx.y, q = blockIdx.z;
+  const int t = threadIdx.x, ml = t % kPrepM, p = (t / kPrepM) % (kN / 2), kg0 = t / (kPrepM * kN / 2);
+  constexpr int kGStride = 256 / (kPrepM * kN / 2);   // 2 k-groups per pass over the block
+  const int mi = mi0 + ml;
+  const int idx = mi * a.nact + ni;
+  const bool live = mi < a.Mc && a.kl[min(idx, a.Mc * a.nact - 1)] != 0;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
-  const int K = FWD ? a.Lk : kl;
-  const int map0 = q * (kN / 2);
-  if (threadIdx.x < kN) colE[threadIdx.x] = 0;
+  const int K = live ? (FWD ? a.Lk : a.kl[idx]) : 0;
+  const int bm = q * (kN / 2) + p;
+  colE[t / kN][t % kN] = 0;
   __syncthreads();
-  for (int e = threadIdx.x; e < kN * K; e += blockDim.x) {
-    const int k = e / kN, j = e - k * kN;
-    const int E = bexp(prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0));
-    if (E > 0) atomicMax(&colE[j], E);
+  int er = 0, ei = 0;
+  for (int kg = kg0; kg * 8 < K; kg += kGStride)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double r;
+      const double2 v = prep_pair<FWD>(a, mi, ni, m, l0, l0a, bm, kg * 8 + u, r);
+      er = max(er, ebound_prod(v.x, r));
+      ei = max(ei, ebound_prod(v.y, r));
+    }
+  if (live) {
+    atomicMax(&colE[ml][2 * p], er);
+    atomicMax(&colE[ml][2 * p + 1], ei);
   }
   __syncthreads();
-  if (threadIdx.x < kN) a.fexp[((int64_t)q * a.Mc * a.nact + idx) * kN + threadIdx.x] = exp_of(colE[threadIdx.x]);
+  if (!live) return;
+  const int fr = e_from(colE[ml][2 * p]), fi = e_from(colE[ml][2 * p + 1]);
+  if (kg0 == 0) {
+    int* fx = a.fexp + ((int64_t)q * a.Mc * a.nact + idx) * kN;
+    fx[2 * p] = fr;
+    fx[2 * p + 1] = fi;
+  }
   const int64_t base = (int64_t)q * a.qstride + (FWD ? (int64_t)idx * a.Lk * kN * kSl : a.opoff_i[idx]);
-  for (int e = threadIdx.x; e < kN * K; e += blockDim.x) {
-    const int k = e / kN, j = e - k * kN;
-    uint16_t d[kSl];
-    slice7(prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0), exp_of(colE[j]), d);
-    const int64_t o = base + (int64_t)(k >> 4) * kBChunk + ((j >> 3) * 2 + ((k & 15) >> 3)) * 64 + (j & 7) * 8 + (k & 7);
+  const int jr = 2 * p, ji = 2 * p + 1;
+  for (int kg = kg0; kg * 8 < K; kg += kGStride) {
+    double2 v[8];
+    double rr[8];
 #pragma unroll
-    for (int s = 0; s < kSl; ++s) a.ops[o + (int64_t)s * kBTile] = d[s];
+    for (int u = 0; u < 8; ++u) v[u] = prep_pair<FWD>(a, mi, ni, m, l0, l0a, bm, kg * 8 + u, rr[u]);
+    uint32_t wr[kSl][4], wi[kSl][4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      uint32_t d0[kSl], d1[kSl], e0[kSl], e1[kSl];
+      digits7(fix47_prod(v[u].x, rr[u], fr), d0);
+      digits7(fix47_prod(v[u + 1].x, rr[u + 1], fr), d1);
+      digits7(fix47_prod(v[u].y, rr[u], fi), e0);
+      digits7(fix47_prod(v[u + 1].y, rr[u + 1], fi), e1);
+#pragma unroll
+      for (int sl = 0; sl < kSl; ++sl) {
+        wr[sl][u / 2] = __byte_perm(d0[sl], d1[sl], 0x7632);   // bf16(k+u) | bf16(k+u+1) << 16
+        wi[sl][u / 2] = __byte_perm(e0[sl], e1[sl], 0x7632);
+      }
+    }
+    const int k = kg * 8;
+    // element (j, k..k+7) of chunk k/16: one 16-byte core-matrix row per slice
+    const int64_t o = base + (int64_t)(k >> 4) * kBChunk + ((k & 15) >> 3) * 64;
+#pragma unroll
+    for (int sl = 0; sl < kSl; ++sl) {
+      *reinterpret_cast<uint4*>(a.ops + o + (int64_t)sl * kBTile + (jr >> 3) * 128 + (jr & 7) * 8) =
+          make_uint4(wr[sl][0], wr[sl][1], wr[sl][2], wr[sl][3]);
+      *reinterpret_cast<uint4*>(a.ops + o + (int64_t)sl * kBTile + (ji >> 3) * 128 + (ji & 7) * 8) =
+          make_uint4(wi[sl][0], wi[sl][1], wi[sl][2], wi[sl][3]);
+    }
   }
 }
 
@@ -493,7 +570,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_i;
-  k_tcxp<false><<<dim3(out.Mc, t.nact, nq), 256, 0, st>>>(pa);
+  k_tcxp<false><<<dim3((out.Mc + kPrepM - 1) / kPrepM, t.nact, nq), 256, 0, st>>>(pa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GemmArgs a{};
@@ -517,7 +594,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   a.G = out.G;
   a.phase = t.minv_factored ? t.minv_phase : make_double2(1.0, 0.0);
   a.phase_mode = phase_mode(a.phase);
-  a.idesc = tc::make_idesc(128, kN, 0, 0, 0);
+  a.idesc = tc::make_idesc(128, kN, 1, 0, 0);   // bf16 slices
   a.err = P->err_word;
   e = cudaFuncSetAttribute(k_tcx_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
@@ -544,7 +621,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_f;
-  k_tcxp<true><<<dim3(in.Mc, t.nact, nq), 256, 0, st>>>(pa);
+  k_tcxp<true><<<dim3((in.Mc + kPrepM - 1) / kPrepM, t.nact, nq), 256, 0, st>>>(pa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GemmArgs a{};
@@ -570,7 +647,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   a.s_n = out.s_n;
   a.s_l = out.s_l;
   a.mlo_out = out.mlo;
-  a.idesc = tc::make_idesc(128, kN, 0, 0, 0);
+  a.idesc = tc::make_idesc(128, kN, 1, 0, 0);   // bf16 slices
   a.err = P->err_word;
   e = cudaFuncSetAttribute(k_tcx_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;

@@ -71,7 +71,7 @@ struct TabTable {
 };
 
 // Sliced Wigner-d tables of one transform for the float64-accurate tensor-core contractions
-// (kernels_tcx.cu, S2W_FP64_TC): seven fp16 slices per entry, in 128-row x 16-deep chunks with the
+// (kernels_tcx.cu, S2W_FP64_TC): seven bf16 slices per entry, in 128-row x 16-deep chunks with the
 // slices of a chunk contiguous.  Tile (m, n) starts at l0a = max(|m|,|n|) rounded down to 8.
 struct TcxTable {
   int Lb = 0;                  // beta rows of the inverse tables (rings rounded up to 128)
