@@ -5,9 +5,10 @@ Workload: 16 real maps per GPU at L = 256, N = 8, lambda = 2, J0 = 2, spin 0, Mc
 sampling; harmonic coefficients seeded complex Gaussian with variance (l+1)^-2 and the
 reality condition (synth.py), synthesised to maps by the library's inverse SHT before
 timing.  One step = analysis + synthesis (Algorithm 1) of the whole batch: the metric is
-the round trip per map, the paper's protocol (Sec. 4.4).  Default precision "fp64_table":
+the round trip per map, the paper's protocol (Sec. 4.4).  Default precision "fp64_tc":
 float64 accuracy with precomputed Wigner-d tables built at plan creation (outside the timed
-region, like the paper's precomputed mode, Sec. 4.2); the other modes are timed on the same
+region, like the paper's precomputed mode, Sec. 4.2) and the l-contractions on the tensor
+cores by exact integer slicing; the other modes are timed on the same
 inputs under "other_modes", and the same maps sampled on Driscoll-Healy grids under
 "samplings".
 
@@ -49,7 +50,8 @@ PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64_tc"] = P
 # capture of the kernel as it is built now (profiles/*_traffic_*.md).
 # An entry is dropped whenever its kernel changes; a missing entry reports null.
 TRAFFIC_BYTES = {("fp64", "wigner_forward"): 368.88e6 / 9 + 0.54e6 / 9,   # k_wig_fwd, on-the-fly mode
-                 ("fp64_table", "wigner_forward"): 209.0e6}   # k_tab_fwd (k_tab_fwd_traffic_..._fp64_table.md)
+                 ("fp64_table", "wigner_forward"): 209.0e6,   # k_tab_fwd (k_tab_fwd_traffic_..._fp64_table.md)
+                 ("fp64_tc", "dft_forward"): 88.24e6}         # k_dftg_fwd (k_dftg_fwd_traffic_..._fp64_tc.md)
 
 
 def dist_init():
@@ -553,7 +555,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the plain float64 path")
-    ap.add_argument("--precision", default="fp64_table", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="fp64_tc", choices=sorted(PRECISIONS))
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-study timing")
     ap.add_argument("--no-ball", action="store_true", help="skip the ball-study timing")
     ap.add_argument("--no-batching", action="store_true", help="skip the batching-study timing")

@@ -98,6 +98,7 @@ struct DftcArgs {
   const float4* gph;    // [nact][Ng] exp(+i n gamma_g) as pairs
   const int* nvals;     // [nact] the n values carried
   double scale;
+  int jb;               // jobs per pass of the two alpha stages (gamma-side kernels)
 };
 
 template <bool REAL, bool PLAIN>
@@ -221,11 +222,15 @@ __device__ __forceinline__ void racc(Acc& a, float xh, float xl, float wh, float
 }
 
 // Stage 1: for every column j2, the length-n1 DFT over j1 of x[n2 j1 + j2], times the twiddle
-// w_n^{SIGN j2 k1}, into tmp[k1 n2 + j2].  Work items: (j2, output pair).
+// w_n^{SIGN j2 k1}, into tmp[k1 n2 + j2].  nb transforms at once (x, tmp advance by n per
+// transform).  Work items: (transform, j2, output pair).
 template <int SIGN, bool PLAIN>
-__device__ void stage1_sym(const float4* x, float4* tmp, const float4* tw, int n, int n1, int n2) {
-  const int h1 = (n1 - 1) / 2, nit = n2 * (h1 + 1);
-  for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+__device__ void stage1_sym(const float4* x0b, float4* tmp0, const float4* tw, int n, int n1, int n2, int nb) {
+  const int h1 = (n1 - 1) / 2, per = n2 * (h1 + 1), nit = nb * per;
+  for (int it0 = threadIdx.x; it0 < nit; it0 += blockDim.x) {
+    const int qb = it0 / per, it = it0 - qb * per;
+    const float4* x = x0b + qb * n;
+    float4* tmp = tmp0 + qb * n;
     const int j2 = it / (h1 + 1), kk = it - j2 * (h1 + 1);
     const float4 x0 = x[j2];
     if (kk == 0) {
@@ -266,19 +271,26 @@ __device__ void stage1_sym(const float4* x, float4* tmp, const float4* tw, int n
 }
 
 // Stage 2: for every row k1, the length-n2 DFT of tmp[k1 n2 + j2] over j2; output k1 + n1 k2
-// goes to store(k, re, im).  AB (n float4) receives the row sums and differences first.
+// of transform qb goes to store(qb, k, re, im).  nb transforms at once (tmp and AB advance by
+// n per transform); AB receives the row sums and differences first.
 template <int SIGN, bool PLAIN, class Store>
-__device__ void stage2_sym(const float4* tmp, float4* AB, const float4* tw, int n, int n1, int n2, Store store) {
-  const int h2 = (n2 - 1) / 2;
-  for (int it = threadIdx.x; it < n1 * h2; it += blockDim.x) {
+__device__ void stage2_sym(const float4* tmp0, float4* AB0, const float4* tw, int n, int n1, int n2, int nb,
+                           Store store) {
+  const int h2 = (n2 - 1) / 2, pera = n1 * h2;
+  for (int it0 = threadIdx.x; it0 < nb * pera; it0 += blockDim.x) {
+    const int qb = it0 / pera, it = it0 - qb * pera;
     const int k1 = it / h2, j = it - k1 * h2 + 1;
-    const float4* row = tmp + k1 * n2;
+    const float4* row = tmp0 + qb * n + k1 * n2;
+    float4* AB = AB0 + qb * n;
     AB[2 * it] = cadd<PLAIN>(row[j], row[n2 - j], 1.f);
     AB[2 * it + 1] = cadd<PLAIN>(row[j], row[n2 - j], -1.f);
   }
   __syncthreads();
-  const int nit = n1 * (h2 + 1);
-  for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+  const int per = n1 * (h2 + 1), nit = nb * per;
+  for (int it0 = threadIdx.x; it0 < nit; it0 += blockDim.x) {
+    const int qb = it0 / per, it = it0 - qb * per;
+    const float4* tmp = tmp0 + qb * n;
+    const float4* AB = AB0 + qb * n;
     const int k1 = it / (h2 + 1), kk = it - k1 * (h2 + 1);
     const float4 x0 = tmp[k1 * n2];
     const float4* ab = AB + 2 * k1 * h2;
@@ -289,7 +301,7 @@ __device__ void stage2_sym(const float4* tmp, float4* AB, const float4* tw, int 
         racc<PLAIN>(re, a.x, a.y, 1.f, 0.f);
         racc<PLAIN>(im, a.z, a.w, 1.f, 0.f);
       }
-      store(k1, re, im);
+      store(qb, k1, re, im);
       continue;
     }
     Acc cr{x0.x, x0.y}, ci{x0.z, x0.w}, sr{0.f, 0.f}, si{0.f, 0.f};
@@ -323,8 +335,8 @@ __device__ void stage2_sym(const float4* tmp, float4* AB, const float4* tw, int 
       }
     }
     const float sg = (float)SIGN;
-    store(k1 + n1 * kk, comb<PLAIN>(cr, -sg, si), comb<PLAIN>(ci, sg, sr));
-    store(k1 + n1 * (n2 - kk), comb<PLAIN>(cr, sg, si), comb<PLAIN>(ci, -sg, sr));
+    store(qb, k1 + n1 * kk, comb<PLAIN>(cr, -sg, si), comb<PLAIN>(ci, sg, sr));
+    store(qb, k1 + n1 * (n2 - kk), comb<PLAIN>(cr, sg, si), comb<PLAIN>(ci, -sg, sr));
   }
 }
 
@@ -372,13 +384,15 @@ __global__ void k_dftg_fwd(DftcArgs a) {
     make_jobs(a.nvals, a.nact, REAL, jn, jp, nj);
     njs = nj;
   }
+  __syncthreads();
+  const int nj = njs, JB = a.jb;
   float4* tw = s4;
-  float4* tmp = tw + n;
-  float4* AB = tmp + n;
-  float4* HZ = AB + n;   // [jobs][n]
+  float4* HZ = tw + n;        // [jobs][n]
+  float4* tmp = HZ + nj * n;  // [JB][n]
+  float4* AB = tmp + JB * n;  // [JB][n]
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   __syncthreads();
-  const int nj = njs, Ng = a.Ng, hg = (Ng - 1) / 2;
+  const int Ng = a.Ng, hg = (Ng - 1) / 2;
   const int64_t ring = (int64_t)a.nr * n;
   const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
   // H_j(alpha) = sum_g W(alpha, gamma_g) exp(-i n_j gamma_g)
@@ -415,17 +429,18 @@ __global__ void k_dftg_fwd(DftcArgs a) {
         if (q < jc) HZ[(j0 + q) * n + al] = pack<PLAIN>(hr[q], hi[q]);
     }
   }
-  // one complex alpha DFT per job
-  for (int j = 0; j < nj; ++j) {
+  // one complex alpha DFT per job, JB jobs per pass of the two stages
+  for (int jb0 = 0; jb0 < nj; jb0 += JB) {
+    const int nb = min(JB, nj - jb0);
     __syncthreads();
-    stage1_sym<-1, PLAIN>(HZ + j * n, tmp, tw, n, a.n1, a.n2);
+    stage1_sym<-1, PLAIN>(HZ + jb0 * n, tmp, tw, n, a.n1, a.n2, nb);
     __syncthreads();
-    const int ni = jn[j], pi = jp[j];
-    double2* Gn = a.G + (((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc;
-    double2* Gp = (pi >= 0) ? a.G + (((int64_t)b * a.nact + pi) * a.nr + t) * a.Mc : nullptr;
     const double sc = a.scale;
     const int mlo = a.mlo;
-    stage2_sym<-1, PLAIN>(tmp, AB, tw, n, a.n1, a.n2, [&](int k, Acc re, Acc im) {
+    stage2_sym<-1, PLAIN>(tmp, AB, tw, n, a.n1, a.n2, nb, [&](int qb, int k, Acc re, Acc im) {
+      const int ni = jn[jb0 + qb], pi = jp[jb0 + qb];
+      double2* Gn = a.G + (((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc;
+      double2* Gp = (pi >= 0) ? a.G + (((int64_t)b * a.nact + pi) * a.nr + t) * a.Mc : nullptr;
       const double zr = to_double(re) * sc, zi = to_double(im) * sc;
       if (REAL) {
         if (k < L) Gn[k] = make_double2(zr, zi);                 // G_{m=k, n}
@@ -451,20 +466,21 @@ __global__ void k_dftg_inv(DftcArgs a) {
     make_jobs(a.nvals, a.nact, REAL, jn, jp, nj);
     njs = nj;
   }
-  float4* tw = s4;
-  float4* x = tw + n;
-  float4* tmp = x + n;
-  float4* AB = tmp + n;
-  float4* HZ = AB + n;   // [jobs][n]
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
   __syncthreads();
-  const int nj = njs;
-  for (int j = 0; j < nj; ++j) {
-    const int ni = jn[j], pi = jp[j];
-    const double2* Gn = a.G + (((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc;
-    const double2* Gp = a.G + (((int64_t)b * a.nact + (pi >= 0 ? pi : ni)) * a.nr + t) * a.Mc;
+  const int nj = njs, JB = a.jb;
+  float4* tw = s4;
+  float4* x = tw + n;         // [JB][n] stage-1 input, then stage-2 scratch (AB)
+  float4* tmp = x + JB * n;   // [JB][n]
+  float4* HZ = tmp + JB * n;  // [jobs][n]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = a.tw[i];
+  for (int jb0 = 0; jb0 < nj; jb0 += JB) {
+    const int nb = min(JB, nj - jb0);
     __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
+      const int qb = e / n, k = e - qb * n;
+      const int ni = jn[jb0 + qb], pi = jp[jb0 + qb];
+      const double2* Gn = a.G + (((int64_t)b * a.nact + ni) * a.nr + t) * a.Mc;
+      const double2* Gp = a.G + (((int64_t)b * a.nact + (pi >= 0 ? pi : ni)) * a.nr + t) * a.Mc;
       double2 v;
       if (REAL) {
         if (k < L) {
@@ -478,14 +494,14 @@ __global__ void k_dftg_inv(DftcArgs a) {
         v = Gn[m - a.mlo];
       }
       const float2 r = split1_bits(v.x), im = split1_bits(v.y);
-      x[k] = make_float4(r.x, r.y, im.x, im.y);
+      x[qb * n + k] = make_float4(r.x, r.y, im.x, im.y);
     }
     __syncthreads();
-    stage1_sym<1, PLAIN>(x, tmp, tw, n, a.n1, a.n2);
+    stage1_sym<1, PLAIN>(x, tmp, tw, n, a.n1, a.n2, nb);
     __syncthreads();
-    float4* Z = HZ + j * n;
-    stage2_sym<1, PLAIN>(tmp, AB, tw, n, a.n1, a.n2,
-                         [&](int k, Acc re, Acc im) { Z[k] = make_float4(re.s, re.c, im.s, im.c); });
+    float4* Z = HZ + jb0 * n;
+    stage2_sym<1, PLAIN>(tmp, x, tw, n, a.n1, a.n2, nb,
+                         [&](int qb, int k, Acc re, Acc im) { Z[qb * n + k] = make_float4(re.s, re.c, im.s, im.c); });
   }
   __syncthreads();
   // W(alpha, gamma_g) = sum_j Z_j(alpha) exp(+i n_j gamma_g); gamma_g and gamma_{Ng-g} share
@@ -541,6 +557,7 @@ DftcArgs make_args(const GridTables& g, const TransformSpec& t, ColumnArgs c) {
   a.gph = t.gphase4;
   a.nvals = t.nvals;
   a.scale = 0.0;
+  a.jb = 1;
   return a;
 }
 
@@ -552,14 +569,26 @@ int dftg_jobs(const TransformSpec& t, bool real) {
     if (!real || v >= 0) ++nj;
   return nj;
 }
-size_t dftg_smem(const GridTables& g, const TransformSpec& t, bool real, bool fwd) {
-  return (size_t)((fwd ? 3 : 4) * g.n + dftg_jobs(t, real) * g.n) * sizeof(float4);
+// shared memory of a gamma-side block: twiddles, the jobs' transforms and two stage buffers of
+// jb transforms each
+size_t dftg_smem_jb(const GridTables& g, int nj, int jb) { return (size_t)(1 + nj + 2 * jb) * g.n * sizeof(float4); }
+constexpr size_t kDftgSmemMax = 200 * 1024;
+// jobs per pass of the two alpha stages: up to 4 (every thread busy in both stages at the
+// headline sizes), fewer when the shared memory would exceed the budget; 0 if even one does
+int dftg_jb(const GridTables& g, const TransformSpec& t, bool real) {
+  const int nj = dftg_jobs(t, real);
+  for (int jb = std::min(nj, 4); jb >= 1; --jb)
+    if (dftg_smem_jb(g, nj, jb) <= kDftgSmemMax) return jb;
+  return 0;
 }
-bool use_dftg(const GridTables& g, const TransformSpec& t, bool real, bool fwd) {
+size_t dftg_smem(const GridTables& g, const TransformSpec& t, bool real) {
+  return dftg_smem_jb(g, dftg_jobs(t, real), dftg_jb(g, t, real));
+}
+bool use_dftg(const GridTables& g, const TransformSpec& t, bool real) {
   if (real)   // every negative n needs its partner -n among the carried values
     for (int v : t.nvals_h)
       if (v < 0 && std::find(t.nvals_h.begin(), t.nvals_h.end(), -v) == t.nvals_h.end()) return false;
-  return dftg_jobs(t, real) <= kMaxJobs && dftg_smem(g, t, real, fwd) <= 200 * 1024;
+  return dftg_jobs(t, real) <= kMaxJobs && dftg_jb(g, t, real) >= 1;
 }
 
 template <class K>
@@ -580,8 +609,9 @@ cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, con
   a.pix_sb = pix_sb;
   a.scale = (2.0 * 3.14159265358979323846 / g.n) * t.gscale;
   dim3 grid(c.nr, c.B);
-  if (use_dftg(g, t, real, true)) {
-    const size_t sm = dftg_smem(g, t, real, true);
+  if (use_dftg(g, t, real)) {
+    const size_t sm = dftg_smem(g, t, real);
+    a.jb = dftg_jb(g, t, real);
     const int th = t.dft_threads_fwd;
     if (plain)
       return real ? launch(k_dftg_fwd<true, true>, grid, sm, st, a, th) : launch(k_dftg_fwd<false, true>, grid, sm, st, a, th);
@@ -599,8 +629,9 @@ cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, Col
   a.pix_out = pix;
   a.pix_sb = pix_sb;
   dim3 grid(c.nr, c.B);
-  if (use_dftg(g, t, real, false)) {
-    const size_t sm = dftg_smem(g, t, real, false);
+  if (use_dftg(g, t, real)) {
+    const size_t sm = dftg_smem(g, t, real);
+    a.jb = dftg_jb(g, t, real);
     const int th = t.dft_threads_inv;
     if (plain)
       return real ? launch(k_dftg_inv<true, true>, grid, sm, st, a, th) : launch(k_dftg_inv<false, true>, grid, sm, st, a, th);
