@@ -231,7 +231,7 @@ struct PrepArgs {
   const double2* mult;       // ... or the full complex one (mult_r == nullptr)
   const double2* G;          // forward source: columns [B][nact][nr][Mc]
   uint16_t* ops;             // destination slices
-  int* fexp;                 // [q][Mc * nact][32] column exponents
+  int* fexp;                 // [q][Mc * nact][32] column exponent bounds (+ kEOff; 0 = zero column)
   int64_t qstride;           // operand elements per 16-map chunk
 };
 
@@ -258,53 +258,73 @@ __device__ __forceinline__ double2 prep_pair(const PrepArgs& a, int mi, int ni, 
   return make_double2(fma(c.x, u.x, -c.y * u.y), fma(c.x, u.y, c.y * u.x));
 }
 
-// Block (8 consecutive m, n, 16-map chunk), 256 threads.  Work item (m, map, group of 8
-// reduction indices): the 8 m of a group read 128 contiguous bytes per (map, k), and the
-// slices of 8 consecutive k of one column form one 16-byte row of a core matrix (one vector
-// store per slice).  Pass 1: column exponent bounds (register maxima, one shared atomic per
-// column and thread; for a product c r the bound of |c| |r|); pass 2: the seven slices, the
-// product c r formed in the integer domain.
+// Two passes over the data, each a grid of blocks (8 consecutive m, n, 16-map chunk, 64-wide
+// slice of K) of 256 threads, so that every block does the same short amount of work whatever
+// the K extent of its m.  Work item (m, map, group of 8 reduction indices): the 8 m of a group
+// read 128 contiguous bytes per (map, k).
+//   k_tcxe: column exponent bounds (for a product c r the bound of |c| |r|), reduced in
+//           registers, then shared memory, then one global atomicMax per column and block into
+//           fexp (zeroed before; 0 = zero column, else exponent + kEOff);
+//   k_tcxs: the seven slices, the product c r formed in the integer domain; the slices of 8
+//           consecutive k of one column form one 16-byte row of a core matrix (one vector store
+//           per slice).
 constexpr int kPrepM = 8;
+constexpr int kPrepK = 64;   // reduction indices per block
 
 template <bool FWD>
-__global__ void __launch_bounds__(256, 2) k_tcxp(PrepArgs a) {
+__global__ void __launch_bounds__(256) k_tcxe(PrepArgs a, int ks_n) {
   __shared__ int colE[kPrepM][kN];
-  const int mi0 = blockIdx.x * kPrepM, ni = blockIdx.y, q = blockIdx.z;
+  const int mi0 = blockIdx.x * kPrepM, ni = blockIdx.y, q = blockIdx.z / ks_n, ks = blockIdx.z % ks_n;
   const int t = threadIdx.x, ml = t % kPrepM, p = (t / kPrepM) % (kN / 2), kg0 = t / (kPrepM * kN / 2);
-  constexpr int kGStride = 256 / (kPrepM * kN / 2);   // 2 k-groups per pass over the block
+  constexpr int kGStride = 256 / (kPrepM * kN / 2);
   const int mi = mi0 + ml;
   const int idx = mi * a.nact + ni;
   const bool live = mi < a.Mc && a.kl[min(idx, a.Mc * a.nact - 1)] != 0;
   const int m = a.mlo + mi, nn = a.nvals[ni];
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
-  const int K = live ? (FWD ? a.Lk : a.kl[idx]) : 0;
+  const int K = live ? min(FWD ? a.Lk : a.kl[idx], (ks + 1) * kPrepK) : 0;
   const int bm = q * (kN / 2) + p;
   colE[t / kN][t % kN] = 0;
   __syncthreads();
   int er = 0, ei = 0;
-  for (int kg = kg0; kg * 8 < K; kg += kGStride)
+  for (int kg = ks * (kPrepK / 8) + kg0; kg * 8 < K; kg += kGStride) {
+    double2 v[8];
+    double r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = prep_pair<FWD>(a, mi, ni, m, l0, l0a, bm, kg * 8 + u, r[u]);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      double r;
-      const double2 v = prep_pair<FWD>(a, mi, ni, m, l0, l0a, bm, kg * 8 + u, r);
-      er = max(er, ebound_prod(v.x, r));
-      ei = max(ei, ebound_prod(v.y, r));
+      er = max(er, ebound_prod(v[u].x, r[u]));
+      ei = max(ei, ebound_prod(v[u].y, r[u]));
     }
-  if (live) {
-    atomicMax(&colE[ml][2 * p], er);
-    atomicMax(&colE[ml][2 * p + 1], ei);
   }
+  if (er > 0) atomicMax(&colE[ml][2 * p], er);
+  if (ei > 0) atomicMax(&colE[ml][2 * p + 1], ei);
   __syncthreads();
-  if (!live) return;
-  const int fr = e_from(colE[ml][2 * p]), fi = e_from(colE[ml][2 * p + 1]);
-  if (kg0 == 0) {
-    int* fx = a.fexp + ((int64_t)q * a.Mc * a.nact + idx) * kN;
-    fx[2 * p] = fr;
-    fx[2 * p + 1] = fi;
-  }
+  const int j = t % kN, mj = t / kN;   // one thread per (m, column)
+  const int idxj = (mi0 + mj) * a.nact + ni;
+  if (mi0 + mj < a.Mc && colE[mj][j] > 0)
+    atomicMax(a.fexp + ((int64_t)q * a.Mc * a.nact + idxj) * kN + j, colE[mj][j]);
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_tcxs(PrepArgs a, int ks_n) {
+  const int mi0 = blockIdx.x * kPrepM, ni = blockIdx.y, q = blockIdx.z / ks_n, ks = blockIdx.z % ks_n;
+  const int t = threadIdx.x, ml = t % kPrepM, p = (t / kPrepM) % (kN / 2), kg0 = t / (kPrepM * kN / 2);
+  constexpr int kGStride = 256 / (kPrepM * kN / 2);
+  const int mi = mi0 + ml;
+  if (mi >= a.Mc) return;
+  const int idx = mi * a.nact + ni;
+  if (a.kl[idx] == 0) return;
+  const int m = a.mlo + mi, nn = a.nvals[ni];
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int K = min(FWD ? a.Lk : a.kl[idx], (ks + 1) * kPrepK);
+  const int bm = q * (kN / 2) + p;
+  const int* fx = a.fexp + ((int64_t)q * a.Mc * a.nact + idx) * kN;
+  const int fr = e_from(fx[2 * p]), fi = e_from(fx[2 * p + 1]);
   const int64_t base = (int64_t)q * a.qstride + (FWD ? (int64_t)idx * a.Lk * kN * kSl : a.opoff_i[idx]);
   const int jr = 2 * p, ji = 2 * p + 1;
-  for (int kg = kg0; kg * 8 < K; kg += kGStride) {
+  for (int kg = ks * (kPrepK / 8) + kg0; kg * 8 < K; kg += kGStride) {
     double2 v[8];
     double rr[8];
 #pragma unroll
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
   const int e_r = a.rexp[(int64_t)idx * a.rstride + row];
   bool ok = true;
   for (int map0 = 0, q = 0; map0 < a.B && ok; map0 += kN / 2, ++q) {
-    if (tid < kN) fexp_s[tid] = a.fexp[((int64_t)q * a.Mc * a.nact + idx) * kN + tid];
+    if (tid < kN) fexp_s[tid] = e_from(a.fexp[((int64_t)q * a.Mc * a.nact + idx) * kN + tid]);
     if (tid == 0) {
       const uint16_t* bq = a.ops + (int64_t)q * a.qstride + boff;
       auto load = [&](int c, int s) {
@@ -570,8 +590,13 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_i;
-  k_tcxp<false><<<dim3((out.Mc + kPrepM - 1) / kPrepM, t.nact, nq), 256, 0, st>>>(pa);
-  cudaError_t e = cudaGetLastError();
+  const int ksn = (tab.kli_max + kPrepK - 1) / kPrepK;
+  cudaError_t e = cudaMemsetAsync(pa.fexp, 0, (size_t)nq * out.Mc * t.nact * kN * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const dim3 pg((out.Mc + kPrepM - 1) / kPrepM, t.nact, nq * ksn);
+  k_tcxe<false><<<pg, 256, 0, st>>>(pa, ksn);
+  k_tcxs<false><<<pg, 256, 0, st>>>(pa, ksn);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GemmArgs a{};
   a.A = tab.inv;
@@ -621,8 +646,13 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_f;
-  k_tcxp<true><<<dim3((in.Mc + kPrepM - 1) / kPrepM, t.nact, nq), 256, 0, st>>>(pa);
-  cudaError_t e = cudaGetLastError();
+  const int ksn = (tab.Lk + kPrepK - 1) / kPrepK;
+  cudaError_t e = cudaMemsetAsync(pa.fexp, 0, (size_t)nq * in.Mc * t.nact * kN * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const dim3 pg((in.Mc + kPrepM - 1) / kPrepM, t.nact, nq * ksn);
+  k_tcxe<true><<<pg, 256, 0, st>>>(pa, ksn);
+  k_tcxs<true><<<pg, 256, 0, st>>>(pa, ksn);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GemmArgs a{};
   a.A = tab.fwd;

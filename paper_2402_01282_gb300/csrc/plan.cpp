@@ -434,6 +434,7 @@ s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
         rf += (int64_t)kf[idx] * tab->Lk * 7;
         ro += (int64_t)32 * 7 * ki[idx];
         tab->klf_max = std::max(tab->klf_max, kf[idx]);
+        tab->kli_max = std::max(tab->kli_max, ki[idx]);
       }
     tab->op_i = ro;
     tab->op_f = (int64_t)32 * 7 * tab->Lk * (int64_t)nidx;

@@ -77,6 +77,7 @@ struct TcxTable {
   int Lb = 0;                  // beta rows of the inverse tables (rings rounded up to 128)
   int Lk = 0;                  // beta' reduction extent of the forward tables (rings rounded up to 16)
   int klf_max = 0;             // largest forward row extent
+  int kli_max = 0;             // largest inverse K extent
   int64_t* off_i = nullptr;    // device [Mc * nact] element offset of inverse tile (m, n)
   int64_t* off_f = nullptr;    // forward tile offsets
   int64_t* opoff_i = nullptr;  // device [Mc * nact] offset of the inverse data slices of (m, n)
