@@ -51,7 +51,7 @@ PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64_tc"] = P
 # An entry is dropped whenever its kernel changes; a missing entry reports null.
 TRAFFIC_BYTES = {("fp64", "wigner_forward"): 368.88e6 / 9 + 0.54e6 / 9,   # k_wig_fwd, on-the-fly mode
                  ("fp64_table", "wigner_forward"): 209.0e6,   # k_tab_fwd (k_tab_fwd_traffic_..._fp64_table.md)
-                 ("fp64_tc", "dft_forward"): 88.24e6}         # k_dftg_fwd (k_dftg_fwd_traffic_..._fp64_tc.md)
+                 ("fp64_tc", "dft_forward"): 88.6e6}          # k_dftg_fwd (k_dftg_fwd_traffic_..._fp64_tc.md)
 
 
 def dist_init():

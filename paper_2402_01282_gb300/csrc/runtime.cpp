@@ -83,7 +83,7 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     return record_error(S2W_ECUDA, "autotune scratch initialisation failed");
   }
   Timer tm;
-  const int cand_threads[] = {128, 256, 512};
+  const int cand_threads[] = {128, 256, 384, 512};
   const int cand_mb[] = {4, 8, 16};
   for (TransformSpec* t : specs) {
     const GridTables& g = P->grids[t->grid];
