@@ -233,3 +233,25 @@ def test_dynamic_range_and_map_chunks(lib, mode):
         assert rel(sc[b], Wp_ref) < TOL
     for b in range(B):
         assert rel(f2[b], f[b]) < TOL, b
+
+
+def test_sliced_mode_largest_bandlimit(lib):
+    """S2W_FP64_TC at L = 512 (K = 512 reduction terms, the largest the exact float32 sums of
+    the sliced products allow): two maps, the SHT both ways on arbitrary samples and
+    band-limited coefficients against the oracle, and the round trip on the GPU."""
+    L, B = 512, 2
+    plan = lib.Plan(L, 1, 2.0, 9, reality=True, batch=B, precision=4)
+    rng = synth.rng_for(508, 0)
+    flm = np.stack([synth.flm_random(L, rng, reality=True) for _ in range(B)])
+    fd = plan.empty_map()
+    plan.sht_inverse(to_dev(np.ascontiguousarray(flm[:, :, L - 1:])), fd)
+    got = fd.cpu().numpy()
+    assert rel(got[1], harmonic.sht_inverse(flm[1], L).real) < TOL
+    pix = synth.pixels_random((B, L, 2 * L - 1), rng)
+    out = plan.empty_flm()
+    plan.sht_forward(to_dev(pix), out)
+    plan.check()
+    assert rel(out.cpu().numpy()[0], harmonic.sht_forward(pix[0], L)[:, L - 1:]) < TOL
+    plan.sht_forward(fd, out)
+    plan.check()
+    assert rel(out.cpu().numpy(), flm[:, :, L - 1:]) < TOL
