@@ -151,7 +151,7 @@ __device__ __forceinline__ void two_sum_add(Acc& a, float x) {
 // ------------------------------------------------------------------ table packing (plan time)
 struct PackArgs {
   const int* nvals;
-  int nact, L, nr, Mc, mlo;
+  int nact, L, nr, Mc, mlo, lmin;
   const int64_t *toff_i, *toff_f;   // float-pair tables (kernels_tab.cu layout)
   const int* tkp;
   int tLp;
@@ -169,17 +169,18 @@ __global__ void k_tcx_pack(PackArgs a) {
   const int kli = a.kli[idx], klf = a.klf[idx];
   if (kli == 0) return;
   const int m = a.mlo + mi, nn = a.nvals[ni], L = a.L;
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int l0 = max(abs(m), abs(nn)), l0s = l0 & ~7;   // the float-pair tables start at l0s
+  const int lb = max(l0, a.lmin), la = lb & ~7;         // the sliced tables at la
   const int kp = a.tkp[idx];
   const float2* Ti = a.tinv + a.toff_i[idx];   // [kp][tLp]
   const float2* Tf = a.tfwd + a.toff_f[idx];   // [tLk][kp]
-  // inverse: rows beta, K = l - l0a
+  // inverse: rows beta, K = l - la
   const int nkci = kli / kKc;
   for (int r = threadIdx.x; r < a.Lb; r += blockDim.x) {
     auto val = [&](int k) -> double {
-      const int l = l0a + k;
-      if (r >= a.nr || l < l0 || l >= L || k >= kp) return 0.0;
-      const float2 p = Ti[(int64_t)k * a.tLp + r];
+      const int l = la + k, ks = l - l0s;
+      if (r >= a.nr || l < lb || l >= L || ks >= kp) return 0.0;
+      const float2 p = Ti[(int64_t)ks * a.tLp + r];
       return (double)p.x + (double)p.y;
     };
     int eb = 0;
@@ -194,13 +195,13 @@ __global__ void k_tcx_pack(PackArgs a) {
       for (int s = 0; s < kSl; ++s) a.inv[o + (int64_t)s * kATile] = (uint16_t)(d[s] >> 16);
     }
   }
-  // forward: rows l - l0a, K = beta'
+  // forward: rows l - la, K = beta'
   const int nkcf = a.Lk / kKc;
   for (int r = threadIdx.x; r < klf; r += blockDim.x) {
-    const int l = l0a + r;
+    const int l = la + r, rs = l - l0s;
     auto val = [&](int k) -> double {
-      if (k >= a.nr || l < l0 || l >= L || r >= kp) return 0.0;
-      const float2 p = Tf[(int64_t)k * kp + r];
+      if (k >= a.nr || l < lb || l >= L || rs >= kp) return 0.0;
+      const float2 p = Tf[(int64_t)k * kp + rs];
       return (double)p.x + (double)p.y;
     };
     int eb = 0;
@@ -220,7 +221,7 @@ __global__ void k_tcx_pack(PackArgs a) {
 // ------------------------------------------------------------------ data slicing (every call)
 struct PrepArgs {
   const int* nvals;
-  int nact, L, nr, Mc, mlo, B;
+  int nact, L, nr, Mc, mlo, B, lmin;
   const int* kl;             // inverse: K extent (0 = empty); forward: row extent (0 = empty)
   const int64_t* opoff_i;    // inverse: operand offset of (m, n) within a 16-map chunk
   int Lk;
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(256) k_tcxe(PrepArgs a, int ks_n) {
   const int idx = mi * a.nact + ni;
   const bool live = mi < a.Mc && a.kl[min(idx, a.Mc * a.nact - 1)] != 0;
   const int m = a.mlo + mi, nn = a.nvals[ni];
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int l0 = max(max(abs(m), abs(nn)), a.lmin), l0a = l0 & ~7;   // first l with a nonzero term
   const int K = live ? min(FWD ? a.Lk : a.kl[idx], (ks + 1) * kPrepK) : 0;
   const int bm = q * (kN / 2) + p;
   colE[t / kN][t % kN] = 0;
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(256) k_tcxs(PrepArgs a, int ks_n) {
   const int idx = mi * a.nact + ni;
   if (a.kl[idx] == 0) return;
   const int m = a.mlo + mi, nn = a.nvals[ni];
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int l0 = max(max(abs(m), abs(nn)), a.lmin), l0a = l0 & ~7;   // first l with a nonzero term
   const int K = min(FWD ? a.Lk : a.kl[idx], (ks + 1) * kPrepK);
   const int bm = q * (kN / 2) + p;
   const int* fx = a.fexp + ((int64_t)q * a.Mc * a.nact + idx) * kN;
@@ -368,7 +369,7 @@ struct GemmArgs {
   const int* fexp;
   int64_t qstride;
   const int* nvals;
-  int nact, L, nr, Lk, Mc, mlo, B;
+  int nact, L, nr, Lk, Mc, mlo, B, lmin;
   double2* G;               // inverse output
   int phase_mode;           // inverse: 0 general, 1: +1, 2: -1, 3: +i, 4: -i
   double2 phase;
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
   const int kl = a.kl[idx], L = a.L, nr = a.nr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = a.mlo + mi, nn = a.nvals[ni];
-  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int l0 = max(max(abs(m), abs(nn)), a.lmin), l0a = l0 & ~7;   // first l with a nonzero term
   if (!FWD && kl == 0) {   // l0 >= L: this (m, n) column of every map is zero
     for (int e = tid; e < a.B * 128; e += kThreads) {
       const int b = e >> 7, beta = rt * 128 + (e & 127);
@@ -543,6 +544,7 @@ cudaError_t launch_tcx_pack(const TransformSpec& t, const TcxTable& tab, const T
   a.nr = nr;
   a.Mc = Mc;
   a.mlo = mlo;
+  a.lmin = tab.lmin;
   a.toff_i = src.off_inv;
   a.toff_f = src.off_fwd;
   a.tkp = src.kp;
@@ -578,6 +580,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   pa.mlo = out.mlo;
   pa.B = out.B;
   pa.kl = tab.kli;
+  pa.lmin = tab.lmin;
   pa.opoff_i = tab.opoff_i;
   pa.Lk = tab.Lk;
   pa.coef = in.coef;
@@ -590,14 +593,16 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_i;
-  const int ksn = (tab.kli_max + kPrepK - 1) / kPrepK;
+  const int ksn = (tab.kli_max + kPrepK - 1) / kPrepK;   // 0 when every multiplier is zero
   cudaError_t e = cudaMemsetAsync(pa.fexp, 0, (size_t)nq * out.Mc * t.nact * kN * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const dim3 pg((out.Mc + kPrepM - 1) / kPrepM, t.nact, nq * ksn);
-  k_tcxe<false><<<pg, 256, 0, st>>>(pa, ksn);
-  k_tcxs<false><<<pg, 256, 0, st>>>(pa, ksn);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (ksn > 0) {
+    const dim3 pg((out.Mc + kPrepM - 1) / kPrepM, t.nact, nq * ksn);
+    k_tcxe<false><<<pg, 256, 0, st>>>(pa, ksn);
+    k_tcxs<false><<<pg, 256, 0, st>>>(pa, ksn);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   GemmArgs a{};
   a.A = tab.inv;
   a.off = tab.off_i;
@@ -620,6 +625,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   a.phase = t.minv_factored ? t.minv_phase : make_double2(1.0, 0.0);
   a.phase_mode = phase_mode(a.phase);
   a.idesc = tc::make_idesc(128, kN, 1, 0, 0);   // bf16 slices
+  a.lmin = tab.lmin;
   a.err = P->err_word;
   e = cudaFuncSetAttribute(k_tcx_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
@@ -641,6 +647,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   pa.mlo = in.mlo;
   pa.B = in.B;
   pa.kl = tab.klf;
+  pa.lmin = tab.lmin;
   pa.Lk = tab.Lk;
   pa.G = in.G;
   pa.ops = P->tcx_ops;
@@ -678,6 +685,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   a.s_l = out.s_l;
   a.mlo_out = out.mlo;
   a.idesc = tc::make_idesc(128, kN, 1, 0, 0);   // bf16 slices
+  a.lmin = tab.lmin;
   a.err = P->err_word;
   e = cudaFuncSetAttribute(k_tcx_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <tuple>
 
 #include "s2w_internal.h"
 #include "tiling.h"
@@ -263,6 +264,15 @@ s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int
       ph4[(size_t)i * ng + gi] = split4(ph[(size_t)i * ng + gi]);
     }
   t.gscale = gscale;
+  // the l-contractions only need l where some multiplier is nonzero (the wavelet filters
+  // vanish below their scale's support, Eq. A3)
+  t.lmin_h = L;
+  for (int l = 0; l < L && t.lmin_h == L; ++l)
+    for (int i = 0; i < t.nact; ++i)
+      if (minv[(size_t)l * t.nact + i] != cplx(0.0) || mfwd[(size_t)l * t.nact + i] != cplx(0.0)) {
+        t.lmin_h = l;
+        break;
+      }
   // adjoint multipliers: the forward DFT kernel carries (2 pi/(2L-1)) gscale, the inverse
   // none, so transposing a DFT moves that factor into the contraction beside it.
   const double dft_scale = (2.0 * kPi / (2.0 * L - 1.0)) * gscale;
@@ -397,13 +407,13 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
 // wavelet scales; specs with the same (L, n values) share one), packed from temporary
 // float-pair tables (make_tab) that are freed once packed; plus the data-slice workspace.
 s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
-  std::map<std::pair<int, std::vector<int>>, TcxTable*> cache;
+  std::map<std::tuple<int, std::vector<int>, int>, TcxTable*> cache;
   std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
   for (TransformSpec& t : P->wav_t) specs.push_back(&t);
   int64_t op_max = 0, fx_max = 0;
   const int nq = (P->p.batch + 15) / 16;
   for (TransformSpec* t : specs) {
-    auto key = std::make_pair(t->L, t->nvals_h);
+    auto key = std::make_tuple(t->L, t->nvals_h, t->lmin_h);
     auto it = cache.find(key);
     if (it != cache.end()) {
       t->tcx = it->second;
@@ -413,6 +423,7 @@ s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     const int nr = rings_of(P->p.sampling, L);
     TcxTable* tab = new TcxTable();
     P->tcx_tables.push_back(tab);
+    tab->lmin = t->lmin_h;
     tab->Lb = ((nr + 127) / 128) * 128;
     tab->Lk = ((nr + 15) / 16) * 16;
     const size_t nidx = (size_t)Mc * t->nact;
@@ -422,7 +433,7 @@ s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     for (int mi = 0; mi < Mc; ++mi)
       for (int ni = 0; ni < t->nact; ++ni) {
         const size_t idx = (size_t)mi * t->nact + ni;
-        const int l0 = std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni]));
+        const int l0 = std::max(std::max(std::abs(mlo + mi), std::abs(t->nvals_h[ni])), t->lmin_h);
         oi[idx] = ri;
         of[idx] = rf;
         oo[idx] = ro;

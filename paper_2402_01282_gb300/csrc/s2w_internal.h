@@ -72,12 +72,14 @@ struct TabTable {
 
 // Sliced Wigner-d tables of one transform for the float64-accurate tensor-core contractions
 // (kernels_tcx.cu, S2W_FP64_TC): seven bf16 slices per entry, in 128-row x 16-deep chunks with the
-// slices of a chunk contiguous.  Tile (m, n) starts at l0a = max(|m|,|n|) rounded down to 8.
+// slices of a chunk contiguous.
 struct TcxTable {
   int Lb = 0;                  // beta rows of the inverse tables (rings rounded up to 128)
   int Lk = 0;                  // beta' reduction extent of the forward tables (rings rounded up to 16)
   int klf_max = 0;             // largest forward row extent
   int kli_max = 0;             // largest inverse K extent
+  int lmin = 0;                // first l with a nonzero multiplier: tile (m, n) covers
+                               // l >= max(|m|, |n|, lmin), starting at that rounded down to 8
   int64_t* off_i = nullptr;    // device [Mc * nact] element offset of inverse tile (m, n)
   int64_t* off_f = nullptr;    // forward tile offsets
   int64_t* opoff_i = nullptr;  // device [Mc * nact] offset of the inverse data slices of (m, n)
@@ -97,6 +99,7 @@ struct TransformSpec {
   int nact = 0;              // number of n values carried
   int* nvals = nullptr;      // device [nact]
   std::vector<int> nvals_h;
+  int lmin_h = 0;               // first l at which mult_inv or mult_fwd is nonzero for some n
   double2* mult_inv = nullptr;  // [L][nact] multiplier applied before the inverse contraction
   double2* mult_fwd = nullptr;  // [L][nact] multiplier applied after the forward contraction
   // mult_inv = minv_phase * minv_r with one complex phase for the whole transform (the

@@ -52,7 +52,7 @@ def test_autotune_keeps_results(lib):
     plan.autotune()
     for k in range(plan.nscales + 2):
         th_f, th_i, mb = plan.launch_shapes(k)
-        assert th_f in (128, 256, 512) and th_i in (128, 256, 512) and mb in (4, 8, 16)
+        assert th_f in (128, 256, 384, 512) and th_i in (128, 256, 384, 512) and mb in (4, 8, 16)
     f = maps_for(L, 0, True, B, 930)
     wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
     plan.forward(to_dev(f), wav, scal)

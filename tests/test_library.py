@@ -56,6 +56,13 @@ def test_invalid_params_rejected_without_gpu(built_lib):
     # Driscoll-Healy above its supported band-limit: unsupported, still before any CUDA call
     p = s2w.Params(600, 2, 0, 0, 0, 1, 0, 0, 2.0, s2w.S2W_SAMPLING_DH)
     assert built_lib.s2w_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == 5
+    # the sliced tensor-core mode beyond K = 512 reduction terms (L > 512, or more than 512 rings)
+    for L, smp in ((600, s2w.S2W_SAMPLING_MW), (300, s2w.S2W_SAMPLING_DH)):
+        p = s2w.Params(L, 2, 0, 0, 0, 1, s2w.S2W_FP64_TC, 0, 2.0, smp)
+        assert built_lib.s2w_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == 5
+    # an unknown precision mode
+    p = s2w.Params(8, 2, 0, 0, 0, 1, 7, 0, 2.0, 0)
+    assert built_lib.s2w_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == 1
 
 
 def test_param_structs_match_header(tmp_path):
