@@ -121,9 +121,7 @@ s2w_status fwd_transform(s2w_plan* P, const TransformSpec& t, const void* pix, i
   ColumnArgs c = cols(P, t.nact, t.L);
   {
     TraceScope ts(P, st, K_DFT_FWD, P->trace_on ? dft_flops(P, t) : 0.0);
-    S2W_CUDA(P->native64 ? launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st)
-                         : launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st, t.tc != nullptr),
-             "azimuthal DFT (forward)");
+    S2W_CUDA(launch_dft_forward_mode(P, g, t, pix, pix_sb, c, st), "azimuthal DFT (forward)");
   }
   {
     TraceScope ts(P, st, K_WIG_FWD, P->trace_on ? contraction_terms(P, t) * term_flops(P, t) : 0.0);
@@ -151,9 +149,7 @@ s2w_status inv_transform(s2w_plan* P, const TransformSpec& t, CoefArgs in, void*
   }
   {
     TraceScope ts(P, st, K_DFT_INV, P->trace_on ? dft_flops(P, t) : 0.0);
-    S2W_CUDA(P->native64 ? launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st)
-                         : launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr),
-             "azimuthal DFT (inverse)");
+    S2W_CUDA(launch_dft_inverse_mode(P, g, t, c, pix, pix_sb, st), "azimuthal DFT (inverse)");
   }
   return S2W_OK;
 }
@@ -221,6 +217,20 @@ size_t pix_bytes(const s2w_plan* P) { return P->real ? sizeof(double) : sizeof(d
 }  // namespace
 
 namespace s2w {
+cudaError_t launch_dft_forward_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
+                                    int64_t pix_sb, ColumnArgs c, cudaStream_t st) {
+  if (P->native64) return launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st);
+  if (P->tcx && t.dftx_fwd != nullptr) return launch_dftx_forward(P, g, t, pix, pix_sb, P->real, c, st);
+  return launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st, t.tc != nullptr);
+}
+
+cudaError_t launch_dft_inverse_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                                    void* pix, int64_t pix_sb, cudaStream_t st) {
+  if (P->native64) return launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st);
+  if (P->tcx && t.dftx_inv != nullptr) return launch_dftx_inverse(P, g, t, c, pix, pix_sb, P->real, st);
+  return launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr);
+}
+
 // Lets other translation units report through s2w_last_error().
 s2w_status record_error(s2w_status s, const std::string& msg) { return fail(s, msg); }
 

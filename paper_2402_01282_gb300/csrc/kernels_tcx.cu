@@ -34,6 +34,7 @@
 #include "comp32.cuh"
 #include "s2w_internal.h"
 #include "tc_sm100.cuh"
+#include "slice7.cuh"
 
 namespace s2w {
 namespace {
@@ -41,7 +42,6 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kN = 32;                         // MMA N: 16 maps x (re, im)
 constexpr int kKc = 16;                        // K chunk (one MMA deep)
-constexpr int kSl = 7;                         // slices per value
 constexpr int kATile = 128 * kKc;              // elements of one table slice chunk
 constexpr int kBTile = kN * kKc;               // elements of one data slice chunk
 constexpr int kAChunk = kSl * kATile;          // 14336
@@ -52,101 +52,6 @@ constexpr size_t kSmem = (size_t)kStages * kStageElems * sizeof(uint16_t);   // 
 constexpr uint32_t kWaitIter = 1u << 20;   // bounded mbarrier polls (far above any legitimate wait)
 constexpr int kTmemCols = 256;                 // 7 accumulators x 32 columns
 
-__device__ __forceinline__ int core16(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
-
-// biased float64 exponent of v (0 for zero and subnormals, which the slicing treats as zero)
-__device__ __forceinline__ int bexp(double v) {
-  return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF;
-}
-
-// round(v 2^(47 - e)) for |v| < 2^e, by integer operations on the float64 fields
-__device__ __forceinline__ long long fix47(double v, int e) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const int E = (int)(u >> 52) & 0x7FF;
-  if (E == 0) return 0;
-  const int sh = 1028 + e - E;   // >= 6 when |v| < 2^e
-  if (sh >= 63) return 0;
-  const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const long long X = (long long)((M + (1ull << (sh - 1))) >> sh);
-  return (u >> 63) ? -X : X;
-}
-
-// round(c r 2^(47 - e)) for |c r| < 2^e: the 106-bit product of the significands by one
-// 64 x 64 high multiply (the bits below 2^53 of the product only decide exact ties)
-__device__ __forceinline__ long long fix47_prod(double c, double r, int e) {
-  const unsigned long long uc = (unsigned long long)__double_as_longlong(c);
-  const unsigned long long ur = (unsigned long long)__double_as_longlong(r);
-  const int Ec = (int)(uc >> 52) & 0x7FF, Er = (int)(ur >> 52) & 0x7FF;
-  if (Ec == 0 || Er == 0) return 0;
-  const int s2 = 2050 + e - Ec - Er;   // shift after the high multiply, >= 6 when |c r| < 2^e
-  if (s2 >= 63) return 0;
-  const unsigned long long Mc = (uc & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const unsigned long long Mr = (ur & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const unsigned long long H = __umul64hi(Mc << 11, Mr);   // floor(Mc Mr / 2^53)
-  const long long X = (long long)((H + (1ull << (s2 - 1))) >> s2);
-  return ((uc ^ ur) >> 63) ? -X : X;
-}
-
-// exponent bound of a value (max |v| < 2^e over values is the max of these), offset by 4096 so
-// that a zero column (all bounds 0) reads as e = 0
-constexpr int kEOff = 4096;
-__device__ __forceinline__ int ebound(double v) {
-  const int E = bexp(v);
-  return E > 0 ? E - 1022 + kEOff : 0;
-}
-__device__ __forceinline__ int ebound_prod(double c, double r) {   // |c r| < 2^(Ec - 1022) 2^(Er - 1022)
-  const int Ec = bexp(c), Er = bexp(r);
-  return (Ec > 0 && Er > 0) ? Ec + Er - 2044 + kEOff : 0;
-}
-__device__ __forceinline__ int e_from(int eb) { return eb > 0 ? eb - kEOff : 0; }
-
-// X (|X| < 2^48) -> seven balanced base-128 digits in [-64, 63], most significant first, as
-// the float32 bit patterns of the digit values: the balanced digits are the plain base-128
-// digits of X + 64 (128^7 - 1)/127, less 64; each float is exact, and its upper 16 bits are
-// the bfloat16 encoding of the same value.
-constexpr long long kDigitBias = 283691315109952ll;   // 64 (128^7 - 1)/127
-__device__ __forceinline__ void digits7(long long X, uint32_t (&f)[kSl]) {
-  const unsigned long long Y = (unsigned long long)(X + kDigitBias);
-#pragma unroll
-  for (int i = 0; i < kSl; ++i) {
-    const unsigned int u = (unsigned int)(Y >> (7 * (kSl - 1 - i))) & 127u;
-    f[i] = __float_as_uint(__uint_as_float(0x4B000000u | u) - 8388672.0f);   // u - 64
-  }
-}
-
-// 2^k x for a float64 x, by the exponent field (zero below the normal range)
-__device__ __forceinline__ double scale2(double x, int k) {
-  const long long b = __double_as_longlong(x);
-  const int E = (int)((unsigned long long)b >> 52) & 0x7FF;
-  if (E == 0) return 0.0;
-  const int En = E + k;
-  if (En <= 0) return 0.0;
-  if (En >= 2047) return __longlong_as_double((b & (long long)0x8000000000000000ull) | 0x7FF0000000000000ll);
-  return __longlong_as_double(b + ((long long)k << 52));
-}
-
-__device__ __forceinline__ double neg(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
-}
-
-// float -> float64 with integer operations (exact for normal floats; subnormals give 0)
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int e = (u >> 23) & 0xFFu;
-  if (e == 0u) return 0.0;
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)b);
-}
-
-// a += x exactly as a pair (TwoSum into the high part, the error into the low part)
-__device__ __forceinline__ void two_sum_add(Acc& a, float x) {
-  const float s = __fadd_rn(a.s, x);
-  const float z = __fsub_rn(s, a.s);
-  const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, z)), __fsub_rn(x, z));
-  a.s = s;
-  a.c = __fadd_rn(a.c, t);
-}
 
 // ------------------------------------------------------------------ table packing (plan time)
 struct PackArgs {
@@ -446,13 +351,16 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
         if (!ok) break;
         tc::fence_after_sync();
         const uint32_t A0 = tc::smem_u32(stage0 + s * kStageElems), B0 = A0 + kAChunk * 2u;
+        // the slice operands of a stage differ only in their start address: descriptors by
+        // offset (address field = byte address / 16), all 28 MMAs unrolled
+        const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
+        const uint32_t acc0 = c > 0 ? 1u : 0u;
+#pragma unroll
         for (int qq = 0; qq < kSl; ++qq)
-          for (int sa = 0; sa <= qq; ++sa) {
-            const int sb = qq - sa;
-            tc::mma_f16(tmem + (uint32_t)(32 * qq), tc::make_sdesc(A0 + (uint32_t)(sa * kATile * 2), 128, 256),
-                        tc::make_sdesc(B0 + (uint32_t)(sb * kBTile * 2), 128, 256), a.idesc,
-                        (c > 0 || sa > 0) ? 1u : 0u);
-          }
+#pragma unroll
+          for (int sa = 0; sa <= qq; ++sa)
+            tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kATile * 2 / 16)),
+                        dB + (uint64_t)((qq - sa) * (kBTile * 2 / 16)), a.idesc, sa > 0 ? 1u : acc0);
         tc::mma_commit(&bar_mma[s]);
         if (c + kStages - 1 < nkc) {
           // the stage of chunk c + 2 last held chunk c - 1: its MMAs must be done

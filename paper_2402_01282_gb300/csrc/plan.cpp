@@ -481,6 +481,45 @@ s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
   return S2W_OK;
 }
 
+// S2W_FP64_TC: sliced twiddle tables of the tensor-core DFTs for every transform whose carried n
+// values fit (dftx_shape_ok): per band-limit one inverse table (scale 1) and one forward table
+// per normalisation (2 pi/(2L-1)) gscale, shared between specs; plus the data-slice workspace.
+s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+  std::map<std::pair<int, double>, DftxTable*> cache;
+  std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
+  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+  for (TransformSpec& t : P->raw_t) specs.push_back(&t);
+  int64_t ops = 0, fx = 0;
+  auto table = [&](int L, double scale, const DftxTable** out) -> s2w_status {
+    auto key = std::make_pair(L, scale);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out = it->second;
+      return S2W_OK;
+    }
+    DftxTable* tab = new DftxTable();
+    P->dftx_tables.push_back(tab);
+    std::vector<uint16_t> hc, hs;
+    build_dftx_table(L, scale, tab, hc, hs);
+    S2W_TRY(upload(P, hc, &tab->cos, st, err));
+    S2W_TRY(upload(P, hs, &tab->sin, st, err));
+    cache[key] = tab;
+    *out = tab;
+    return S2W_OK;
+  };
+  for (TransformSpec* t : specs) {
+    if (!dftx_shape_ok(*t, P->real)) continue;
+    const int nr = rings_of(P->p.sampling, t->L);
+    S2W_TRY(table(t->L, 1.0, &t->dftx_inv));
+    S2W_TRY(table(t->L, (2.0 * kPi / (2.0 * t->L - 1.0)) * t->gscale, &t->dftx_fwd));
+    ops = std::max(ops, dftx_ops_elems(*t, P->real, P->p.batch, nr));
+    fx = std::max(fx, dftx_fexp_elems(P->p.batch, nr));
+  }
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ops, 1), &P->dftx_ops, err));
+  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(fx, 1), &P->dftx_fexp, err));
+  return S2W_OK;
+}
+
 // Float-pair tables of one transform (offsets, allocation, the build and fold kernels).
 s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStream_t st, std::string& err) {
   const GridTables& g = P->grids[t.grid];
@@ -668,6 +707,7 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
 
   if (P->tensor) S2W_TRY(build_tc_tables(P, st, err));
   if (P->tcx) S2W_TRY(build_tcx_tables(P, st, err));
+  if (P->tcx) S2W_TRY(build_dftx_tables(P, st, err));
   if (P->precompute || P->tensor) S2W_TRY(build_tab_tables(P, st, err, !P->tensor));
 
   // workspaces
@@ -702,6 +742,8 @@ void free_plan(s2w_plan* P) {
   P->tab_tables.clear();
   for (TcxTable* t : P->tcx_tables) delete t;
   P->tcx_tables.clear();
+  for (DftxTable* t : P->dftx_tables) delete t;
+  P->dftx_tables.clear();
 }
 
 }  // namespace s2w

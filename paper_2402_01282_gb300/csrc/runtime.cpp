@@ -96,12 +96,11 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     c.Mc = P->real ? t->L : 2 * t->L - 1;
     c.mlo = P->real ? 0 : -(t->L - 1);
     const int64_t pix_sb = (int64_t)(2 * t->N - 1) * g.nr * (2 * t->L - 1);
-    const bool plain = t->tc != nullptr;
     float best = 1e30f;
     int pick = t->dft_threads_fwd;
     for (int th : cand_threads) {
       t->dft_threads_fwd = th;
-      const float ms = time_best(st, tm, 3, [&] { return launch_dftc_forward(g, *t, buf, pix_sb, P->real, c, st, plain); });
+      const float ms = time_best(st, tm, 3, [&] { return launch_dft_forward_mode(P, g, *t, buf, pix_sb, c, st); });
       if (ms < best) best = ms, pick = th;
     }
     t->dft_threads_fwd = pick;
@@ -109,7 +108,7 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     pick = t->dft_threads_inv;
     for (int th : cand_threads) {
       t->dft_threads_inv = th;
-      const float ms = time_best(st, tm, 3, [&] { return launch_dftc_inverse(g, *t, c, buf, pix_sb, P->real, st, plain); });
+      const float ms = time_best(st, tm, 3, [&] { return launch_dft_inverse_mode(P, g, *t, c, buf, pix_sb, st); });
       if (ms < best) best = ms, pick = th;
     }
     t->dft_threads_inv = pick;

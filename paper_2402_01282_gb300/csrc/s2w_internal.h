@@ -91,6 +91,20 @@ struct TcxTable {
   int64_t op_i = 0, op_f = 0;  // data-slice elements per 16-map chunk (inverse, forward)
 };
 
+// Sliced twiddle tables of the tensor-core DFTs (S2W_FP64_TC, kernels_dftx.cu) for one length
+// n = 2L - 1 and one normalisation s: rows k = 0..L-1 (frequencies), reduction index p = 0..L-1
+// (the index pairs p, n - p of the symmetric odd-length DFT), entries s cos(2 pi p k/n) and
+// s sin(2 pi p k/n) as seven bf16 slices in 128-row x 16-deep chunks (the TcxTable layout).
+struct DftxTable {
+  int L = 0;
+  int Kp = 0;                  // reduction extent: L rounded up to 16
+  int Mt = 0;                  // row tiles of 128
+  double scale = 1.0;
+  int e = 0;                   // every entry |v| < 2^e
+  uint16_t* cos = nullptr;
+  uint16_t* sin = nullptr;
+};
+
 // One Wigner / SHT transform instance: band-limit, the n values it carries and the
 // per-(l, n) multipliers that fuse the harmonic products into the contraction.
 struct TransformSpec {
@@ -116,6 +130,10 @@ struct TransformSpec {
   const TcTable* tc = nullptr;  // reduced-precision modes: packed tiles (shared between specs)
   const TabTable* tab = nullptr;  // precompute = 1: float64-accurate tables (shared between specs)
   const TcxTable* tcx = nullptr;  // S2W_FP64_TC: sliced tables (shared between specs)
+  // S2W_FP64_TC: sliced twiddles of the tensor-core azimuthal DFTs (forward: normalisation
+  // (2 pi/(2L-1)) gscale folded in; inverse: 1), null where the compensated DFTs run
+  const DftxTable* dftx_fwd = nullptr;
+  const DftxTable* dftx_inv = nullptr;
   // launch shapes chosen by s2w_plan_autotune (defaults otherwise)
   int dft_threads_fwd = 256, dft_threads_inv = 256;   // threads per block of the DFT kernels
   int inv_mb = 16;                                     // maps per block of the inverse contraction
@@ -150,6 +168,9 @@ struct s2w_plan {
   std::vector<s2w::TcxTable*> tcx_tables;  // owned
   uint16_t* tcx_ops = nullptr;         // data slices of the current contraction
   int* tcx_fexp = nullptr;             // their column exponents
+  std::vector<s2w::DftxTable*> dftx_tables;  // owned
+  uint16_t* dftx_ops = nullptr;        // data slices of the current tensor-core DFT
+  int* dftx_fexp = nullptr;            // their column exponents
   int cur_batch = 0;                   // > 0: maps per launch for an internal caller (ball transforms)
   bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
   std::vector<s2w::TabTable*> tab_tables;  // owned
@@ -253,6 +274,27 @@ cudaError_t launch_tab_inverse(const GridTables& g, const TransformSpec& t, Coef
                                cudaStream_t st);
 cudaError_t launch_tab_forward(const GridTables& g, const TransformSpec& t, ColumnArgs in, CoefArgs out,
                                cudaStream_t st);
+
+// Tensor-core azimuthal DFTs of S2W_FP64_TC (kernels_dftx.cu); same contracts as
+// launch_dft_forward / launch_dft_inverse.  dftx_shape_ok: the transform's carried n values fit
+// (at most 16 jobs, the -n partner of every n for real maps, L <= 512, shared memory of the
+// prologue kernels); the workspace sizes are for B maps on nr rings.
+struct DftxTable;
+bool dftx_shape_ok(const TransformSpec& t, bool real);
+int64_t dftx_ops_elems(const TransformSpec& t, bool real, int B, int nr);
+int64_t dftx_fexp_elems(int B, int nr);
+void build_dftx_table(int L, double scale, DftxTable* tab, std::vector<uint16_t>& hcos, std::vector<uint16_t>& hsin);
+cudaError_t launch_dftx_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
+                                int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st);
+cudaError_t launch_dftx_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                                void* pix, int64_t pix_sb, bool real, cudaStream_t st);
+
+// The azimuthal DFTs of a transform in the plan's precision mode (api.cpp): plain float64,
+// tensor-core (S2W_FP64_TC where the shape fits), or compensated / plain float32.
+cudaError_t launch_dft_forward_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
+                                    int64_t pix_sb, ColumnArgs c, cudaStream_t st);
+cudaError_t launch_dft_inverse_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                                    void* pix, int64_t pix_sb, cudaStream_t st);
 
 // Compensated-float32 versions of the two DFT launchers (kernels_dft_c32.cu); same contract.
 // plain = ordinary float32 arithmetic (the reduced-precision modes).
