@@ -51,7 +51,33 @@ PEAKS["fp32_split"] = PEAKS["bf16"] = PEAKS["fp64_table"] = PEAKS["fp64_tc"] = P
 # An entry is dropped whenever its kernel changes; a missing entry reports null.
 TRAFFIC_BYTES = {("fp64", "wigner_forward"): 368.88e6 / 9 + 0.54e6 / 9,   # k_wig_fwd, on-the-fly mode
                  ("fp64_table", "wigner_forward"): 209.0e6,   # k_tab_fwd (k_tab_fwd_traffic_..._fp64_table.md)
-                 ("fp64_tc", "dft_forward"): 88.6e6}          # k_dftg_fwd (k_dftg_fwd_traffic_..._fp64_tc.md)
+                 # the dft_forward region in fp64_tc: k_dftx_fwd_prep + k_dftx_gemm (tensor-core form)
+                 # and k_dftg_fwd (compensated form), as the autotuner mixed them
+                 # (launches_sphere_L256_N8_B16_fp64_tc.md)
+                 ("fp64_tc", "dft_forward"): 196.25e6}
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (driver-written), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs: torch copy, read+write bytes)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback: 6.8 TB/s, one earlier GB300 measurement"
+
+
+def dft_bytes_per_step(plan):
+    """Algorithmic HBM bytes of one direction of azimuthal DFTs in one step: for every transform
+    (spin SHT, scaling function, each wavelet scale) its pixels (real float64 samples,
+    B (2N_j-1) L_j (2L_j-1)) and its columns (complex float64, m >= 0, the carried n,
+    B nact L_j L_j) each moved once."""
+    def one(Lt, Nt, nact):
+        return B * ((2 * Nt - 1) * Lt * (2 * Lt - 1) * 8 + nact * Lt * Lt * 16)
+    tot = one(L, 1, 1) + one(plan.L_phi, 1, 1)
+    for s in range(plan.nscales):
+        Lj, Nj = plan.Lj[s], plan.Nj[s]
+        tot += one(Lj, Nj, sum(1 for n in range(-(Nj - 1), Nj) if (N + n) % 2 == 1))
+    return tot
 
 
 def dist_init():
@@ -170,8 +196,9 @@ PRECISION_DOC = {
     "bf16": "reduced: split-bf16, tcgen05 contractions on precomputed Wigner-d tiles, bf16 hi/lo tables "
             "and data (3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
     "fp64_tc": "float64 accuracy on the tensor cores: precomputed Wigner-d tables and the data cut into "
-               "seven 7-bit integer slices (fp16), 28 slice products per K step summed exactly in float32 "
-               "TMEM accumulators (error-free splitting); compensated-float32 DFTs",
+               "seven 7-bit integer slices (bf16), 28 slice products per K step summed exactly in float32 "
+               "TMEM accumulators (error-free splitting); azimuthal DFTs on the tensor cores by the same "
+               "slicing or in compensated float32, whichever the autotuner measured faster per transform",
 }
 # Differentiation study: gradient of sum_j mean |W^j|^2 w.r.t. the pixels of 8 real maps at
 # L = 512, N = 4, lambda = 2, J0 = 3 (analysis + its hand-written adjoint per step).
@@ -476,16 +503,28 @@ def run_ours(args, world, rank, local):
             dist.destroy_process_group()
         return
     maps = B * world * args.steps
+    dft_forms = [plan.dft_forms(k) for k in range(plan.nscales + 2)]
     dom = max(trace.items(), key=lambda kv: kv[1][1])
     name, (launches, ms, flops) = dom
-    achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-    peak, peak_src = PEAKS[args.precision]
-    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES.get((args.precision, name)), "traffic_unit": "bytes/launch",
-                "peak_source": peak_src,
-                "per_kernel": {k: {"launches": v[0], "ms": v[1], "tflops": (v[2] / (v[1] * 1e-3) / 1e12) if v[1] else 0.0}
-                               for k, v in trace.items()}}
+    per_kernel = {k: {"launches": v[0], "ms": v[1], "tflops": (v[2] / (v[1] * 1e-3) / 1e12) if v[1] else 0.0}
+                  for k, v in trace.items()}
+    if args.precision == "fp64_tc" and name.startswith("dft"):
+        # tensor-core DFTs: the speed of light is HBM, the DFT's own input and output read and
+        # written once (dft_bytes_per_step), against the measured copy bandwidth
+        hbm, hbm_src = hbm_peak()
+        achieved = dft_bytes_per_step(plan) * args.steps / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": TRAFFIC_BYTES.get((args.precision, name)),
+                    "traffic_unit": "bytes/launch", "peak_source": hbm_src,
+                    "algorithmic_bytes_per_launch": dft_bytes_per_step(plan) / (launches / args.steps),
+                    "per_kernel": per_kernel}
+    else:
+        achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        peak, peak_src = PEAKS[args.precision]
+        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": TRAFFIC_BYTES.get((args.precision, name)), "traffic_unit": "bytes/launch",
+                    "peak_source": peak_src, "per_kernel": per_kernel}
     line = {
         "metric": METRIC, "value": maps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -494,6 +533,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "L": L, "N": N, "lambda": LAM, "J0": J0, "spin": 0,
                    "maps_per_gpu": B, "precision": args.precision, "precompute": PRECOMPUTE.get(args.precision, 0),
                    "launch_shapes": None if args.no_autotune else [plan.launch_shapes(k) for k in range(plan.nscales + 2)],
+                   "dft_tensor_cores": dft_forms,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MB write)"},
         "precision_detail": PRECISION_DOC[args.precision],
@@ -508,9 +548,12 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
                 "d2h_bytes_per_step": int(f.numel() * 8), "max_rel_err": e2e_err},
         # the trace records one region per DFT and per contraction; a contraction region launches
-        # KERNELS_PER_CONTRACTION[precision] kernels of the library
-        "gpu_launches": int(sum(v[0] * (KERNELS_PER_CONTRACTION.get(args.precision, 1) if k.startswith("wigner") else 1)
-                                for k, v in trace.items())),
+        # KERNELS_PER_CONTRACTION[precision] kernels of the library, a DFT region 2 in the
+        # tensor-core form (prologue + GEMM) and 1 otherwise (every transform's forward and inverse
+        # DFT once per step)
+        "gpu_launches": int(sum(v[0] * KERNELS_PER_CONTRACTION.get(args.precision, 1)
+                                for k, v in trace.items() if k.startswith("wigner"))
+                            + args.steps * sum(2 if tc else 1 for pair in dft_forms for tc in pair)),
     }
     if world == 1 and not args.no_cpu_baseline:
         dt, cerr = cpu_baseline_sample()

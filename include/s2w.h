@@ -73,10 +73,14 @@ typedef enum {
  *                  support L <= 256 (S2W_EUNSUPPORTED above).
  * S2W_FP64_TC      float64 accuracy (1e-11 target) with every l-contraction on the tensor cores:
  *                  precomputed Wigner-d tables and the data cut into seven 7-bit integer slices
- *                  (fp16), the slice products exact and their float32 sums exact (Ozaki's
- *                  error-free splitting); DFTs in compensated float32 pairs.  The tables are
- *                  always precomputed (precompute is ignored).  L <= 512 and at most 512 rings
- *                  (S2W_EUNSUPPORTED above). */
+ *                  (bf16), the slice products exact and their float32 sums exact (Ozaki's
+ *                  error-free splitting); the azimuthal DFTs on the tensor cores by the same
+ *                  slicing (the symmetric odd-length DFT as two GEMMs against sliced twiddle
+ *                  tables) where the carried n fit (at most 16 per ring), else, and for the
+ *                  gamma DFTs, compensated float32 pairs; s2w_plan_autotune may pick the
+ *                  compensated DFTs where they are faster.  The tables are always precomputed
+ *                  (precompute is ignored).  L <= 512 and at most 512 rings (S2W_EUNSUPPORTED
+ *                  above). */
 typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3, S2W_FP64_TC = 4 } s2w_precision;
 
 /* S2W_SAMPLING_MW  McEwen-Wiaux: L rings; the forward transforms' colatitude integral is
@@ -272,16 +276,23 @@ s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f
 
 /* ---- runtime: autotuner and batch executor ------------------------------------------
  * s2w_plan_autotune times, on the plan's own shapes and workspace, the candidate launch shapes
- * of its kernels (threads per block of the DFT kernels: 128, 256, 512; maps per block of the
+ * of its kernels (threads per block of the DFT kernels: 128, 256, 384, 512; maps per block of the
  * on-the-fly inverse contraction: 4, 8, 16) for every transform of the plan (spin SHT,
- * scaling function, each wavelet scale) and keeps the fastest.  Synchronises the stream;
- * allocates a pixel scratch for the duration of the call; overwrites the plan's workspaces.
- * The paper has no counterpart (its kernels are compiled by XLA). */
+ * scaling function, each wavelet scale) and keeps the fastest.  In S2W_FP64_TC it also times
+ * both forms of the azimuthal DFTs of each transform and direction (tensor-core, compensated
+ * float32; both float64-accurate) and keeps the faster; without autotuning the tensor-core form
+ * runs wherever its tables exist.  Synchronises the stream; allocates a pixel scratch for the
+ * duration of the call; overwrites the plan's workspaces.  The paper has no counterpart (its
+ * kernels are compiled by XLA). */
 s2w_status s2w_plan_autotune(s2w_plan* plan, void* stream);
 /* The launch shapes in use for transform `transform` (0 = spin SHT, 1 = scaling function,
  * 2 + s = wavelet scale s); any output may be NULL. */
 s2w_status s2w_plan_launch_shapes(const s2w_plan* plan, int transform, int* dft_threads_fwd,
                                   int* dft_threads_inv, int* inv_mb);
+/* The form of the azimuthal DFTs in use for transform `transform` (numbering as above), forward
+ * and inverse: 1 = tensor cores (S2W_FP64_TC with tables for the transform), 0 = the precision
+ * mode's SIMT kernels; either output may be NULL.  The paper has no counterpart. */
+s2w_status s2w_plan_dft_forms(const s2w_plan* plan, int transform, int* tc_fwd, int* tc_inv);
 
 /* A batch runs the transforms of `count` distinct plans (maps of different band-limits, spins
  * and sizes) as one CUDA graph: the plans' calls are captured once on a fork of streams (one

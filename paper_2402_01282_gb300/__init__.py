@@ -31,7 +31,7 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_ball_sl_forward", "s2w_ball_sl_inverse", "s2w_forward_adjoint", "s2w_inverse_adjoint",
            "s2w_ball_wav_plan_create", "s2w_ball_wav_plan_destroy", "s2w_ball_wav_query_layout",
            "s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint",
-           "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_batch_create",
+           "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_plan_dft_forms", "s2w_batch_create",
            "s2w_batch_launch", "s2w_batch_destroy"]
 KERNEL_KINDS = 5
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
     lib.s2w_ball_wav_check.argtypes = [vp]
     lib.s2w_plan_autotune.argtypes = [vp, vp]
     lib.s2w_plan_launch_shapes.argtypes = [vp, ctypes.c_int, ip, ip, ip]
+    lib.s2w_plan_dft_forms.argtypes = [vp, ctypes.c_int, ip, ip]
     vpp = ctypes.POINTER(vp)
     lib.s2w_batch_create.argtypes = [vpp, ctypes.c_int, vpp, vpp, vpp, vpp, ctypes.c_int, vp, vpp]
     lib.s2w_batch_launch.argtypes = [vp, vp]
@@ -274,6 +275,13 @@ class Plan:
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(_lib.s2w_plan_launch_shapes(self._h, transform, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def dft_forms(self, transform: int):
+        """(forward, inverse) form of the azimuthal DFTs of a transform: 1 = tensor cores,
+        0 = the precision mode's SIMT kernels (numbering as in launch_shapes)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.s2w_plan_dft_forms(self._h, transform, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     # ------------------------------------------------------------------ tracing
     def trace(self, on: bool = True, capacity: int = 4096):

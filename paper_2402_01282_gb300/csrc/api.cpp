@@ -220,14 +220,14 @@ namespace s2w {
 cudaError_t launch_dft_forward_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
                                     int64_t pix_sb, ColumnArgs c, cudaStream_t st) {
   if (P->native64) return launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st);
-  if (P->tcx && t.dftx_fwd != nullptr) return launch_dftx_forward(P, g, t, pix, pix_sb, P->real, c, st);
+  if (P->tcx && t.dftx_fwd != nullptr && !t.dft_comp_fwd) return launch_dftx_forward(P, g, t, pix, pix_sb, P->real, c, st);
   return launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st, t.tc != nullptr);
 }
 
 cudaError_t launch_dft_inverse_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
                                     void* pix, int64_t pix_sb, cudaStream_t st) {
   if (P->native64) return launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st);
-  if (P->tcx && t.dftx_inv != nullptr) return launch_dftx_inverse(P, g, t, c, pix, pix_sb, P->real, st);
+  if (P->tcx && t.dftx_inv != nullptr && !t.dft_comp_inv) return launch_dftx_inverse(P, g, t, c, pix, pix_sb, P->real, st);
   return launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr);
 }
 

@@ -96,22 +96,32 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     c.Mc = P->real ? t->L : 2 * t->L - 1;
     c.mlo = P->real ? 0 : -(t->L - 1);
     const int64_t pix_sb = (int64_t)(2 * t->N - 1) * g.nr * (2 * t->L - 1);
+    // S2W_FP64_TC with tensor-core DFT tables: both DFT forms (tensor-core, compensated) are timed
+    const int nforms = (P->tcx && t->dftx_fwd != nullptr) ? 2 : 1;
     float best = 1e30f;
     int pick = t->dft_threads_fwd;
-    for (int th : cand_threads) {
-      t->dft_threads_fwd = th;
-      const float ms = time_best(st, tm, 3, [&] { return launch_dft_forward_mode(P, g, *t, buf, pix_sb, c, st); });
-      if (ms < best) best = ms, pick = th;
-    }
+    bool comp = t->dft_comp_fwd;
+    for (int form = 0; form < nforms; ++form)
+      for (int th : cand_threads) {
+        t->dft_threads_fwd = th;
+        t->dft_comp_fwd = form == 1;
+        const float ms = time_best(st, tm, 3, [&] { return launch_dft_forward_mode(P, g, *t, buf, pix_sb, c, st); });
+        if (ms < best) best = ms, pick = th, comp = form == 1;
+      }
     t->dft_threads_fwd = pick;
+    t->dft_comp_fwd = comp;
     best = 1e30f;
     pick = t->dft_threads_inv;
-    for (int th : cand_threads) {
-      t->dft_threads_inv = th;
-      const float ms = time_best(st, tm, 3, [&] { return launch_dft_inverse_mode(P, g, *t, c, buf, pix_sb, st); });
-      if (ms < best) best = ms, pick = th;
-    }
+    comp = t->dft_comp_inv;
+    for (int form = 0; form < nforms; ++form)
+      for (int th : cand_threads) {
+        t->dft_threads_inv = th;
+        t->dft_comp_inv = form == 1;
+        const float ms = time_best(st, tm, 3, [&] { return launch_dft_inverse_mode(P, g, *t, c, buf, pix_sb, st); });
+        if (ms < best) best = ms, pick = th, comp = form == 1;
+      }
     t->dft_threads_inv = pick;
+    t->dft_comp_inv = comp;
     if (t->tc == nullptr && t->tab == nullptr && t->tcx == nullptr) {
       CoefArgs in;
       in.coef = P->flm_ws;
@@ -144,6 +154,15 @@ s2w_status s2w_plan_launch_shapes(const s2w_plan* P, int transform, int* dft_thr
   if (dft_threads_fwd) *dft_threads_fwd = t.dft_threads_fwd;
   if (dft_threads_inv) *dft_threads_inv = t.dft_threads_inv;
   if (inv_mb) *inv_mb = t.inv_mb;
+  return S2W_OK;
+}
+
+s2w_status s2w_plan_dft_forms(const s2w_plan* P, int transform, int* tc_fwd, int* tc_inv) {
+  if (P == nullptr) return record_error(S2W_EINVAL, "plan is NULL");
+  if (transform < 0 || transform > P->nscales + 1) return record_error(S2W_EINVAL, "transform index out of range");
+  const TransformSpec& t = transform == 0 ? P->sht : transform == 1 ? P->scal_t : P->wav_t[transform - 2];
+  if (tc_fwd) *tc_fwd = (P->tcx && t.dftx_fwd != nullptr && !t.dft_comp_fwd) ? 1 : 0;
+  if (tc_inv) *tc_inv = (P->tcx && t.dftx_inv != nullptr && !t.dft_comp_inv) ? 1 : 0;
   return S2W_OK;
 }
 

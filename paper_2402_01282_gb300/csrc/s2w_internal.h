@@ -136,6 +136,9 @@ struct TransformSpec {
   const DftxTable* dftx_inv = nullptr;
   // launch shapes chosen by s2w_plan_autotune (defaults otherwise)
   int dft_threads_fwd = 256, dft_threads_inv = 256;   // threads per block of the DFT kernels
+  // S2W_FP64_TC: run the compensated-float32 DFTs instead of the tensor-core ones (the autotuner
+  // sets these where they are faster, typically at small band-limits)
+  bool dft_comp_fwd = false, dft_comp_inv = false;
   int inv_mb = 16;                                     // maps per block of the inverse contraction
 };
 
