@@ -53,6 +53,11 @@ def test_invalid_params_rejected_without_gpu(built_lib):
         assert built_lib.s2w_last_error()
     assert built_lib.s2w_plan_destroy(None) == 1
     assert built_lib.s2w_forward(None, None, None, None, None) == 1
+    # the runtime queries on a NULL plan
+    a, b, c = ctypes.c_int(7), ctypes.c_int(7), ctypes.c_int(7)
+    assert built_lib.s2w_plan_launch_shapes(None, 0, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == 1
+    assert built_lib.s2w_plan_dft_forms(None, 0, ctypes.byref(a), ctypes.byref(b)) == 1
+    assert (a.value, b.value) == (7, 7)   # outputs untouched on error
     # Driscoll-Healy above its supported band-limit: unsupported, still before any CUDA call
     p = s2w.Params(600, 2, 0, 0, 0, 1, 0, 0, 2.0, s2w.S2W_SAMPLING_DH)
     assert built_lib.s2w_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == 5
