@@ -122,6 +122,13 @@ s2w_status s2w_plan_create(const s2w_params* params, void* stream, s2w_plan** ou
 /* Frees the plan.  The caller must make sure no work using it is still queued. */
 s2w_status s2w_plan_destroy(s2w_plan* plan);
 
+/* Device memory the plan holds, in bytes (HOST pointers, either may be NULL): *table_bytes its
+ * precomputed tables (Wigner-d tables of the precomputed modes, as in the paper's precompute mode
+ * of Sec. 4.2, quadrature matrices, twiddles, seeds, filters); *workspace_bytes the per-call
+ * scratch sized for its batch (columns, harmonic workspace, data slices).  Temporary tables freed
+ * during plan creation are not counted. */
+s2w_status s2w_plan_device_bytes(const s2w_plan* plan, int64_t* table_bytes, int64_t* workspace_bytes);
+
 /* Sizes (in elements of the plan's pixel type, per map) of the map, the
  * concatenated wavelet coefficients and the scaling coefficients; the number of
  * scales; wav_offsets[0..nscales] (element offsets of each scale inside one map's
@@ -265,13 +272,18 @@ s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
  * when they need it (a host application that owns every device allocation and forbids new
  * ones after start-up, or code running while a CUDA graph is captured, where cudaMalloc is not
  * allowed) and cannot borrow the plan's workspace because another call on the same plan may be
- * running.  The paper has no counterpart: it is a deployment variant of the Eq. 3 transform.
+ * running.  The paper has no counterpart.
  * Its m-column scratch is a fixed 16 MiB device array inside the library (held by every GPU
  * that loads it, until exit): the call allocates nothing and returns S2W_EINVAL when
- * batch * R(L) * Mc exceeds 1,048,576 complex elements (e.g. 16 real MW maps at L = 256).  The first
- * call on a device looks the array's device address up (make it before any stream capture).
- * All calls share the array; calls whose work overlaps on the GPU race on it.  Same arguments,
- * layouts and results as s2w_sht_inverse. */
+ * batch * R(L) * Mc exceeds 1,048,576 complex elements (R(L) = L rings on MW, 2L on DH; e.g. 16
+ * real MW maps at L = 256).  Every call made outside stream capture looks the array's device
+ * address up and caches it per device; a call made during capture uses the cached address, so
+ * make one call on each device before capturing (and again after cudaDeviceReset).  All calls
+ * share the array and it keeps the previous call's contents (every element a call reads it has
+ * written first); calls whose work overlaps on the GPU race on it.  Same arguments and layouts as
+ * s2w_sht_inverse; the l-contraction always runs the on-the-fly Wigner-d recursion (whatever the
+ * plan's precision mode), so the results match s2w_sht_inverse to the float64 tolerance (1e-11
+ * relative), not bit for bit. */
 s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f, void* stream);
 
 /* ---- runtime: autotuner and batch executor ------------------------------------------
@@ -310,8 +322,22 @@ s2w_status s2w_batch_launch(s2w_batch* batch, void* stream);
 s2w_status s2w_batch_destroy(s2w_batch* batch);
 
 /* Synchronises the plan's last stream, then reads and clears the device error word.
- * Returns S2W_OK, S2W_ECUDA (asynchronous CUDA error) or the recorded status. */
+ * Returns S2W_OK, S2W_ECUDA (asynchronous CUDA error) or the recorded status:
+ *   S2W_ETIMEOUT    a bounded mbarrier wait of a tensor-core kernel ran out (the kernel set the
+ *                   word, let its own copies and MMAs in flight land, freed its tensor memory and
+ *                   returned; the outputs of that call are undefined, the context stays usable);
+ *   S2W_ENONFINITE  S2W_FP64_TC only: the exponent pass that reads every value before the
+ *                   tensor-core slicing met a NaN or Inf (in the input, or produced from it), so
+ *                   the outputs of that call are not meaningful.  The other modes do not check and
+ *                   propagate NaN and Inf to the outputs. */
 s2w_status s2w_check(const s2w_plan* plan);
+
+/* Failure-path test hook (the paper has no counterpart): while on != 0, every tensor-core
+ * l-contraction launch of the plan (S2W_FP64_TC) makes its first bounded mbarrier wait wait on a
+ * barrier that nothing completes, so the wait runs out after its poll limit with bulk copies in
+ * flight and the kernel takes its timeout path; s2w_check then returns S2W_ETIMEOUT.  No fault,
+ * trap or hang is involved.  on = 0 restores normal operation. */
+s2w_status s2w_plan_inject_timeout(s2w_plan* plan, int on);
 
 /* Message for the most recent failing call on this thread ("" if none). */
 const char* s2w_last_error(void);

@@ -32,7 +32,8 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_ball_wav_plan_create", "s2w_ball_wav_plan_destroy", "s2w_ball_wav_query_layout",
            "s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint",
            "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_plan_dft_forms", "s2w_batch_create",
-           "s2w_batch_launch", "s2w_batch_destroy"]
+           "s2w_batch_launch", "s2w_batch_destroy", "s2w_plan_device_bytes",
+           "s2w_plan_inject_timeout"]
 KERNEL_KINDS = 5
 
 
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
     lib.s2w_plan_autotune.argtypes = [vp, vp]
     lib.s2w_plan_launch_shapes.argtypes = [vp, ctypes.c_int, ip, ip, ip]
     lib.s2w_plan_dft_forms.argtypes = [vp, ctypes.c_int, ip, ip]
+    lib.s2w_plan_device_bytes.argtypes = [vp, i64p, i64p]
+    lib.s2w_plan_inject_timeout.argtypes = [vp, ctypes.c_int]
     vpp = ctypes.POINTER(vp)
     lib.s2w_batch_create.argtypes = [vpp, ctypes.c_int, vpp, vpp, vpp, vpp, ctypes.c_int, vp, vpp]
     lib.s2w_batch_launch.argtypes = [vp, vp]
@@ -135,15 +138,23 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _ptr(t, real: bool, name: str):
+def _ptr(t, real: bool, name: str, need: int | None = None):
+    """Device address of tensor t after checking what the kernels rely on: a contiguous CUDA
+    tensor of the plan's element type on the CURRENT device (the library launches on the current
+    device and indexes the buffer from its start) holding at least `need` elements (the sizes the
+    C ABI's layouts give; the kernels would read or write past a smaller buffer)."""
     import torch
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, but the current device is cuda:{torch.cuda.current_device()}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     want = torch.float64 if real else torch.complex128
     if t.dtype != want:
         raise ValueError(f"{name} must be {want}, got {t.dtype}")
+    if need is not None and t.numel() < need:
+        raise ValueError(f"{name} holds {t.numel()} elements, the plan needs {need}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -222,47 +233,77 @@ class Plan:
         return wav[:, a:b].view(self.batch, *self.scale_shape(s))
 
     # ------------------------------------------------------------------ transforms
+    # elements of each buffer a call reads or writes (the layouts of include/s2w.h)
+    def _n_map(self):
+        return self.batch * self.map_elems
+
+    def _n_wav(self):
+        return self.batch * self.wav_elems
+
+    def _n_scal(self):
+        return self.batch * self.scal_elems
+
+    def _n_flm(self):
+        return self.batch * self.L * self.Mc
+
+    def _n_scale(self, s: int):
+        if not 0 <= s < self.nscales:
+            raise ValueError(f"scale index {s} out of range [0, {self.nscales})")
+        return self.batch * (self.wav_offsets[s + 1] - self.wav_offsets[s])
+
+    def _n_flmn(self, s: int):
+        Lj, Nj = self.Lj[s], self.Nj[s]
+        return self.batch * (2 * Nj - 1) * Lj * (Lj if self.real else 2 * Lj - 1)
+
     def forward(self, f, wav, scal, stream=None):
-        _check(_lib.s2w_forward(self._h, _ptr(f, self.real, "f"), _ptr(wav, self.real, "wav"),
-                                _ptr(scal, self.real, "scal"), _stream(stream)))
+        _check(_lib.s2w_forward(self._h, _ptr(f, self.real, "f", self._n_map()),
+                                _ptr(wav, self.real, "wav", self._n_wav()),
+                                _ptr(scal, self.real, "scal", self._n_scal()), _stream(stream)))
 
     def inverse(self, wav, scal, f, stream=None):
-        _check(_lib.s2w_inverse(self._h, _ptr(wav, self.real, "wav"), _ptr(scal, self.real, "scal"),
-                                _ptr(f, self.real, "f"), _stream(stream)))
+        _check(_lib.s2w_inverse(self._h, _ptr(wav, self.real, "wav", self._n_wav()),
+                                _ptr(scal, self.real, "scal", self._n_scal()),
+                                _ptr(f, self.real, "f", self._n_map()), _stream(stream)))
 
     def forward_adjoint(self, gwav, gscal, gf, stream=None):
         """gf = A^H (gwav, gscal), A the analysis operator of forward()."""
-        _check(_lib.s2w_forward_adjoint(self._h, _ptr(gwav, self.real, "gwav"), _ptr(gscal, self.real, "gscal"),
-                                        _ptr(gf, self.real, "gf"), _stream(stream)))
+        _check(_lib.s2w_forward_adjoint(self._h, _ptr(gwav, self.real, "gwav", self._n_wav()),
+                                        _ptr(gscal, self.real, "gscal", self._n_scal()),
+                                        _ptr(gf, self.real, "gf", self._n_map()), _stream(stream)))
 
     def inverse_adjoint(self, gf, gwav, gscal, stream=None):
         """(gwav, gscal) = S^H gf, S the synthesis operator of inverse()."""
-        _check(_lib.s2w_inverse_adjoint(self._h, _ptr(gf, self.real, "gf"), _ptr(gwav, self.real, "gwav"),
-                                        _ptr(gscal, self.real, "gscal"), _stream(stream)))
+        _check(_lib.s2w_inverse_adjoint(self._h, _ptr(gf, self.real, "gf", self._n_map()),
+                                        _ptr(gwav, self.real, "gwav", self._n_wav()),
+                                        _ptr(gscal, self.real, "gscal", self._n_scal()), _stream(stream)))
 
     def sht_forward(self, f, flm, stream=None):
-        _check(_lib.s2w_sht_forward(self._h, _ptr(f, self.real, "f"), _ptr(flm, False, "flm"),
-                                    _stream(stream)))
+        _check(_lib.s2w_sht_forward(self._h, _ptr(f, self.real, "f", self._n_map()),
+                                    _ptr(flm, False, "flm", self._n_flm()), _stream(stream)))
 
     def sht_inverse(self, flm, f, stream=None):
-        _check(_lib.s2w_sht_inverse(self._h, _ptr(flm, False, "flm"), _ptr(f, self.real, "f"),
-                                    _stream(stream)))
+        _check(_lib.s2w_sht_inverse(self._h, _ptr(flm, False, "flm", self._n_flm()),
+                                    _ptr(f, self.real, "f", self._n_map()), _stream(stream)))
 
     def sht_inverse_static(self, flm, f, stream=None):
         """s2w_sht_inverse with its scratch in the library's fixed device array (allocates nothing)."""
-        _check(_lib.s2w_sht_inverse_static(self._h, _ptr(flm, False, "flm"), _ptr(f, self.real, "f"),
-                                           _stream(stream)))
+        _check(_lib.s2w_sht_inverse_static(self._h, _ptr(flm, False, "flm", self._n_flm()),
+                                           _ptr(f, self.real, "f", self._n_map()), _stream(stream)))
 
     def wigner_forward(self, s: int, f, flmn, stream=None):
-        _check(_lib.s2w_wigner_forward(self._h, s, _ptr(f, self.real, "f"), _ptr(flmn, False, "flmn"),
-                                       _stream(stream)))
+        _check(_lib.s2w_wigner_forward(self._h, s, _ptr(f, self.real, "f", self._n_scale(s)),
+                                       _ptr(flmn, False, "flmn", self._n_flmn(s)), _stream(stream)))
 
     def wigner_inverse(self, s: int, flmn, f, stream=None):
-        _check(_lib.s2w_wigner_inverse(self._h, s, _ptr(flmn, False, "flmn"), _ptr(f, self.real, "f"),
-                                       _stream(stream)))
+        _check(_lib.s2w_wigner_inverse(self._h, s, _ptr(flmn, False, "flmn", self._n_flmn(s)),
+                                       _ptr(f, self.real, "f", self._n_scale(s)), _stream(stream)))
 
     def check(self):
         _check(_lib.s2w_check(self._h))
+
+    def inject_timeout(self, on: bool = True):
+        """Failure-path test hook: the plan's tensor-core contraction waits run out (S2W_ETIMEOUT)."""
+        _check(_lib.s2w_plan_inject_timeout(self._h, int(on)))
 
     # ------------------------------------------------------------------ runtime
     def autotune(self, stream=None):
@@ -281,6 +322,12 @@ class Plan:
         0 = the precision mode's SIMT kernels (numbering as in launch_shapes)."""
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(_lib.s2w_plan_dft_forms(self._h, transform, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def device_bytes(self):
+        """(table bytes, workspace bytes) of device memory the plan holds."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.s2w_plan_device_bytes(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
     # ------------------------------------------------------------------ tracing
@@ -343,21 +390,27 @@ class BallPlan:
         dt = torch.float64 if self.real else torch.complex128
         return torch.empty((self.batch, self.P, self.R, 2 * self.L - 1), dtype=dt, device=device)
 
+    def _n_coef(self):
+        return self.batch * self.P * self.L * self.Mc
+
+    def _n_pix(self):
+        return self.batch * self.P * self.R * (2 * self.L - 1)
+
     def laguerre_forward(self, f_r, f_p, stream=None):
-        _check(_lib.s2w_laguerre_forward(self._h, _ptr(f_r, False, "f_r"), _ptr(f_p, False, "f_p"),
-                                         _stream(stream)))
+        _check(_lib.s2w_laguerre_forward(self._h, _ptr(f_r, False, "f_r", self._n_coef()),
+                                         _ptr(f_p, False, "f_p", self._n_coef()), _stream(stream)))
 
     def laguerre_inverse(self, f_p, f_r, stream=None):
-        _check(_lib.s2w_laguerre_inverse(self._h, _ptr(f_p, False, "f_p"), _ptr(f_r, False, "f_r"),
-                                         _stream(stream)))
+        _check(_lib.s2w_laguerre_inverse(self._h, _ptr(f_p, False, "f_p", self._n_coef()),
+                                         _ptr(f_r, False, "f_r", self._n_coef()), _stream(stream)))
 
     def sl_forward(self, f, flmp, stream=None):
-        _check(_lib.s2w_ball_sl_forward(self._h, _ptr(f, self.real, "f"), _ptr(flmp, False, "flmp"),
-                                        _stream(stream)))
+        _check(_lib.s2w_ball_sl_forward(self._h, _ptr(f, self.real, "f", self._n_pix()),
+                                        _ptr(flmp, False, "flmp", self._n_coef()), _stream(stream)))
 
     def sl_inverse(self, flmp, f, stream=None):
-        _check(_lib.s2w_ball_sl_inverse(self._h, _ptr(flmp, False, "flmp"), _ptr(f, self.real, "f"),
-                                        _stream(stream)))
+        _check(_lib.s2w_ball_sl_inverse(self._h, _ptr(flmp, False, "flmp", self._n_coef()),
+                                        _ptr(f, self.real, "f", self._n_pix()), _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -380,12 +433,15 @@ class Batch:
         n = len(plans)
         vp = ctypes.c_void_p
 
+        sizes = {"f": lambda p: p._n_map(), "out": lambda p: p._n_map(), "wav": lambda p: p._n_wav(),
+                 "scal": lambda p: p._n_scal()}
+
         def arr(ts, name):
             if ts is None:
                 return None
             a = (vp * n)()
             for i, (t, p) in enumerate(zip(ts, plans)):
-                a[i] = _ptr(t, p.real, name)
+                a[i] = _ptr(t, p.real, name, sizes[name](p))
             return a
         self._keep = (list(plans), f, wav, scal, out)
         hp = (vp * n)(*[p._h for p in plans])
@@ -458,22 +514,30 @@ class BallWavPlan:
         return wav[a:b].view(self.batch, self.Pj[k], 2 * self.Nj[k] - 1, rings(self.Lj[k], self.sampling),
                              2 * self.Lj[k] - 1)
 
+    def _n_field(self):
+        return self.batch * self.field_elems
+
     def forward(self, f, wav, scal, stream=None):
-        _check(_lib.s2w_ball_forward(self._h, _ptr(f, self.real, "f"), _ptr(wav, self.real, "wav"),
-                                     _ptr(scal, self.real, "scal"), _stream(stream)))
+        nf = self._n_field()
+        _check(_lib.s2w_ball_forward(self._h, _ptr(f, self.real, "f", nf), _ptr(wav, self.real, "wav", self.wav_elems),
+                                     _ptr(scal, self.real, "scal", nf), _stream(stream)))
 
     def inverse(self, wav, scal, f, stream=None):
-        _check(_lib.s2w_ball_inverse(self._h, _ptr(wav, self.real, "wav"), _ptr(scal, self.real, "scal"),
-                                     _ptr(f, self.real, "f"), _stream(stream)))
+        nf = self._n_field()
+        _check(_lib.s2w_ball_inverse(self._h, _ptr(wav, self.real, "wav", self.wav_elems),
+                                     _ptr(scal, self.real, "scal", nf), _ptr(f, self.real, "f", nf), _stream(stream)))
 
     def forward_adjoint(self, gwav, gscal, gf, stream=None):
-        _check(_lib.s2w_ball_forward_adjoint(self._h, _ptr(gwav, self.real, "gwav"),
-                                             _ptr(gscal, self.real, "gscal"), _ptr(gf, self.real, "gf"),
+        nf = self._n_field()
+        _check(_lib.s2w_ball_forward_adjoint(self._h, _ptr(gwav, self.real, "gwav", self.wav_elems),
+                                             _ptr(gscal, self.real, "gscal", nf), _ptr(gf, self.real, "gf", nf),
                                              _stream(stream)))
 
     def inverse_adjoint(self, gf, gwav, gscal, stream=None):
-        _check(_lib.s2w_ball_inverse_adjoint(self._h, _ptr(gf, self.real, "gf"), _ptr(gwav, self.real, "gwav"),
-                                             _ptr(gscal, self.real, "gscal"), _stream(stream)))
+        nf = self._n_field()
+        _check(_lib.s2w_ball_inverse_adjoint(self._h, _ptr(gf, self.real, "gf", nf),
+                                             _ptr(gwav, self.real, "gwav", self.wav_elems),
+                                             _ptr(gscal, self.real, "gscal", nf), _stream(stream)))
 
     def check(self):
         _check(_lib.s2w_ball_wav_check(self._h))

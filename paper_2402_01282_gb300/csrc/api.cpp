@@ -268,6 +268,15 @@ const char* s2w_last_error(void) { return g_last_error.c_str(); }
 
 const char* s2w_version(void) { return "s2w-gb300 0.1 (sm_103a, float64)"; }
 
+s2w_status s2w_plan_device_bytes(const s2w_plan* P, int64_t* table_bytes, int64_t* workspace_bytes) {
+  if (P == nullptr) return s2w::record_error(S2W_EINVAL, "plan is NULL");
+  int64_t tot = 0;
+  for (size_t b : P->owned_bytes) tot += (int64_t)b;
+  if (table_bytes) *table_bytes = tot - P->workspace_bytes;
+  if (workspace_bytes) *workspace_bytes = P->workspace_bytes;
+  return S2W_OK;
+}
+
 s2w_status s2w_plan_create(const s2w_params* params, void* stream, s2w_plan** out) {
   if (out == nullptr) return fail(S2W_EINVAL, "out is NULL");
   *out = nullptr;
@@ -481,6 +490,12 @@ s2w_status s2w_check(const s2w_plan* P) {
     cudaMemset(P->err_word, 0, sizeof(int));
     return fail((s2w_status)word, "device error word set");
   }
+  return S2W_OK;
+}
+
+s2w_status s2w_plan_inject_timeout(s2w_plan* P, int on) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  P->inject_timeout = on ? 1 : 0;
   return S2W_OK;
 }
 

@@ -172,6 +172,9 @@ __global__ void k_dftx_fwd_prep(XArgs a) {
           HZ[(j0 + q) * n + al] = z;
           const int e = max(fbound(z.x), fbound(z.z));
           if (e > 0) atomicMax(&emax[j0 + q], e);
+          // a NaN or Inf sample (exponent field all ones) would be sliced as a finite integer
+          if ((__float_as_uint(z.x) & 0x7F800000u) == 0x7F800000u || (__float_as_uint(z.z) & 0x7F800000u) == 0x7F800000u)
+            atomicCAS(a.err, 0, (int)S2W_ENONFINITE);
         }
     }
   }
@@ -229,12 +232,15 @@ __global__ void k_dftx_inv_prep(XArgs a) {
   __syncthreads();
   const int nj = njs;
   int e = 0;
+  bool bad = false;
   for (int i = threadIdx.x; i < a.nact * Mc; i += blockDim.x) {
     const int ni = i / Mc, mi = i - ni * Mc;
     const double2 v = a.Gin[(((int64_t)b * a.nact + ni) * a.nr + t) * Mc + mi];
     Gs[i] = v;
     e = max(e, max(ebound(v.x), ebound(v.y)));
+    bad |= (bexp(v.x) == 0x7FF) | (bexp(v.y) == 0x7FF);   // NaN or Inf: sliced as a finite integer otherwise
   }
+  if (bad) atomicCAS(a.err, 0, (int)S2W_ENONFINITE);
   if (e > 0) atomicMax(&emax, e);
   __syncthreads();
   const int f = emax > 0 ? e_from(emax) + 1 : 0;   // the fold doubles the bound

@@ -50,6 +50,7 @@ constexpr int kStageElems = kAChunk + kBChunk;
 constexpr int kStages = 3;
 constexpr size_t kSmem = (size_t)kStages * kStageElems * sizeof(uint16_t);   // 107520 B
 constexpr uint32_t kWaitIter = 1u << 20;   // bounded mbarrier polls (far above any legitimate wait)
+constexpr uint32_t kInjectIter = 1u << 10;  // polls of the injected wait (s2w_plan_inject_timeout)
 constexpr int kTmemCols = 256;                 // 7 accumulators x 32 columns
 
 
@@ -139,6 +140,7 @@ struct PrepArgs {
   uint16_t* ops;             // destination slices
   int* fexp;                 // [q][Mc * nact][32] column exponent bounds (+ kEOff; 0 = zero column)
   int64_t qstride;           // operand elements per 16-map chunk
+  int* err;                  // plan error word: k_tcxe records S2W_ENONFINITE for a NaN or Inf value
 };
 
 // Source of the data operand at reduction index k of column (mi, ni) for map bm: the pair
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256) k_tcxe(PrepArgs a, int ks_n) {
   colE[t / kN][t % kN] = 0;
   __syncthreads();
   int er = 0, ei = 0;
+  bool bad = false;   // a NaN or Inf (exponent field all ones) among the values read
   for (int kg = ks * (kPrepK / 8) + kg0; kg * 8 < K; kg += kGStride) {
     double2 v[8];
     double r[8];
@@ -202,8 +205,10 @@ __global__ void __launch_bounds__(256) k_tcxe(PrepArgs a, int ks_n) {
     for (int u = 0; u < 8; ++u) {
       er = max(er, ebound_prod(v[u].x, r[u]));
       ei = max(ei, ebound_prod(v[u].y, r[u]));
+      bad |= (bexp(v[u].x) == 0x7FF) | (bexp(v[u].y) == 0x7FF) | (bexp(r[u]) == 0x7FF);
     }
   }
+  if (bad) atomicCAS(a.err, 0, (int)S2W_ENONFINITE);   // the first recorded status is kept
   if (er > 0) atomicMax(&colE[ml][2 * p], er);
   if (ei > 0) atomicMax(&colE[ml][2 * p + 1], ei);
   __syncthreads();
@@ -284,12 +289,13 @@ struct GemmArgs {
   int mlo_out;
   uint32_t idesc;
   int* err;
+  int inject_timeout;       // test hook (s2w_plan_inject_timeout): make a bounded wait run out
 };
 
 template <bool FWD>
 __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bar_ld[kStages], bar_mma[kStages];
+  __shared__ __align__(8) uint64_t bar_ld[kStages], bar_mma[kStages], bar_never;
   __shared__ uint32_t tbase;
   __shared__ int fexp_s[kN];
   const int rt = blockIdx.x, mi = blockIdx.y, ni = blockIdx.z, idx = mi * a.nact + ni;
@@ -312,6 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
       tc::mbar_init(&bar_ld[s], 1);
       tc::mbar_init(&bar_mma[s], 1);
     }
+    tc::mbar_init(&bar_never, 1);   // nothing arrives on it: the injected timeout waits here
   }
   if (warp == 0) tc::tmem_alloc(&tbase, kTmemCols);
   tc::fence_before_sync();
@@ -322,6 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
   const int64_t boff = FWD ? (int64_t)idx * a.Lk * kN * kSl : a.opoff_i[idx];
   constexpr uint32_t stage_bytes = (uint32_t)kStageElems * 2u;
   uint32_t ph_ld[kStages] = {0u, 0u, 0u}, ph_mma[kStages] = {0u, 0u, 0u};
+  unsigned pend_ld = 0u, pend_mma = 0u;   // thread 0: stages with copies / MMAs not yet waited for
   const int row = rt * 128 + warp * 32 + lane;
   const int e_r = a.rexp[(int64_t)idx * a.rstride + row];
   bool ok = true;
@@ -334,8 +342,10 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
         tc::mbar_expect_tx(&bar_ld[s], stage_bytes);
         tc::bulk_g2s(S, a.A + aoff + (int64_t)c * kAChunk, kAChunk * 2u, &bar_ld[s]);
         tc::bulk_g2s(S + kAChunk, bq + (int64_t)c * kBChunk, kBChunk * 2u, &bar_ld[s]);
+        pend_ld |= 1u << s;
       };
-      auto wait = [&](uint64_t* bar, uint32_t& ph) {
+      // bounded wait; `bit` marks the stage's pending copies (pend_ld) or MMAs (pend_mma)
+      auto wait = [&](uint64_t* bar, uint32_t& ph, unsigned& pend, int s) {
         if (!ok) return;
         if (!tc::mbar_wait(bar, ph, kWaitIter)) {
           atomicExch(a.err, (int)S2W_ETIMEOUT);
@@ -343,11 +353,19 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
           return;
         }
         ph ^= 1u;
+        pend &= ~(1u << s);
       };
       for (int c = 0; c < kStages - 1 && c < nkc; ++c) load(c, c);
+      if (a.inject_timeout && q == 0 && !tc::mbar_wait(&bar_never, 0u, kInjectIter)) {
+        // injected failure: a wait that nothing completes runs out (after a short poll limit, so
+        // that a test does not wait for the full one) with copies in flight, and the timeout path
+        // below (error word, settling the copies, freeing TMEM) is the one exercised
+        atomicExch(a.err, (int)S2W_ETIMEOUT);
+        ok = false;
+      }
       for (int c = 0; c < nkc && ok; ++c) {
         const int s = c % kStages;
-        wait(&bar_ld[s], ph_ld[s]);
+        wait(&bar_ld[s], ph_ld[s], pend_ld, s);
         if (!ok) break;
         tc::fence_after_sync();
         const uint32_t A0 = tc::smem_u32(stage0 + s * kStageElems), B0 = A0 + kAChunk * 2u;
@@ -362,10 +380,11 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
             tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kATile * 2 / 16)),
                         dB + (uint64_t)((qq - sa) * (kBTile * 2 / 16)), a.idesc, sa > 0 ? 1u : acc0);
         tc::mma_commit(&bar_mma[s]);
+        pend_mma |= 1u << s;
         if (c + kStages - 1 < nkc) {
           // the stage of chunk c + 2 last held chunk c - 1: its MMAs must be done
           const int sn = (c + kStages - 1) % kStages;
-          if (c >= 1) wait(&bar_mma[sn], ph_mma[sn]);
+          if (c >= 1) wait(&bar_mma[sn], ph_mma[sn], pend_mma, sn);
           if (!ok) break;
           load(c + kStages - 1, sn);
         }
@@ -373,7 +392,15 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
       // the MMAs still outstanding: chunks max(0, nkc - 3) .. nkc - 1 (every earlier chunk was
       // waited for before its stage was reloaded)
       for (int c = nkc > kStages ? nkc - kStages : 0; c < nkc && ok; ++c)
-        wait(&bar_mma[c % kStages], ph_mma[c % kStages]);
+        wait(&bar_mma[c % kStages], ph_mma[c % kStages], pend_mma, c % kStages);
+      if (!ok) {
+        // after a timeout: let this CTA's own copies and MMAs in flight land (bounded) before
+        // the CTA frees its TMEM and exits
+        for (int s = 0; s < kStages; ++s) {
+          if (pend_ld & (1u << s)) tc::mbar_wait(&bar_ld[s], ph_ld[s], kWaitIter);
+          if (pend_mma & (1u << s)) tc::mbar_wait(&bar_mma[s], ph_mma[s], kWaitIter);
+        }
+      }
     }
     ok = __syncthreads_and(ok);
     if (!ok) break;
@@ -501,6 +528,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_i;
+  pa.err = P->err_word;
   const int ksn = (tab.kli_max + kPrepK - 1) / kPrepK;   // 0 when every multiplier is zero
   cudaError_t e = cudaMemsetAsync(pa.fexp, 0, (size_t)nq * out.Mc * t.nact * kN * sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -535,6 +563,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   a.idesc = tc::make_idesc(128, kN, 1, 0, 0);   // bf16 slices
   a.lmin = tab.lmin;
   a.err = P->err_word;
+  a.inject_timeout = P->inject_timeout;
   e = cudaFuncSetAttribute(k_tcx_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
   k_tcx_gemm<false><<<dim3(tab.Lb / 128, out.Mc, t.nact), kThreads, kSmem, st>>>(a);
@@ -561,6 +590,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   pa.ops = P->tcx_ops;
   pa.fexp = P->tcx_fexp;
   pa.qstride = tab.op_f;
+  pa.err = P->err_word;
   const int ksn = (tab.Lk + kPrepK - 1) / kPrepK;
   cudaError_t e = cudaMemsetAsync(pa.fexp, 0, (size_t)nq * in.Mc * t.nact * kN * sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -595,6 +625,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   a.idesc = tc::make_idesc(128, kN, 1, 0, 0);   // bf16 slices
   a.lmin = tab.lmin;
   a.err = P->err_word;
+  a.inject_timeout = P->inject_timeout;
   e = cudaFuncSetAttribute(k_tcx_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
   if (tab.klf_max == 0) return cudaSuccess;

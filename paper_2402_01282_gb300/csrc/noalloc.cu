@@ -10,9 +10,12 @@
 // allocating routine.
 //
 // Device address: host code cannot hand `g_static_cols` itself to a kernel (in host code that
-// name is a host-side stand-in, not a device address).  The first call on each device, with
-// that device current, asks the runtime for the address with cudaGetSymbolAddress and caches
-// it; make that first call before any stream capture begins.
+// name is a host-side stand-in, not a device address).  Every call made while its stream is NOT
+// being captured asks the runtime for the address with cudaGetSymbolAddress, with the call's
+// device current, and caches it per device; a call made during stream capture uses the cached
+// address without any runtime lookup, so the first call on a device must come before any
+// capture.  A cached address is only valid while the device's context lives: after
+// cudaDeviceReset, make one uncaptured call again before capturing.
 //
 // Sharing: all calls (on every plan and stream of a device) share the one array and it keeps
 // the previous call's contents.  The kernels overwrite every element they later read, so
@@ -50,19 +53,28 @@ extern "C" s2w_status s2w_sht_inverse_static(const s2w_plan* cP, const void* flm
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return record_error(S2W_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return record_error(S2W_EUNSUPPORTED, "device index out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess)
+    return record_error(S2W_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   double2* cols = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_ptr[dev] == nullptr) {
+    if (cap == cudaStreamCaptureStatusNone) {
+      // refresh the address on every uncaptured call: it changes if the context was re-created
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_static_cols);
       if (e != cudaSuccess)
         return record_error(S2W_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_ptr[dev] = static_cast<double2*>(p);
+    } else if (g_ptr[dev] == nullptr) {
+      return record_error(S2W_EINVAL,
+                          "s2w_sht_inverse_static: first call on this device made during stream capture; "
+                          "make one call before capturing");
     }
     cols = g_ptr[dev];
   }
-  cudaStream_t st = (cudaStream_t)stream;
   P->last_stream = st;
   const TransformSpec& t = P->sht;
   const GridTables& g = P->grids[t.grid];

@@ -97,6 +97,7 @@ s2w_status upload(s2w_plan* P, const std::vector<T>& h, T** d, cudaStream_t st, 
     return S2W_ENOMEM;
   }
   P->owned.push_back(p);
+  P->owned_bytes.push_back(h.size() * sizeof(T));
   if (cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     err = "cudaMemcpyAsync failed while uploading a plan table";
     return S2W_ECUDA;
@@ -309,6 +310,23 @@ s2w_status build_spec(s2w_plan* P, cudaStream_t st, TransformSpec& t, int L, int
   return S2W_OK;
 }
 
+// Workspace (per-call scratch sized for the batch, as opposed to the plan's tables): counted in
+// P->workspace_bytes for s2w_plan_device_bytes.
+template <class T>
+s2w_status alloc_ws(s2w_plan* P, size_t n, T** d, std::string& err) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "workspace allocation failed";
+    return S2W_ENOMEM;
+  }
+  P->owned.push_back(q);
+  P->owned_bytes.push_back(n * sizeof(T));
+  P->workspace_bytes += (int64_t)(n * sizeof(T));
+  *d = static_cast<T*>(q);
+  return S2W_OK;
+}
+
 template <class T>
 s2w_status alloc_dev(s2w_plan* P, size_t n, T** d, std::string& err) {
   void* q = nullptr;
@@ -318,6 +336,7 @@ s2w_status alloc_dev(s2w_plan* P, size_t n, T** d, std::string& err) {
     return S2W_ENOMEM;
   }
   P->owned.push_back(q);
+  P->owned_bytes.push_back(n * sizeof(T));
   *d = static_cast<T*>(q);
   return S2W_OK;
 }
@@ -394,12 +413,13 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     }
     for (size_t i = mark; i < P->owned.size(); ++i) cudaFree(P->owned[i]);
     P->owned.resize(mark);
+    P->owned_bytes.resize(mark);
     cache[key] = tab;
     t->tc = tab;
   }
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tc_b_hi, err));
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tc_b_lo, err));
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * sc_max, 1), &P->tc_scale, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tc_b_hi, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tc_b_lo, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(nq * sc_max, 1), &P->tc_scale, err));
   return S2W_OK;
 }
 
@@ -473,11 +493,12 @@ s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     }
     for (size_t i = mark; i < P->owned.size(); ++i) cudaFree(P->owned[i]);
     P->owned.resize(mark);
+    P->owned_bytes.resize(mark);
     cache[key] = tab;
     t->tcx = tab;
   }
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tcx_ops, err));
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(nq * fx_max, 1), &P->tcx_fexp, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(nq * op_max, 1), &P->tcx_ops, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(nq * fx_max, 1), &P->tcx_fexp, err));
   return S2W_OK;
 }
 
@@ -515,8 +536,8 @@ s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     ops = std::max(ops, dftx_ops_elems(*t, P->real, P->p.batch, nr));
     fx = std::max(fx, dftx_fexp_elems(P->p.batch, nr));
   }
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(ops, 1), &P->dftx_ops, err));
-  S2W_TRY(alloc_dev(P, (size_t)std::max<int64_t>(fx, 1), &P->dftx_fexp, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(ops, 1), &P->dftx_ops, err));
+  S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(fx, 1), &P->dftx_fexp, err));
   return S2W_OK;
 }
 
@@ -718,16 +739,9 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     gmax = std::max(gmax, B * (2 * P->Nj[sc] - 1) * (int64_t)rings_of(smp, P->Lj[sc]) * Mcj);
   }
   P->g_ws_elems = gmax;
-  void* q = nullptr;
-  if (cudaMalloc(&q, gmax * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); err = "workspace allocation failed"; return S2W_ENOMEM; }
-  P->owned.push_back(q);
-  P->g_ws = (double2*)q;
-  if (cudaMalloc(&q, B * (int64_t)L * P->Mc * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); err = "workspace allocation failed"; return S2W_ENOMEM; }
-  P->owned.push_back(q);
-  P->flm_ws = (double2*)q;
-  if (cudaMalloc(&q, sizeof(int)) != cudaSuccess) { cudaGetLastError(); err = "workspace allocation failed"; return S2W_ENOMEM; }
-  P->owned.push_back(q);
-  P->err_word = (int*)q;
+  S2W_TRY(alloc_ws(P, (size_t)gmax, &P->g_ws, err));
+  S2W_TRY(alloc_ws(P, (size_t)(B * (int64_t)L * P->Mc), &P->flm_ws, err));
+  S2W_TRY(alloc_ws(P, 1, &P->err_word, err));
   if (cudaMemsetAsync(P->err_word, 0, sizeof(int), st) != cudaSuccess) { err = "memset failed"; return S2W_ECUDA; }
   if (cudaStreamSynchronize(st) != cudaSuccess) { err = "plan upload failed"; return S2W_ECUDA; }
   return S2W_OK;
@@ -736,6 +750,8 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
 void free_plan(s2w_plan* P) {
   for (void* q : P->owned) cudaFree(q);
   P->owned.clear();
+  P->owned_bytes.clear();
+  P->workspace_bytes = 0;
   for (TcTable* t : P->tc_tables) delete t;
   P->tc_tables.clear();
   for (TabTable* t : P->tab_tables) delete t;

@@ -181,8 +181,11 @@ struct s2w_plan {
   double2* g_ws = nullptr;             // largest [batch][nact or 2N-1][rings_j][Mc_j] column buffer
   int64_t g_ws_elems = 0;
   int* err_word = nullptr;             // device error word
+  int inject_timeout = 0;              // test hook: tensor-core contraction waits run out (s2w_plan_inject_timeout)
   cudaStream_t last_stream = nullptr;
   std::vector<void*> owned;            // every device allocation, freed on destroy
+  std::vector<size_t> owned_bytes;     // their sizes
+  int64_t workspace_bytes = 0;         // the part of them that is per-call scratch
 
   // tracing
   bool trace_on = false;

@@ -58,6 +58,11 @@ def test_invalid_params_rejected_without_gpu(built_lib):
     assert built_lib.s2w_plan_launch_shapes(None, 0, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == 1
     assert built_lib.s2w_plan_dft_forms(None, 0, ctypes.byref(a), ctypes.byref(b)) == 1
     assert (a.value, b.value) == (7, 7)   # outputs untouched on error
+    t, w = ctypes.c_int64(7), ctypes.c_int64(7)
+    assert built_lib.s2w_plan_device_bytes(None, ctypes.byref(t), ctypes.byref(w)) == 1
+    assert (t.value, w.value) == (7, 7)
+    assert built_lib.s2w_plan_inject_timeout(None, 1) == 1
+    assert built_lib.s2w_check(None) == 1
     # Driscoll-Healy above its supported band-limit: unsupported, still before any CUDA call
     p = s2w.Params(600, 2, 0, 0, 0, 1, 0, 0, 2.0, s2w.S2W_SAMPLING_DH)
     assert built_lib.s2w_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == 5
