@@ -571,7 +571,9 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "L": L, "N": N, "lambda": LAM, "J0": J0, "spin": 0,
                    "maps_per_gpu": B, "precision": args.precision, "precompute": PRECOMPUTE.get(args.precision, 0),
                    "launch_shapes": None if args.no_autotune else [plan.launch_shapes(k) for k in range(plan.nscales + 2)],
-                   "dft_tensor_cores": dft_forms,
+                   "dft_forms": dft_forms,
+                   "dft_forms_key": "per transform (SHT, scaling, scales) forward/inverse: 2 tensor-core "
+                                    "prime-factor, 1 tensor-core direct, 0 SIMT",
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MB write)"},
         "precision_detail": PRECISION_DOC[args.precision],
@@ -590,12 +592,12 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
                 "d2h_bytes_per_step": int(f.numel() * 8), "max_rel_err": e2e_err},
         # the trace records one region per DFT and per contraction; a contraction region launches
-        # KERNELS_PER_CONTRACTION[precision] kernels of the library, a DFT region 2 in the
-        # tensor-core form (prologue + GEMM) and 1 otherwise (every transform's forward and inverse
-        # DFT once per step)
+        # KERNELS_PER_CONTRACTION[precision] kernels of the library, a DFT region 2 in the direct
+        # tensor-core form (prologue + GEMM) and 1 in the prime-factor and SIMT forms (every
+        # transform's forward and inverse DFT once per step)
         "gpu_launches": int(sum(v[0] * KERNELS_PER_CONTRACTION.get(args.precision, 1)
                                 for k, v in trace.items() if k.startswith("wigner"))
-                            + args.steps * sum(2 if tc else 1 for pair in dft_forms for tc in pair)),
+                            + args.steps * sum(2 if form == 1 else 1 for pair in dft_forms for form in pair)),
     }
     if world == 1 and not args.no_cpu_baseline:
         dt, cerr = cpu_baseline_sample()

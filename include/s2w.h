@@ -302,9 +302,18 @@ s2w_status s2w_plan_autotune(s2w_plan* plan, void* stream);
 s2w_status s2w_plan_launch_shapes(const s2w_plan* plan, int transform, int* dft_threads_fwd,
                                   int* dft_threads_inv, int* inv_mb);
 /* The form of the azimuthal DFTs in use for transform `transform` (numbering as above), forward
- * and inverse: 1 = tensor cores (S2W_FP64_TC with tables for the transform), 0 = the precision
- * mode's SIMT kernels; either output may be NULL.  The paper has no counterpart. */
+ * and inverse: 2 = tensor cores, prime-factor form (S2W_FP64_TC where 2L-1 = n1 n2 fits the
+ * kernel: the n2-point stage an exact sliced GEMM against a table resident in shared memory, the
+ * n1-point stage and the gamma DFT in compensated float32, one persistent kernel per direction;
+ * the default wherever its tables exist), 1 = tensor cores, direct form (the symmetric
+ * odd-length DFT as two sliced GEMMs streaming their twiddle tables), 0 = the precision mode's
+ * SIMT kernels; either output may be NULL.  The paper has no counterpart. */
 s2w_status s2w_plan_dft_forms(const s2w_plan* plan, int transform, int* tc_fwd, int* tc_inv);
+/* Forces the forms of transform `transform`'s azimuthal DFTs (codes as above, -1 = the default);
+ * S2W_EUNSUPPORTED if the plan has no tables for a requested tensor-core form (every form is
+ * float64-accurate, so results agree to the float64 tolerance).  For tests and comparisons; the
+ * paper has no counterpart. */
+s2w_status s2w_plan_set_dft_forms(s2w_plan* plan, int transform, int fwd, int inv);
 
 /* A batch runs the transforms of `count` distinct plans (maps of different band-limits, spins
  * and sizes) as one CUDA graph: the plans' calls are captured once on a fork of streams (one

@@ -33,7 +33,7 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint",
            "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_plan_dft_forms", "s2w_batch_create",
            "s2w_batch_launch", "s2w_batch_destroy", "s2w_plan_device_bytes",
-           "s2w_plan_inject_timeout"]
+           "s2w_plan_inject_timeout", "s2w_plan_set_dft_forms"]
 KERNEL_KINDS = 5
 
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.s2w_plan_autotune.argtypes = [vp, vp]
     lib.s2w_plan_launch_shapes.argtypes = [vp, ctypes.c_int, ip, ip, ip]
     lib.s2w_plan_dft_forms.argtypes = [vp, ctypes.c_int, ip, ip]
+    lib.s2w_plan_set_dft_forms.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.s2w_plan_device_bytes.argtypes = [vp, i64p, i64p]
     lib.s2w_plan_inject_timeout.argtypes = [vp, ctypes.c_int]
     vpp = ctypes.POINTER(vp)
@@ -318,11 +319,16 @@ class Plan:
         return a.value, b.value, c.value
 
     def dft_forms(self, transform: int):
-        """(forward, inverse) form of the azimuthal DFTs of a transform: 1 = tensor cores,
-        0 = the precision mode's SIMT kernels (numbering as in launch_shapes)."""
+        """(forward, inverse) form of the azimuthal DFTs of a transform: 2 = tensor cores,
+        prime-factor form; 1 = tensor cores, direct form; 0 = the precision mode's SIMT kernels
+        (numbering as in launch_shapes)."""
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(_lib.s2w_plan_dft_forms(self._h, transform, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def set_dft_forms(self, transform: int, fwd: int, inv: int):
+        """Forces the DFT forms of a transform (codes of dft_forms, -1 = default)."""
+        _check(_lib.s2w_plan_set_dft_forms(self._h, transform, fwd, inv))
 
     def device_bytes(self):
         """(table bytes, workspace bytes) of device memory the plan holds."""

@@ -217,18 +217,35 @@ size_t pix_bytes(const s2w_plan* P) { return P->real ? sizeof(double) : sizeof(d
 }  // namespace
 
 namespace s2w {
+int dft_form_used(const s2w_plan* P, const TransformSpec& t, bool fwd) {
+  if (!P->tcx) return kDftComp;
+  const int f = fwd ? t.dft_form_fwd : t.dft_form_inv;
+  const bool pfa = (fwd ? (const void*)t.dftp_fwd : (const void*)t.dftp_inv) != nullptr;
+  const bool gemm = (fwd ? (const void*)t.dftx_fwd : (const void*)t.dftx_inv) != nullptr;
+  if (f == kDftComp) return kDftComp;
+  if (f == kDftPfa && pfa) return kDftPfa;
+  if (f == kDftGemm && gemm) return kDftGemm;
+  return pfa ? kDftPfa : gemm ? kDftGemm : kDftComp;
+}
+
 cudaError_t launch_dft_forward_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
                                     int64_t pix_sb, ColumnArgs c, cudaStream_t st) {
   if (P->native64) return launch_dft_forward(P, g, t, pix, pix_sb, P->real, c, st);
-  if (P->tcx && t.dftx_fwd != nullptr && !t.dft_comp_fwd) return launch_dftx_forward(P, g, t, pix, pix_sb, P->real, c, st);
-  return launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st, t.tc != nullptr);
+  switch (dft_form_used(P, t, true)) {
+    case kDftPfa: return launch_dftp_forward(P, g, t, pix, pix_sb, P->real, c, st);
+    case kDftGemm: return launch_dftx_forward(P, g, t, pix, pix_sb, P->real, c, st);
+    default: return launch_dftc_forward(g, t, pix, pix_sb, P->real, c, st, t.tc != nullptr);
+  }
 }
 
 cudaError_t launch_dft_inverse_mode(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
                                     void* pix, int64_t pix_sb, cudaStream_t st) {
   if (P->native64) return launch_dft_inverse(P, g, t, c, pix, pix_sb, P->real, st);
-  if (P->tcx && t.dftx_inv != nullptr && !t.dft_comp_inv) return launch_dftx_inverse(P, g, t, c, pix, pix_sb, P->real, st);
-  return launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr);
+  switch (dft_form_used(P, t, false)) {
+    case kDftPfa: return launch_dftp_inverse(P, g, t, c, pix, pix_sb, P->real, st);
+    case kDftGemm: return launch_dftx_inverse(P, g, t, c, pix, pix_sb, P->real, st);
+    default: return launch_dftc_inverse(g, t, c, pix, pix_sb, P->real, st, t.tc != nullptr);
+  }
 }
 
 // Lets other translation units report through s2w_last_error().

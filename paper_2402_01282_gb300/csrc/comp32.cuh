@@ -53,12 +53,18 @@ namespace s2w {
 // hi = v truncated to 24 significant bits, lo = the remaining 29 mantissa bits truncated to
 // 24, so hi + lo = v to 2^-48 relative.  |v| < 2^-126 returns (0, 0) and lo is dropped once it
 // falls below the float range (|v| < ~2^-75): both are far below any term these kernels sum.
+// NaN stays NaN, and Inf or a value beyond the float range (|v| >= 2^128) becomes Inf, so that
+// a non-finite input stays visible to the checks downstream instead of becoming a finite float.
 __device__ __forceinline__ float2 split1_bits(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const unsigned int hi32 = (unsigned int)(u >> 32), lo32 = (unsigned int)u;
   const int E = (int)((hi32 >> 20) & 0x7FFu) - 1023;
   if (E < -126) return make_float2(0.f, 0.f);
   const unsigned int sign = hi32 & 0x80000000u;
+  if (E >= 128) {
+    const bool nan = E == 1024 && ((hi32 & 0xFFFFFu) | lo32) != 0u;
+    return make_float2(__uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.f);
+  }
   const unsigned int mant23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
   const float h = __uint_as_float(sign | ((unsigned int)(E + 127) << 23) | mant23);
   const unsigned int r = lo32 & 0x1FFFFFFFu;

@@ -57,24 +57,6 @@ constexpr int kXTmem = 256;               // 7 accumulators x 32 columns
 constexpr int kXMaxJobs = 16;             // jobs per ring (cpr <= 32)
 static_assert((size_t)kXN / 2 * 2 * 128 * sizeof(float4) <= kXSmem, "inverse epilogue staging");
 
-// round(x 2^(47 - f)) for a float x with |x| < 2^f, by integer operations on its fields
-__device__ __forceinline__ long long fixf(float x, int f) {
-  const unsigned int u = __float_as_uint(x);
-  const int E = (int)((u >> 23) & 0xFFu);
-  if (E == 0) return 0;
-  const long long M = (long long)((u & 0x7FFFFFu) | 0x800000u);   // |x| = M 2^(E - 150)
-  const int sh = 103 + f - E;                                       // X = M 2^-sh
-  long long X;
-  if (sh <= 0) X = M << (-sh);
-  else if (sh >= 25) X = 0;
-  else X = (M + (1ll << (sh - 1))) >> sh;
-  return (u >> 31) ? -X : X;
-}
-// exponent bound of a float pair hi + lo (renormalised): |hi + lo| < 2^e; 0 for zero
-__device__ __forceinline__ int fbound(float hi) {
-  const int E = (int)((__float_as_uint(hi) >> 23) & 0xFFu);
-  return E > 0 ? E - 126 + kEOff : 0;
-}
 
 struct XArgs {
   // prep
@@ -613,19 +595,6 @@ cudaError_t launch_gemm(K kern, cudaStream_t st, XArgs a) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
-}
-
-// host: 7 bf16 slices of round(v 2^(47 - e)), the device digit convention (slice7.cuh)
-void host_digits(double v, int e, uint16_t (&d)[kSl]) {
-  const long long X = std::llround(std::ldexp(v, 47 - e));
-  const unsigned long long Y = (unsigned long long)(X + kDigitBias);
-  for (int i = 0; i < kSl; ++i) {
-    const int u = (int)((Y >> (7 * (kSl - 1 - i))) & 127u) - 64;
-    const float f = (float)u;
-    uint32_t bits;
-    std::memcpy(&bits, &f, sizeof(bits));
-    d[i] = (uint16_t)(bits >> 16);
-  }
 }
 
 int host_core16(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }

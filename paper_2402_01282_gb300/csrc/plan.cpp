@@ -528,7 +528,30 @@ s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     *out = tab;
     return S2W_OK;
   };
+  // prime-factor tables (kernels_dftp.cu), per (L, n1, normalisation)
+  std::map<std::tuple<int, int, double>, DftpTable*> pcache;
+  auto ptable = [&](int L, int n1, int n2, double scale, const DftpTable** out) -> s2w_status {
+    auto key = std::make_tuple(L, n1, scale);
+    auto it = pcache.find(key);
+    if (it != pcache.end()) {
+      *out = it->second;
+      return S2W_OK;
+    }
+    DftpTable* tab = new DftpTable();
+    P->dftp_tables.push_back(tab);
+    std::vector<uint16_t> h;
+    build_dftp_table(L, n1, n2, scale, tab, h);
+    S2W_TRY(upload(P, h, &tab->tab, st, err));
+    pcache[key] = tab;
+    *out = tab;
+    return S2W_OK;
+  };
   for (TransformSpec* t : specs) {
+    int n1 = 0, n2 = 0;
+    if (dftp_shape(*t, P->real, &n1, &n2)) {
+      S2W_TRY(ptable(t->L, n1, n2, 1.0, &t->dftp_inv));
+      S2W_TRY(ptable(t->L, n1, n2, (2.0 * kPi / (2.0 * t->L - 1.0)) * t->gscale, &t->dftp_fwd));
+    }
     if (!dftx_shape_ok(*t, P->real)) continue;
     const int nr = rings_of(P->p.sampling, t->L);
     S2W_TRY(table(t->L, 1.0, &t->dftx_inv));
@@ -760,6 +783,8 @@ void free_plan(s2w_plan* P) {
   P->tcx_tables.clear();
   for (DftxTable* t : P->dftx_tables) delete t;
   P->dftx_tables.clear();
+  for (DftpTable* t : P->dftp_tables) delete t;
+  P->dftp_tables.clear();
 }
 
 }  // namespace s2w

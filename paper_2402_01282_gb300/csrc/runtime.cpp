@@ -96,32 +96,34 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     c.Mc = P->real ? t->L : 2 * t->L - 1;
     c.mlo = P->real ? 0 : -(t->L - 1);
     const int64_t pix_sb = (int64_t)(2 * t->N - 1) * g.nr * (2 * t->L - 1);
-    // S2W_FP64_TC with tensor-core DFT tables: both DFT forms (tensor-core, compensated) are timed
-    const int nforms = (P->tcx && t->dftx_fwd != nullptr) ? 2 : 1;
+    // S2W_FP64_TC: every DFT form with tables for the transform is timed (prime-factor tensor-core
+    // kernel: fixed launch shape; direct tensor-core GEMM and compensated float32: each thread count)
+    for (int dir = 0; dir < 2; ++dir) {
+      const bool fwd = dir == 0;
+      int& form = fwd ? t->dft_form_fwd : t->dft_form_inv;
+      int& threads = fwd ? t->dft_threads_fwd : t->dft_threads_inv;
+      std::vector<int> forms = {kDftComp};
+      if (P->tcx && (fwd ? (const void*)t->dftx_fwd : (const void*)t->dftx_inv) != nullptr) forms.push_back(kDftGemm);
+      if (P->tcx && (fwd ? (const void*)t->dftp_fwd : (const void*)t->dftp_inv) != nullptr) forms.push_back(kDftPfa);
+      if (!P->tcx) forms = {kDftAuto};
+      float best = 1e30f;
+      int pick_th = threads, pick_form = form;
+      for (int fm : forms)
+        for (int th : cand_threads) {
+          if (fm == kDftPfa && th != cand_threads[0]) continue;   // one launch shape
+          threads = th;
+          form = fm;
+          const float ms = time_best(st, tm, 3, [&] {
+            return fwd ? launch_dft_forward_mode(P, g, *t, buf, pix_sb, c, st)
+                       : launch_dft_inverse_mode(P, g, *t, c, buf, pix_sb, st);
+          });
+          if (ms < best) best = ms, pick_th = th, pick_form = fm;
+        }
+      threads = pick_th;
+      form = pick_form;
+    }
     float best = 1e30f;
-    int pick = t->dft_threads_fwd;
-    bool comp = t->dft_comp_fwd;
-    for (int form = 0; form < nforms; ++form)
-      for (int th : cand_threads) {
-        t->dft_threads_fwd = th;
-        t->dft_comp_fwd = form == 1;
-        const float ms = time_best(st, tm, 3, [&] { return launch_dft_forward_mode(P, g, *t, buf, pix_sb, c, st); });
-        if (ms < best) best = ms, pick = th, comp = form == 1;
-      }
-    t->dft_threads_fwd = pick;
-    t->dft_comp_fwd = comp;
-    best = 1e30f;
-    pick = t->dft_threads_inv;
-    comp = t->dft_comp_inv;
-    for (int form = 0; form < nforms; ++form)
-      for (int th : cand_threads) {
-        t->dft_threads_inv = th;
-        t->dft_comp_inv = form == 1;
-        const float ms = time_best(st, tm, 3, [&] { return launch_dft_inverse_mode(P, g, *t, c, buf, pix_sb, st); });
-        if (ms < best) best = ms, pick = th, comp = form == 1;
-      }
-    t->dft_threads_inv = pick;
-    t->dft_comp_inv = comp;
+    int pick = 0;
     if (t->tc == nullptr && t->tab == nullptr && t->tcx == nullptr) {
       CoefArgs in;
       in.coef = P->flm_ws;
@@ -157,12 +159,36 @@ s2w_status s2w_plan_launch_shapes(const s2w_plan* P, int transform, int* dft_thr
   return S2W_OK;
 }
 
+s2w_status s2w_plan_set_dft_forms(s2w_plan* P, int transform, int fwd, int inv) {
+  if (P == nullptr) return record_error(S2W_EINVAL, "plan is NULL");
+  if (transform < 0 || transform > P->nscales + 1) return record_error(S2W_EINVAL, "transform index out of range");
+  if (fwd < -1 || fwd > 2 || inv < -1 || inv > 2) return record_error(S2W_EINVAL, "DFT form must be -1, 0, 1 or 2");
+  TransformSpec& t = transform == 0 ? P->sht : transform == 1 ? P->scal_t : P->wav_t[transform - 2];
+  auto to_form = [&](int code, bool f) -> int {
+    if (code < 0) return kDftAuto;
+    if (code == 0) return kDftComp;
+    const void* tab = code == 2 ? (f ? (const void*)t.dftp_fwd : (const void*)t.dftp_inv)
+                                : (f ? (const void*)t.dftx_fwd : (const void*)t.dftx_inv);
+    return (P->tcx && tab != nullptr) ? (code == 2 ? kDftPfa : kDftGemm) : -1;
+  };
+  const int ff = to_form(fwd, true), fi = to_form(inv, false);
+  if (ff < 0 || fi < 0)
+    return record_error(S2W_EUNSUPPORTED, "that DFT form has no tables for this transform (S2W_FP64_TC only)");
+  t.dft_form_fwd = ff;
+  t.dft_form_inv = fi;
+  return S2W_OK;
+}
+
 s2w_status s2w_plan_dft_forms(const s2w_plan* P, int transform, int* tc_fwd, int* tc_inv) {
   if (P == nullptr) return record_error(S2W_EINVAL, "plan is NULL");
   if (transform < 0 || transform > P->nscales + 1) return record_error(S2W_EINVAL, "transform index out of range");
   const TransformSpec& t = transform == 0 ? P->sht : transform == 1 ? P->scal_t : P->wav_t[transform - 2];
-  if (tc_fwd) *tc_fwd = (P->tcx && t.dftx_fwd != nullptr && !t.dft_comp_fwd) ? 1 : 0;
-  if (tc_inv) *tc_inv = (P->tcx && t.dftx_inv != nullptr && !t.dft_comp_inv) ? 1 : 0;
+  auto code = [&](bool fwd) {
+    const int f = dft_form_used(P, t, fwd);
+    return f == kDftPfa ? 2 : f == kDftGemm ? 1 : 0;
+  };
+  if (tc_fwd) *tc_fwd = code(true);
+  if (tc_inv) *tc_inv = code(false);
   return S2W_OK;
 }
 

@@ -105,6 +105,20 @@ struct DftxTable {
   uint16_t* sin = nullptr;
 };
 
+// Sliced n2-point table of the prime-factor tensor-core DFTs (S2W_FP64_TC, kernels_dftp.cu) for
+// n = 2L - 1 = n1 n2 and one normalisation s: rows 2j / 2j + 1 = s cos / s sin(2 pi p2 j/n2),
+// j <= (n2-1)/2, reduction index p2 < n2 (K rounded up to 16), seven bf16 slices in
+// [chunk][slice][Rs x 16] core-matrix tiles; e1, e2 the output (CRT) index map.
+struct DftpTable {
+  int n = 0, n1 = 1, n2 = 1;
+  int Rs = 0;                  // stored rows: n2 + 1 rounded up to 8
+  int nkc = 0;                 // K chunks of 16
+  int e = 0;                   // every entry |v| < 2^e
+  int e1 = 0, e2 = 0;          // k = (k1 e1 + k2 e2) mod n
+  double scale = 1.0;
+  uint16_t* tab = nullptr;
+};
+
 // One Wigner / SHT transform instance: band-limit, the n values it carries and the
 // per-(l, n) multipliers that fuse the harmonic products into the contraction.
 struct TransformSpec {
@@ -134,13 +148,21 @@ struct TransformSpec {
   // (2 pi/(2L-1)) gscale folded in; inverse: 1), null where the compensated DFTs run
   const DftxTable* dftx_fwd = nullptr;
   const DftxTable* dftx_inv = nullptr;
+  // S2W_FP64_TC: the prime-factor tensor-core DFT tables (null where the length or the jobs do not
+  // fit kernels_dftp.cu); where present this is the default form
+  const DftpTable* dftp_fwd = nullptr;
+  const DftpTable* dftp_inv = nullptr;
   // launch shapes chosen by s2w_plan_autotune (defaults otherwise)
   int dft_threads_fwd = 256, dft_threads_inv = 256;   // threads per block of the DFT kernels
-  // S2W_FP64_TC: run the compensated-float32 DFTs instead of the tensor-core ones (the autotuner
-  // sets these where they are faster, typically at small band-limits)
-  bool dft_comp_fwd = false, dft_comp_inv = false;
+  // S2W_FP64_TC: the form of the azimuthal DFTs, forward and inverse: kDftAuto (the prime-factor
+  // tensor-core kernel where its tables exist, else the direct tensor-core GEMM where its tables
+  // exist, else compensated float32), or one form forced by the autotuner
+  int dft_form_fwd = 0, dft_form_inv = 0;
   int inv_mb = 16;                                     // maps per block of the inverse contraction
 };
+
+// DFT forms of S2W_FP64_TC (TransformSpec::dft_form_*; reported by s2w_plan_dft_forms)
+enum DftForm { kDftAuto = 0, kDftComp = 1, kDftGemm = 2, kDftPfa = 3 };
 
 struct s2w_plan_impl;
 
@@ -172,6 +194,7 @@ struct s2w_plan {
   uint16_t* tcx_ops = nullptr;         // data slices of the current contraction
   int* tcx_fexp = nullptr;             // their column exponents
   std::vector<s2w::DftxTable*> dftx_tables;  // owned
+  std::vector<s2w::DftpTable*> dftp_tables;  // owned
   uint16_t* dftx_ops = nullptr;        // data slices of the current tensor-core DFT
   int* dftx_fexp = nullptr;            // their column exponents
   int cur_batch = 0;                   // > 0: maps per launch for an internal caller (ball transforms)
@@ -294,6 +317,19 @@ cudaError_t launch_dftx_forward(const s2w_plan* P, const GridTables& g, const Tr
                                 int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st);
 cudaError_t launch_dftx_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
                                 void* pix, int64_t pix_sb, bool real, cudaStream_t st);
+
+// Prime-factor tensor-core azimuthal DFTs of S2W_FP64_TC (kernels_dftp.cu), same contracts as
+// launch_dft_forward / launch_dft_inverse; no workspace.  dftp_shape: the factorisation n1 x n2 of
+// 2L - 1 the kernel uses for this transform, false where none fits.
+struct DftpTable;
+bool dftp_shape(const TransformSpec& t, bool real, int* n1, int* n2);
+void build_dftp_table(int L, int n1, int n2, double scale, DftpTable* tab, std::vector<uint16_t>& h);
+cudaError_t launch_dftp_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
+                                int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st);
+cudaError_t launch_dftp_inverse(const s2w_plan* P, const GridTables& g, const TransformSpec& t, ColumnArgs c,
+                                void* pix, int64_t pix_sb, bool real, cudaStream_t st);
+// The form a transform's DFTs run in (kDftComp, kDftGemm or kDftPfa) in S2W_FP64_TC.
+int dft_form_used(const s2w_plan* P, const TransformSpec& t, bool fwd);
 
 // The azimuthal DFTs of a transform in the plan's precision mode (api.cpp): plain float64,
 // tensor-core (S2W_FP64_TC where the shape fits), or compensated / plain float32.

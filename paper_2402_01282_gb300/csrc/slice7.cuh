@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <cstring>
+
 #include "comp32.cuh"
 
 namespace s2w {
@@ -98,6 +101,40 @@ __device__ __forceinline__ double f2d(float f) {
   const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
                                ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)b);
+}
+
+// round(x 2^(47 - f)) for a float x with |x| < 2^f, by integer operations on its fields
+__device__ __forceinline__ long long fixf(float x, int f) {
+  const unsigned int u = __float_as_uint(x);
+  const int E = (int)((u >> 23) & 0xFFu);
+  if (E == 0) return 0;
+  const long long M = (long long)((u & 0x7FFFFFu) | 0x800000u);   // |x| = M 2^(E - 150)
+  const int sh = 103 + f - E;                                       // X = M 2^-sh
+  long long X;
+  if (sh <= 0) X = M << (-sh);
+  else if (sh >= 25) X = 0;
+  else X = (M + (1ll << (sh - 1))) >> sh;
+  return (u >> 31) ? -X : X;
+}
+// the same for a float pair hi + lo (|hi + lo| < 2^f): the two parts rounded separately
+__device__ __forceinline__ long long fixf_pair(float hi, float lo, int f) { return fixf(hi, f) + fixf(lo, f); }
+// exponent bound of a float pair hi + lo (renormalised): |hi + lo| < 2^e; 0 for zero
+__device__ __forceinline__ int fbound(float hi) {
+  const int E = (int)((__float_as_uint(hi) >> 23) & 0xFFu);
+  return E > 0 ? E - 126 + kEOff : 0;
+}
+
+// host: the seven bf16 slices of round(v 2^(47 - e)) in the device digit convention above
+inline void host_digits(double v, int e, uint16_t (&d)[kSl]) {
+  const long long X = std::llround(std::ldexp(v, 47 - e));
+  const unsigned long long Y = (unsigned long long)(X + kDigitBias);
+  for (int i = 0; i < kSl; ++i) {
+    const int u = (int)((Y >> (7 * (kSl - 1 - i))) & 127u) - 64;
+    const float f = (float)u;
+    uint32_t bits;
+    std::memcpy(&bits, &f, sizeof(bits));
+    d[i] = (uint16_t)(bits >> 16);
+  }
 }
 
 // a += x exactly as a pair (TwoSum into the high part, the error into the low part)

@@ -51,13 +51,14 @@ def test_autotune_keeps_results(lib, precision):
     L, N, lam, J0, B = 24, 4, 2.0, 0, 3
     plan = lib.Plan(L, N, lam, J0, reality=True, batch=B, precision=precision)
     forms = [plan.dft_forms(k) for k in range(plan.nscales + 2)]
-    # before autotuning: the tensor-core DFTs wherever S2W_FP64_TC has their tables, else SIMT
-    assert all(f == ((1, 1) if precision == 4 else (0, 0)) for f in forms), forms
+    # before autotuning: the prime-factor tensor-core DFTs wherever S2W_FP64_TC has their tables
+    # (every transform at L = 24: 2L_j - 1 <= 47 fits), else SIMT
+    assert all(f == ((2, 2) if precision == 4 else (0, 0)) for f in forms), forms
     plan.autotune()
     for k in range(plan.nscales + 2):
         th_f, th_i, mb = plan.launch_shapes(k)
         assert th_f in (128, 256, 384, 512) and th_i in (128, 256, 384, 512) and mb in (4, 8, 16)
-        assert all(v in (0, 1) for v in plan.dft_forms(k))
+        assert all(v in ((0, 1, 2) if precision == 4 else (0,)) for v in plan.dft_forms(k))
     f = maps_for(L, 0, True, B, 930)
     wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
     plan.forward(to_dev(f), wav, scal)

@@ -62,6 +62,7 @@ def test_invalid_params_rejected_without_gpu(built_lib):
     assert built_lib.s2w_plan_device_bytes(None, ctypes.byref(t), ctypes.byref(w)) == 1
     assert (t.value, w.value) == (7, 7)
     assert built_lib.s2w_plan_inject_timeout(None, 1) == 1
+    assert built_lib.s2w_plan_set_dft_forms(None, 0, -1, -1) == 1
     assert built_lib.s2w_check(None) == 1
     # Driscoll-Healy above its supported band-limit: unsupported, still before any CUDA call
     p = s2w.Params(600, 2, 0, 0, 0, 1, 0, 0, 2.0, s2w.S2W_SAMPLING_DH)
