@@ -655,7 +655,12 @@ def main():
     ap.add_argument("--no-batching", action="store_true", help="skip the batching-study timing")
     ap.add_argument("--no-sampling", action="store_true", help="skip the Driscoll-Healy timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--maps", type=int, default=B,
+                    help="maps per GPU (default 16, the headline workload; smaller batches are for "
+                         "profiler captures of single kernels, not bench lines)")
     args = ap.parse_args()
+    if args.maps != B:
+        globals()["B"] = args.maps
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)

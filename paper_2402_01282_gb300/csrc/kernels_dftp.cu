@@ -285,11 +285,12 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp(PArgs a) {
             const int k = (k1 * a.e1 + k2 * a.e2) % n;
             const double2 x = make_double2(pair_dbl(xr[k1], ke), pair_dbl(xi[k1], ke));
             if (REAL) {
-              if (k <= h) {
-                a.Gout[(((int64_t)bb * a.nact + jn[q]) * a.nr + t) * a.Mc + k] = x;   // G_{m=k, n}
-              } else if (jp[q] >= 0) {                                                // G_{n-k, -n}
-                a.Gout[(((int64_t)bb * a.nact + jp[q]) * a.nr + t) * a.Mc + (n - k)] = make_double2(x.x, -x.y);
-              }
+              // G_{m, n} = X(m) for m = k <= h; the partner column G_{m', -n} = conj X(n - m') for
+              // m' = n - k in 1..h, and G_{0, -n} = conj X(0)
+              if (k <= h) a.Gout[(((int64_t)bb * a.nact + jn[q]) * a.nr + t) * a.Mc + k] = x;
+              if (jp[q] >= 0 && (k > h || k == 0))
+                a.Gout[(((int64_t)bb * a.nact + jp[q]) * a.nr + t) * a.Mc + (k == 0 ? 0 : n - k)] =
+                    make_double2(x.x, -x.y);
             } else {
               a.Gout[(((int64_t)bb * a.nact + jn[q]) * a.nr + t) * a.Mc + ((k <= h ? k : k - n) - a.mlo)] = x;
             }
