@@ -20,7 +20,9 @@ TOL = 1e-11
 
 
 def rel(a, b):
-    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
+    d = np.abs(np.asarray(a) - np.asarray(b)).max()
+    s = np.abs(np.asarray(b)).max()
+    return d / s if s > 0 else d   # a scale whose filter vanishes on l < L is all zero
 
 
 def to_dev(x):
