@@ -52,8 +52,13 @@ def test_autotune_keeps_results(lib, precision):
     plan = lib.Plan(L, N, lam, J0, reality=True, batch=B, precision=precision)
     forms = [plan.dft_forms(k) for k in range(plan.nscales + 2)]
     # before autotuning: the prime-factor tensor-core DFTs wherever S2W_FP64_TC has their tables
-    # (every transform at L = 24: 2L_j - 1 <= 47 fits), else SIMT
-    assert all(f == ((2, 2) if precision == 4 else (0, 0)) for f in forms), forms
+    # (the SHT and every wavelet scale at L = 24: 2L_j - 1 <= 47 fits; the scaling function at
+    # L_Phi = 1 has no factorisation and takes the direct tensor-core form), else SIMT
+    if precision == 4:
+        assert forms[0] == (2, 2) and all(f == (2, 2) for f in forms[2:]), forms
+        assert forms[1] in ((1, 1), (2, 2)), forms
+    else:
+        assert all(f == (0, 0) for f in forms), forms
     plan.autotune()
     for k in range(plan.nscales + 2):
         th_f, th_i, mb = plan.launch_shapes(k)
