@@ -127,5 +127,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive float32 columns of TMEM into registers, WITHOUT waiting: the values
+// are valid only after tmem_wait_ld() (lets several loads be in flight before one wait).
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Orders later uses of r after a preceding tmem_wait_ld(): an empty volatile asm that reads and
+// writes r (volatile asm statements keep their order, and the uses depend on its outputs).
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[8]) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+}
+
+// Bounded wait with exponential nanosleep back-off between polls (for roles whose waits are long
+// and whose polling would take issue slots from the warps doing the work).
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* mbar, uint32_t parity, uint32_t max_iter) {
+  uint32_t ns = 32;
+  for (uint32_t it = 0; it < max_iter; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+  }
+  return false;
+}
+
 }  // namespace tc
 }  // namespace s2w
