@@ -546,11 +546,17 @@ s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
     *out = tab;
     return S2W_OK;
   };
+  int64_t pops = 0, pfx = 0, pz = 0;
   for (TransformSpec* t : specs) {
     int n1 = 0, n2 = 0;
     if (dftp_shape(*t, P->real, &n1, &n2)) {
       S2W_TRY(ptable(t->L, n1, n2, 1.0, &t->dftp_inv));
       S2W_TRY(ptable(t->L, n1, n2, (2.0 * kPi / (2.0 * t->L - 1.0)) * t->gscale, &t->dftp_fwd));
+      int64_t o = 0, f = 0, z = 0;
+      dftp_ws_elems(*t, P->real, n1, P->p.batch, rings_of(P->p.sampling, t->L), &o, &f, &z);
+      pops = std::max(pops, o);
+      pfx = std::max(pfx, f);
+      pz = std::max(pz, z);
     }
     if (!dftx_shape_ok(*t, P->real)) continue;
     const int nr = rings_of(P->p.sampling, t->L);
@@ -561,6 +567,11 @@ s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
   }
   S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(ops, 1), &P->dftx_ops, err));
   S2W_TRY(alloc_ws(P, (size_t)std::max<int64_t>(fx, 1), &P->dftx_fexp, err));
+  if (pops > 0) {
+    S2W_TRY(alloc_ws(P, (size_t)pops, &P->dftp_ops, err));
+    S2W_TRY(alloc_ws(P, (size_t)pfx, &P->dftp_fexp, err));
+    S2W_TRY(alloc_ws(P, (size_t)pz, &P->dftp_z, err));
+  }
   return S2W_OK;
 }
 

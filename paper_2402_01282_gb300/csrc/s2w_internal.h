@@ -197,6 +197,9 @@ struct s2w_plan {
   std::vector<s2w::DftpTable*> dftp_tables;  // owned
   uint16_t* dftx_ops = nullptr;        // data slices of the current tensor-core DFT
   int* dftx_fexp = nullptr;            // their column exponents
+  uint16_t* dftp_ops = nullptr;        // prime-factor DFTs: data slices in pass order
+  int* dftp_fexp = nullptr;            // their ring exponents
+  float4* dftp_z = nullptr;            // inverse: Z staging between the GEMM and the gamma synthesis
   int cur_batch = 0;                   // > 0: maps per launch for an internal caller (ball transforms)
   bool precompute = false;             // float64-accurate table contractions (S2W_FP64, precompute = 1)
   std::vector<s2w::TabTable*> tab_tables;  // owned
@@ -323,6 +326,7 @@ cudaError_t launch_dftx_inverse(const s2w_plan* P, const GridTables& g, const Tr
 // 2L - 1 the kernel uses for this transform, false where none fits.
 struct DftpTable;
 bool dftp_shape(const TransformSpec& t, bool real, int* n1, int* n2);
+void dftp_ws_elems(const TransformSpec& t, bool real, int n1, int B, int nr, int64_t* ops, int64_t* fexp, int64_t* z);
 void build_dftp_table(int L, int n1, int n2, double scale, DftpTable* tab, std::vector<uint16_t>& h);
 cudaError_t launch_dftp_forward(const s2w_plan* P, const GridTables& g, const TransformSpec& t, const void* pix,
                                 int64_t pix_sb, bool real, ColumnArgs c, cudaStream_t st);
