@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "comp32.cuh"
@@ -55,7 +56,7 @@ constexpr int kPN = 64;                 // GEMM columns per pass (MMA N)
 constexpr int kPBTile = kPN * 16;       // elements of one data slice chunk (64 x 16)
 constexpr int kPChunk = kSl * kPBTile;  // elements of one K chunk of a pass (7 slices)
 constexpr int kPStages = 4;             // bulk-copy stages of the persistent kernel
-constexpr int kPTmemWarps = 8;          // warps 0-7 of the persistent kernel
+constexpr int kPTmemWarps = 16;         // warps 0-15 of the persistent kernel (lane quarter w % 4, chunk w / 4)
 constexpr int kPT = (kPTmemWarps + 1) * 32;   // + the issuing warp
 constexpr uint32_t kPWait = 1u << 20;   // bounded mbarrier polls
 constexpr int kPMaxRpp = 32;            // rings per pass (n1 = 1: 32 slots of 2 columns)
@@ -178,17 +179,39 @@ __global__ void k_dftp_fwd_prep(PArgs a) {
   const int64_t base = (int64_t)b * a.pix_sb + (int64_t)t * n;
   int e = 0;
   bool bad = false;
+  constexpr int HG = (kPMaxNg - 1) / 2;
+  using Raw = typename std::conditional<REAL, double, double2>::type;
+  const Raw* pin = static_cast<const Raw*>(a.pix_in);
+  auto to_pair = [](Raw v) -> float4 {
+    if constexpr (REAL) {
+      const float2 r = split1_bits(v);
+      return make_float4(r.x, r.y, 0.f, 0.f);
+    } else {
+      const float2 r = split1_bits(v.x), i = split1_bits(v.y);
+      return make_float4(r.x, r.y, i.x, i.y);
+    }
+  };
   for (int al = threadIdx.x; al < n; al += blockDim.x) {
-    const float4 w0 = load_pix(a.pix_in, REAL, base + al);
+    // every sample of this alpha in flight before the arithmetic
+    Raw rp[HG], rm[HG];
+    const Raw r0 = pin[base + al];
+#pragma unroll
+    for (int g = 1; g <= HG; ++g)
+      if (g <= hg) {
+        rp[g - 1] = pin[base + g * ring + al];
+        rm[g - 1] = pin[base + (Ng - g) * ring + al];
+      }
+    const float4 w0 = to_pair(r0);
     Acc hr[kJobChunk], hi[kJobChunk];
 #pragma unroll
     for (int q = 0; q < kJobChunk; ++q) {
       hr[q] = Acc{w0.x, w0.y};
       hi[q] = Acc{w0.z, w0.w};
     }
-    for (int g = 1; g <= hg; ++g) {
-      const float4 xp = load_pix(a.pix_in, REAL, base + g * ring + al);
-      const float4 xm = load_pix(a.pix_in, REAL, base + (Ng - g) * ring + al);
+#pragma unroll
+    for (int g = 1; g <= HG; ++g) {
+      if (g > hg) break;
+      const float4 xp = to_pair(rp[g - 1]), xm = to_pair(rm[g - 1]);
       const float4 u = cadd<false>(xp, xm, 1.f), v = cadd<false>(xp, xm, -1.f);
 #pragma unroll
       for (int q = 0; q < kJobChunk; ++q) {
@@ -258,12 +281,27 @@ __global__ void k_dftp_inv_prep(PArgs a) {
   const int nj = njs;
   int e = 0;
   bool bad = false;
-  for (int i = threadIdx.x; i < a.nact * Mc; i += blockDim.x) {
-    const int ni = i / Mc, mi = i - ni * Mc;
-    const double2 v = a.Gin[(((int64_t)b * a.nact + ni) * a.nr + t) * Mc + mi];
-    Gs[i] = v;
-    e = max(e, max(ebound(v.x), ebound(v.y)));
-    bad |= (bexp(v.x) == 0x7FF) | (bexp(v.y) == 0x7FF);
+  // the ring's columns: nact contiguous runs of Mc values; four loads in flight per thread
+  const int total = a.nact * Mc;
+  for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < total) {
+        const int ni = i / Mc, mi = i - ni * Mc;
+        v[u] = a.Gin[(((int64_t)b * a.nact + ni) * a.nr + t) * Mc + mi];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < total) {
+        Gs[i] = v[u];
+        e = max(e, max(ebound(v[u].x), ebound(v[u].y)));
+        bad |= (bexp(v[u].x) == 0x7FF) | (bexp(v[u].y) == 0x7FF);
+      }
+    }
   }
   if (bad) atomicCAS(a.err, 0, (int)S2W_ENONFINITE);
   if (e > 0) atomicMax(&emax, e);
@@ -301,10 +339,10 @@ __global__ void k_dftp_inv_prep(PArgs a) {
 }
 
 // ------------------------------------------------------------------ persistent tensor-core kernel
-// One CTA per SM over the passes; warp 8 (one thread) streams each pass's slices through
-// kPStages bulk-copy stages and issues the MMAs; warps 0-7 drain the accumulators (warp w: TMEM
-// lane quarter w % 4, column chunks 2 (w/4) and 2 (w/4) + 1), take the n1-point DFT and stage the
-// outputs in shared memory, then write them out coalesced (forward: the columns G; inverse: Z).
+// One CTA per SM over the passes; warp 16 (one thread) streams each pass's slices through
+// kPStages bulk-copy stages and issues the MMAs; warps 0-15 drain the accumulators (warp w: TMEM
+// lane quarter w % 4, 16-column chunk w / 4), take the n1-point DFT and stage the outputs in
+// shared memory, then write them out coalesced (forward: the columns G; inverse: Z).
 template <bool FWD, bool REAL, int N1>
 __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
   using SS = SlotShape<N1>;
@@ -418,7 +456,7 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
     }
   } else {
     // ------------------------------------------------------------ TMEM warps
-    const int quarter = warp & 3, grp = warp >> 2;
+    const int quarter = warp & 3, chunk = warp >> 2;
     const int row = 32 * quarter + lane, j = row >> 1, sd = row & 1;
     const bool warp_live = 32 * quarter < a.R;
     const bool live = row < a.R && !(j == 0 && sd == 1);   // rows that produce an output
@@ -504,7 +542,7 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
         }
       }
     };
-    const int tt = tid;   // 0 .. 255 over the TMEM warps
+    const int tt = tid;   // 0 .. 511 over the TMEM warps
     for (int i = 0; i < my; ++i) {
       const int gp = (int)blockIdx.x + i * G;
       // the TMEM warps meet at named barriers below: one abort decision for all of them, taken
@@ -514,19 +552,13 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
       asm volatile("bar.sync 1, %0;" ::"n"(kPTmemWarps * 32) : "memory");
       if (t_abort) break;
       tc::fence_after_sync();
-      Acc acc0[16], acc1[16];
-      if (warp_live) {
-        drain(2 * grp, acc0);
-        drain(2 * grp + 1, acc1);
-      }
+      Acc acc[16];
+      if (warp_live) drain(chunk, acc);
       // every accumulator value this warp needs is in registers: release TMEM to the next pass
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_empty);
-      if (warp_live) {
-        stage_b(gp, 2 * grp, acc0);
-        stage_b(gp, 2 * grp + 1, acc1);
-      }
+      if (warp_live) stage_b(gp, chunk, acc);
       asm volatile("bar.sync 1, %0;" ::"n"(kPTmemWarps * 32) : "memory");
       // coalesced write-out of the pass's staged outputs
       for (int sl = 0; sl < rpp * nj; ++sl) {
