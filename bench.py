@@ -535,6 +535,11 @@ def run_ours(args, world, rank, local):
     ball = None
     if not args.no_ball:
         ball = run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)
+        # the ball study's split-precision arm: reduced sphere contractions, radial maps on the
+        # tensor cores
+        ball["fp32_split"] = {k: v for k, v in run_ball(torch, s2w, stream, flush, max(3, args.steps // 2),
+                                                        "fp32_split").items() if k in ("value", "ms_per_step",
+                                                                                       "max_rel_err")}
 
     if rank != 0:
         if dist:

@@ -200,15 +200,17 @@ s2w_status s2w_wigner_inverse(const s2w_plan* plan, int scale, const void* flmn,
 typedef struct {
   int L;          /* angular band-limit (2 <= L <= 1024) */
   int P;          /* radial band-limit (2 <= P <= 256) */
-  int spin, reality, batch, precision;   /* as in s2w_params (precision S2W_FP64 or S2W_FP64_NATIVE) */
+  int spin, reality, batch, precision;   /* as in s2w_params; in the tensor-core modes (S2W_FP32_SPLIT,
+                                            S2W_BF16, S2W_FP64_TC) the radial maps run on the tensor
+                                            cores as exact sliced GEMMs (float64-accurate) */
   double tau;     /* Laguerre scale tau > 0 */
   int sampling;   /* angular sampling, s2w_sampling */
 } s2w_ball_params;
 
 typedef struct s2w_ball_plan s2w_ball_plan;
 
-/* Builds the radial quadrature and matrices in float64 on the host and an SHT plan for
- * batch*P maps; blocks until uploads complete. */
+/* Builds the radial quadrature and matrices in float64 on the host (sliced for the tensor cores in
+ * the tensor-core modes) and an SHT plan for batch*P maps; blocks until uploads complete. */
 s2w_status s2w_ball_plan_create(const s2w_ball_params* params, void* stream, s2w_ball_plan** out);
 s2w_status s2w_ball_plan_destroy(s2w_ball_plan* plan);
 /* Copies the nodes r_i and weights omega_i (P doubles each, HOST pointers, may be NULL). */
@@ -237,7 +239,11 @@ s2w_status s2w_ball_sl_inverse(const s2w_ball_plan* plan, const void* flmp, void
  * block k = [batch][P_j' node][2N_j-1 gamma][R(L_j) beta][2L_j-1 alpha], starting at element
  * wav_offsets[k] (offsets over the WHOLE batch, unlike s2w_query_layout).
  * The plan holds a sphere wavelet plan over batch*P node maps and two workspaces of
- * batch*P*L*Mc complex.  Same stream, allocation and error conventions as s2w_forward. */
+ * batch*P*L*Mc complex.  Every precision mode is accepted: the sphere transforms run in it, and in
+ * the tensor-core modes (S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_TC) every radial map (the
+ * Fourier-Laguerre transform, its inverse, the per-scale filters and their transposes) runs on the
+ * tensor cores as an exact sliced GEMM, float64-accurate.  Same stream, allocation and error
+ * conventions as s2w_forward. */
 typedef struct {
   int L, N, P, J0, J0r, spin, reality, batch, precision, precompute;   /* precision/precompute as s2w_params */
   double lambda, nu, tau;

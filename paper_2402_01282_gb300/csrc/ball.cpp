@@ -31,6 +31,12 @@ struct s2w_ball_plan {
   double* Ri = nullptr;            // [P][P] K_p(r_i), row i
   float2* Rf2 = nullptr;
   float2* Ri2 = nullptr;
+  // tensor-core precision modes (S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_TC): both maps sliced for the
+  // tensor cores (kernels_radx.cu) and their data-slice workspaces
+  bool tc = false;
+  s2w::RadxMap RfX, RiX;
+  uint16_t* rops = nullptr;
+  int* rfexp = nullptr;
   double2* ws = nullptr;           // [batch][P][L][Mc]
   std::vector<void*> owned;
 };
@@ -192,12 +198,12 @@ s2w_status s2w_ball_plan_create(const s2w_ball_params* prm, void* stream, s2w_ba
   if (p.P < 2 || p.P > 256) return record_error(S2W_EINVAL, "P must satisfy 2 <= P <= 256");
   if (!(p.tau > 0.0) || !std::isfinite(p.tau)) return record_error(S2W_EINVAL, "tau must be > 0");
   if (p.batch < 1) return record_error(S2W_EINVAL, "batch must be >= 1");
-  if (p.precision != S2W_FP64 && p.precision != S2W_FP64_NATIVE)
-    return record_error(S2W_EUNSUPPORTED, "precision mode not implemented for the ball in this build");
+  if (p.precision < S2W_FP64 || p.precision > S2W_FP64_TC) return record_error(S2W_EINVAL, "unknown precision mode");
   s2w_ball_plan* B = new (std::nothrow) s2w_ball_plan();
   if (B == nullptr) return record_error(S2W_ENOMEM, "host allocation failed");
   B->p = p;
-  B->c32 = p.precision == S2W_FP64;
+  B->c32 = p.precision != S2W_FP64_NATIVE;
+  B->tc = p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16 || p.precision == S2W_FP64_TC;
   s2w_params sp{};
   sp.L = p.L;
   sp.N = 1;
@@ -238,6 +244,19 @@ s2w_status s2w_ball_plan_create(const s2w_ball_params* prm, void* stream, s2w_ba
     destroy(B);
     return s;
   }
+  if (B->tc) {
+    // Rf as stored is [p][i] (row p); Ri is [i][p]: the inverse map f_r[i] = sum_p K_p(r_i) f_p[p]
+    // has rows i, so its matrix is Ri itself
+    std::vector<uint16_t> tab;
+    std::vector<int> rexp;
+    build_radx(Rf, P, P, &B->RfX, tab, rexp);
+    if ((s = up(B, tab, &B->RfX.tab, st)) || (s = up(B, rexp, &B->RfX.rexp, st))) return destroy(B), s;
+    build_radx(Ri, P, P, &B->RiX, tab, rexp);
+    if ((s = up(B, tab, &B->RiX.tab, st)) || (s = up(B, rexp, &B->RiX.rexp, st))) return destroy(B), s;
+    std::vector<uint16_t> ops((size_t)radx_ops_elems(p.batch, P, ncol(B)), 0);
+    std::vector<int> fx((size_t)p.batch * ncol(B) * 2, 0);
+    if ((s = up(B, ops, &B->rops, st)) || (s = up(B, fx, &B->rfexp, st))) return destroy(B), s;
+  }
   void* w = nullptr;
   if (cudaMalloc(&w, (size_t)p.batch * P * ncol(B) * sizeof(double2)) != cudaSuccess) {
     cudaGetLastError();
@@ -273,8 +292,11 @@ s2w_status s2w_laguerre_forward(const s2w_ball_plan* B, const void* f_r, void* f
   if (B == nullptr) return record_error(S2W_EINVAL, "plan is NULL");
   s2w_status s;
   if ((s = check_ptr(f_r, "f_r")) || (s = check_ptr(f_p, "f_p"))) return s;
-  cudaError_t e = launch_radial(B->Rf, B->Rf2, (const double2*)f_r, (double2*)f_p, B->p.batch, B->p.P, ncol(B),
-                                B->c32, (cudaStream_t)stream);
+  cudaError_t e =
+      B->tc ? launch_radx(B->RfX, (const double2*)f_r, (double2*)f_p, B->p.batch, B->p.L, B->Mc, nullptr, nullptr,
+                          false, B->rops, B->rfexp, B->sphere->err_word, (cudaStream_t)stream)
+            : launch_radial(B->Rf, B->Rf2, (const double2*)f_r, (double2*)f_p, B->p.batch, B->p.P, ncol(B), B->c32,
+                            (cudaStream_t)stream);
   if (e != cudaSuccess) return record_error(S2W_ECUDA, std::string("radial transform: ") + cudaGetErrorString(e));
   return S2W_OK;
 }
@@ -283,8 +305,11 @@ s2w_status s2w_laguerre_inverse(const s2w_ball_plan* B, const void* f_p, void* f
   if (B == nullptr) return record_error(S2W_EINVAL, "plan is NULL");
   s2w_status s;
   if ((s = check_ptr(f_p, "f_p")) || (s = check_ptr(f_r, "f_r"))) return s;
-  cudaError_t e = launch_radial(B->Ri, B->Ri2, (const double2*)f_p, (double2*)f_r, B->p.batch, B->p.P, ncol(B),
-                                B->c32, (cudaStream_t)stream);
+  cudaError_t e =
+      B->tc ? launch_radx(B->RiX, (const double2*)f_p, (double2*)f_r, B->p.batch, B->p.L, B->Mc, nullptr, nullptr,
+                          false, B->rops, B->rfexp, B->sphere->err_word, (cudaStream_t)stream)
+            : launch_radial(B->Ri, B->Ri2, (const double2*)f_p, (double2*)f_r, B->p.batch, B->p.P, ncol(B), B->c32,
+                            (cudaStream_t)stream);
   if (e != cudaSuccess) return record_error(S2W_ECUDA, std::string("radial transform: ") + cudaGetErrorString(e));
   return S2W_OK;
 }

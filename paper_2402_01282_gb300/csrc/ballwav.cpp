@@ -38,6 +38,13 @@ struct s2w_ball_wav_plan {
   int64_t field_elems = 0, wav_elems = 0;
   float2 *Rf = nullptr, *Ri = nullptr, *RfT = nullptr, *RiT = nullptr;   // full rule, P x P
   std::vector<float2*> Ra, Rs, RaT, RsT;   // per radial scale: [Pj][P], [P][Pj] and transposes
+  // tensor-core precision modes (S2W_FP32_SPLIT, S2W_BF16, S2W_FP64_TC): the same maps sliced for
+  // the tensor cores (kernels_radx.cu), index-aligned with the pairs above, and their workspaces
+  bool tc = false;
+  s2w::RadxMap RfX, RiX, RfTX, RiTX;
+  std::vector<s2w::RadxMap> RaX, RsX, RaTX, RsTX;
+  uint16_t* rops = nullptr;
+  int* rfexp = nullptr;
   double* phi = nullptr;              // [P][L]
   double2* fhat = nullptr;            // [batch][P][L][Mc]
   double2* ws = nullptr;              // [batch * P][L][Mc]
@@ -118,9 +125,14 @@ struct Ctx {
     BW_CUDA(cudaMemsetAsync(q, 0, (size_t)rows * ncol() * sizeof(double2), st), "zero workspace");
     return S2W_OK;
   }
-  s2w_status radial(const float2* R, const double2* in, double2* out, int Pout, int Pin, const double* wi,
-                    const double* wo, bool acc) const {
-    BW_CUDA(launch_radial_gen(R, in, out, B, Pout, Pin, L, Mc, wi, wo, acc, st), "radial map");
+  // one radial map: on the tensor cores (RX, float64-accurate) in the tensor-core precision modes,
+  // else the compensated SIMT kernel on the float pairs R
+  s2w_status radial(const float2* R, const s2w::RadxMap& RX, const double2* in, double2* out, int Pout, int Pin,
+                    const double* wi, const double* wo, bool acc) const {
+    if (W->tc)
+      BW_CUDA(launch_radx(RX, in, out, B, L, Mc, wi, wo, acc, W->rops, W->rfexp, W->sph->err_word, st), "radial map");
+    else
+      BW_CUDA(launch_radial_gen(R, in, out, B, Pout, Pin, L, Mc, wi, wo, acc, st), "radial map");
     return S2W_OK;
   }
   int64_t scale_pix(int k) const {   // elements of one node map of wavelet scale k
@@ -205,16 +217,38 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
       phi[(size_t)q * L + l] = std::sqrt(std::max(0.0, A + Bq - A * Bq));
     }
   }
+  W->tc = p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16 || p.precision == S2W_FP64_TC;
+  // a rows x cols map and its transpose, sliced for the tensor cores (tensor-core modes only)
+  auto sliced = [&](const std::vector<double>& M, int rows, int cols, RadxMap* X, RadxMap* XT) -> s2w_status {
+    if (!W->tc) return S2W_OK;
+    std::vector<double> MT((size_t)rows * cols);
+    for (int i = 0; i < rows; ++i)
+      for (int k = 0; k < cols; ++k) MT[(size_t)k * rows + i] = M[(size_t)i * cols + k];
+    std::vector<uint16_t> tab;
+    std::vector<int> rexp;
+    s2w_status s2;
+    build_radx(M, rows, cols, X, tab, rexp);
+    if ((s2 = upload_vec(W, tab, &X->tab, st)) || (s2 = upload_vec(W, rexp, &X->rexp, st))) return s2;
+    build_radx(MT, cols, rows, XT, tab, rexp);
+    if ((s2 = upload_vec(W, tab, &XT->tab, st)) || (s2 = upload_vec(W, rexp, &XT->rexp, st))) return s2;
+    return S2W_OK;
+  };
   std::vector<float2> a2, a2T;
   if ((s = upload_vec(W, phi, &W->phi, st))) return destroy(W), s;
   pairs(Rf, P, P, a2, a2T);
   if ((s = upload_vec(W, a2, &W->Rf, st)) || (s = upload_vec(W, a2T, &W->RfT, st))) return destroy(W), s;
+  if ((s = sliced(Rf, P, P, &W->RfX, &W->RfTX))) return destroy(W), s;
   pairs(Ri, P, P, a2, a2T);
   if ((s = upload_vec(W, a2, &W->Ri, st)) || (s = upload_vec(W, a2T, &W->RiT, st))) return destroy(W), s;
+  if ((s = sliced(Ri, P, P, &W->RiX, &W->RiTX))) return destroy(W), s;
   W->Ra.resize(W->jr.size());
   W->RaT.resize(W->jr.size());
   W->Rs.resize(W->jr.size());
   W->RsT.resize(W->jr.size());
+  W->RaX.resize(W->jr.size());
+  W->RaTX.resize(W->jr.size());
+  W->RsX.resize(W->jr.size());
+  W->RsTX.resize(W->jr.size());
   for (size_t ri = 0; ri < W->jr.size(); ++ri) {
     const int Pr = W->Pj[ri];
     std::vector<double> rr, oo, KK;
@@ -230,8 +264,16 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
     }
     pairs(Ra, Pr, P, a2, a2T);
     if ((s = upload_vec(W, a2, &W->Ra[ri], st)) || (s = upload_vec(W, a2T, &W->RaT[ri], st))) return destroy(W), s;
+    if ((s = sliced(Ra, Pr, P, &W->RaX[ri], &W->RaTX[ri]))) return destroy(W), s;
     pairs(Rs, P, Pr, a2, a2T);
     if ((s = upload_vec(W, a2, &W->Rs[ri], st)) || (s = upload_vec(W, a2T, &W->RsT[ri], st))) return destroy(W), s;
+    if ((s = sliced(Rs, P, Pr, &W->RsX[ri], &W->RsTX[ri]))) return destroy(W), s;
+  }
+  if (W->tc) {   // data-slice workspace of the largest map (K = P input nodes), column exponents
+    const int64_t ncol = (int64_t)L * W->Mc;
+    std::vector<uint16_t> ops((size_t)radx_ops_elems(p.batch, P, ncol), 0);
+    std::vector<int> fx((size_t)p.batch * ncol * 2, 0);
+    if ((s = upload_vec(W, ops, &W->rops, st)) || (s = upload_vec(W, fx, &W->rfexp, st))) return destroy(W), s;
   }
   void* q = nullptr;
   const size_t cb = (size_t)p.batch * P * L * W->Mc * sizeof(double2);
@@ -286,14 +328,14 @@ s2w_status s2w_ball_forward(const s2w_ball_wav_plan* cW, const void* f, void* wa
   // f_p = K Y f
   BW_TRY(c.zero(W->ws, nb));
   BW_TRY(run_fwd_transform(S, S->sht, f, S->map_elems, c.coef(W->ws), nb, c.st));
-  BW_TRY(c.radial(W->Rf, W->ws, W->fhat, c.P, c.P, nullptr, nullptr, false));
+  BW_TRY(c.radial(W->Rf, W->RfX, W->ws, W->fhat, c.P, c.P, nullptr, nullptr, false));
   // W^Phi = Y^-1 K^-1 (phi f_p)
-  BW_TRY(c.radial(W->Ri, W->fhat, W->ws, c.P, c.P, W->phi, nullptr, false));
+  BW_TRY(c.radial(W->Ri, W->RiX, W->fhat, W->ws, c.P, c.P, W->phi, nullptr, false));
   BW_TRY(run_inv_transform(S, S->sht, c.coef(W->ws), scal, S->map_elems, nb, c.st));
   // W^{jj'} = D^-1_j (conj Psi^j  g^{j'}),  g^{j'} = K'^-1 (kappa^{j'} f_p)
   for (size_t r = 0; r < W->jr.size(); ++r) {
     const int Pr = W->Pj[r];
-    BW_TRY(c.radial(W->Ra[r], W->fhat, W->ws, Pr, c.P, nullptr, nullptr, false));
+    BW_TRY(c.radial(W->Ra[r], W->RaX[r], W->fhat, W->ws, Pr, c.P, nullptr, nullptr, false));
     for (size_t k = 0; k < W->sc_s.size(); ++k) {
       if (W->sc_r[k] != (int)r) continue;
       BW_TRY(run_inv_transform(S, S->wav_t[W->sc_s[k]], c.coef(W->ws), c.wav_at(wav, (int)k), c.scale_pix((int)k),
@@ -316,7 +358,7 @@ s2w_status s2w_ball_inverse(const s2w_ball_wav_plan* cW, const void* wav, const 
   // f_p = phi K Y W^Phi
   BW_TRY(c.zero(W->ws, nb));
   BW_TRY(run_fwd_transform(S, S->sht, scal, S->map_elems, c.coef(W->ws), nb, c.st));
-  BW_TRY(c.radial(W->Rf, W->ws, W->fhat, c.P, c.P, nullptr, W->phi, false));
+  BW_TRY(c.radial(W->Rf, W->RfX, W->ws, W->fhat, c.P, c.P, nullptr, W->phi, false));
   // f_p += kappa^{j'} K' sum_j (Psi^j D_j W^{jj'})
   for (size_t r = 0; r < W->jr.size(); ++r) {
     const int Pr = W->Pj[r];
@@ -326,10 +368,10 @@ s2w_status s2w_ball_inverse(const s2w_ball_wav_plan* cW, const void* wav, const 
       BW_TRY(run_fwd_transform(S, S->wav_t[W->sc_s[k]], c.wav_at(const_cast<void*>(wav), (int)k), c.scale_pix((int)k),
                                c.coef(W->ws), c.B * Pr, c.st));
     }
-    BW_TRY(c.radial(W->Rs[r], W->ws, W->fhat, c.P, Pr, nullptr, nullptr, true));
+    BW_TRY(c.radial(W->Rs[r], W->RsX[r], W->ws, W->fhat, c.P, Pr, nullptr, nullptr, true));
   }
   // f = Y^-1 K^-1 f_p
-  BW_TRY(c.radial(W->Ri, W->fhat, W->ws, c.P, c.P, nullptr, nullptr, false));
+  BW_TRY(c.radial(W->Ri, W->RiX, W->fhat, W->ws, c.P, c.P, nullptr, nullptr, false));
   return run_inv_transform(S, S->sht, c.coef(W->ws), f, S->map_elems, nb, c.st);
 }
 
@@ -347,7 +389,7 @@ s2w_status s2w_ball_forward_adjoint(const s2w_ball_wav_plan* cW, const void* gwa
   // scaling branch: g_p = phi K^-T (Y^-1)^H gscal
   BW_TRY(c.zero(W->ws, nb));
   BW_TRY(run_adj_inv_transform(S, S->sht, gscal, S->map_elems, c.coef(W->ws), nb, c.st));
-  BW_TRY(c.radial(W->RiT, W->ws, W->fhat, c.P, c.P, nullptr, W->phi, false));
+  BW_TRY(c.radial(W->RiT, W->RiTX, W->ws, W->fhat, c.P, c.P, nullptr, W->phi, false));
   // wavelet branch: g_p += (K'^-1 kappa)^T sum_j (D_j^-1 conj Psi^j)^H gwav^{jj'}
   for (size_t r = 0; r < W->jr.size(); ++r) {
     const int Pr = W->Pj[r];
@@ -357,10 +399,10 @@ s2w_status s2w_ball_forward_adjoint(const s2w_ball_wav_plan* cW, const void* gwa
       BW_TRY(run_adj_inv_transform(S, S->wav_t[W->sc_s[k]], c.wav_at(const_cast<void*>(gwav), (int)k),
                                    c.scale_pix((int)k), c.coef(W->ws), c.B * Pr, c.st));
     }
-    BW_TRY(c.radial(W->RaT[r], W->ws, W->fhat, c.P, Pr, nullptr, nullptr, true));
+    BW_TRY(c.radial(W->RaT[r], W->RaTX[r], W->ws, W->fhat, c.P, Pr, nullptr, nullptr, true));
   }
   // gf = Y^H K^T g_p
-  BW_TRY(c.radial(W->RfT, W->fhat, W->ws, c.P, c.P, nullptr, nullptr, false));
+  BW_TRY(c.radial(W->RfT, W->RfTX, W->fhat, W->ws, c.P, c.P, nullptr, nullptr, false));
   return run_adj_fwd_transform(S, S->sht, c.coef(W->ws), gf, S->map_elems, nb, c.st);
 }
 
@@ -378,14 +420,14 @@ s2w_status s2w_ball_inverse_adjoint(const s2w_ball_wav_plan* cW, const void* gf,
   // g_p = K^-T (Y^-1)^H gf
   BW_TRY(c.zero(W->ws, nb));
   BW_TRY(run_adj_inv_transform(S, S->sht, gf, S->map_elems, c.coef(W->ws), nb, c.st));
-  BW_TRY(c.radial(W->RiT, W->ws, W->fhat, c.P, c.P, nullptr, nullptr, false));
+  BW_TRY(c.radial(W->RiT, W->RiTX, W->ws, W->fhat, c.P, c.P, nullptr, nullptr, false));
   // gscal = Y^H K^T (phi g_p)
-  BW_TRY(c.radial(W->RfT, W->fhat, W->ws, c.P, c.P, W->phi, nullptr, false));
+  BW_TRY(c.radial(W->RfT, W->RfTX, W->fhat, W->ws, c.P, c.P, W->phi, nullptr, false));
   BW_TRY(run_adj_fwd_transform(S, S->sht, c.coef(W->ws), gscal, S->map_elems, nb, c.st));
   // gwav^{jj'} = (Psi^j D_j)^H (kappa K')^T g_p
   for (size_t r = 0; r < W->jr.size(); ++r) {
     const int Pr = W->Pj[r];
-    BW_TRY(c.radial(W->RsT[r], W->fhat, W->ws, Pr, c.P, nullptr, nullptr, false));
+    BW_TRY(c.radial(W->RsT[r], W->RsTX[r], W->fhat, W->ws, Pr, c.P, nullptr, nullptr, false));
     for (size_t k = 0; k < W->sc_s.size(); ++k) {
       if (W->sc_r[k] != (int)r) continue;
       BW_TRY(run_adj_fwd_transform(S, S->wav_t[W->sc_s[k]], c.coef(W->ws), c.wav_at(gwav, (int)k),

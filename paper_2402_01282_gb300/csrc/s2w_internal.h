@@ -161,6 +161,22 @@ struct TransformSpec {
   int inv_mb = 16;                                     // maps per block of the inverse contraction
 };
 
+// A real Pout x Pin radial map of the ball sliced for the tensor cores (kernels_radx.cu): seven
+// bf16 digits per entry, one exponent per row, [row tile][K chunk][slice][128 x 16].
+struct RadxMap {
+  int Pout = 0, Pin = 0, Mt = 0, nkc = 0;
+  uint16_t* tab = nullptr;
+  int* rexp = nullptr;
+};
+void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, std::vector<uint16_t>& tab,
+                std::vector<int>& rexp);
+// data-slice workspace (uint16 elements) of a radial map over B maps of ncol complex columns
+int64_t radx_ops_elems(int B, int Pin, int64_t ncol);
+// out[b][o][c] (+)= wo[o][l] sum_q R[o][q] wi[q][l] in[b][q][c] (c = l Mc + m) on the tensor cores,
+// float64-accurate; ops / fexp: workspaces of radx_ops_elems and B * L * Mc * 2 ints.
+cudaError_t launch_radx(const RadxMap& R, const double2* in, double2* out, int B, int L, int Mc, const double* wi,
+                        const double* wo, bool accumulate, uint16_t* ops, int* fexp, int* err, cudaStream_t st);
+
 // DFT forms of S2W_FP64_TC (TransformSpec::dft_form_*; reported by s2w_plan_dft_forms)
 enum DftForm { kDftAuto = 0, kDftComp = 1, kDftGemm = 2, kDftPfa = 3 };
 

@@ -51,9 +51,17 @@ def fields(L, P, B, cfg):
     return np.stack(out)
 
 
-@pytest.mark.parametrize("mode", [(0, 0), (3, 0), (0, 1), (4, 0)])
+# (precision, precompute) and the tolerance of the wavelet and scaling coefficients: float64
+# accuracy (1e-11) in the float64 modes; the reduced modes' targets for S2W_FP32_SPLIT (1e-5) and
+# S2W_BF16 (1e-3), whose radial maps run on the tensor cores float64-accurately and whose sphere
+# contractions carry the reduced precision
+BALL_MODES = [((0, 0), 1e-11), ((3, 0), 1e-11), ((0, 1), 1e-11), ((4, 0), 1e-11), ((1, 0), 1e-5), ((2, 0), 1e-3)]
+
+
+@pytest.mark.parametrize("mode,tol", BALL_MODES)
 @pytest.mark.parametrize("L,N,P,nu,J0,J0r,B", CASES)
-def test_ball_analysis_parity(lib, L, N, P, nu, J0, J0r, B, mode):
+def test_ball_analysis_parity(lib, L, N, P, nu, J0, J0r, B, mode, tol):
+    TOL = tol
     plan = lib.BallWavPlan(L, N, P, 2.0, nu, J0, J0r, batch=B, precision=mode[0], precompute=mode[1])
     f = fields(L, P, B, 920)
     wav, scal = plan.empty_wav(), plan.empty_field()
@@ -91,9 +99,10 @@ def test_ball_synthesis_arbitrary(lib, L, N, P, nu, J0, J0r, B):
         assert rel(got[b], ref) < TOL
 
 
+@pytest.mark.parametrize("mode", [0, 4])   # the adjoints' radial maps: SIMT and tensor cores (transposed tables)
 @pytest.mark.parametrize("L,N,P,nu,J0,J0r,B", CASES[:2])
-def test_ball_adjoints(lib, L, N, P, nu, J0, J0r, B):
-    plan = lib.BallWavPlan(L, N, P, 2.0, nu, J0, J0r, batch=B)
+def test_ball_adjoints(lib, L, N, P, nu, J0, J0r, B, mode):
+    plan = lib.BallWavPlan(L, N, P, 2.0, nu, J0, J0r, batch=B, precision=mode)
     rng = synth.rng_for(922, L)
     x = synth.pixels_random((B, P, L, 2 * L - 1), rng)
     gw = synth.pixels_random((plan.wav_elems,), rng)
@@ -128,11 +137,12 @@ def test_ball_adjoints(lib, L, N, P, nu, J0, J0r, B):
         assert abs(lhs - inner(x[b], fs)) < TOL * np.linalg.norm(x[b]) * (np.linalg.norm(gw) + np.linalg.norm(gs)) * 10
 
 
-def test_ball_full_size_config(lib):
+@pytest.mark.parametrize("mode", [0, 4])   # S2W_FP64, and S2W_FP64_TC (the ball study's mode)
+def test_ball_full_size_config(lib, mode):
     """L = P = 128, N = 4, lambda = nu = 2, J0 = J0' = 0, one real field."""
     import torch
     L, N, P, lam, nu = 128, 4, 128, 2.0, 2.0
-    plan = lib.BallWavPlan(L, N, P, lam, nu, 0, 0, batch=1)
+    plan = lib.BallWavPlan(L, N, P, lam, nu, 0, 0, batch=1, precision=mode)
     _, _, K = laguerre.quadrature(P)
     pq = [1, 5, 37, 127]   # p = 1 reaches the lowest radial scale (kappa^0(1) = 1)
     a = [synth.flm_random(L, synth.rng_for(5, q), reality=True) for q in range(len(pq))]
