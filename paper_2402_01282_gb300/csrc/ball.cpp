@@ -248,11 +248,13 @@ s2w_status s2w_ball_plan_create(const s2w_ball_params* prm, void* stream, s2w_ba
     // Rf as stored is [p][i] (row p); Ri is [i][p]: the inverse map f_r[i] = sum_p K_p(r_i) f_p[p]
     // has rows i, so its matrix is Ri itself
     std::vector<uint16_t> tab;
-    std::vector<int> rexp;
-    build_radx(Rf, P, P, &B->RfX, tab, rexp);
-    if ((s = up(B, tab, &B->RfX.tab, st)) || (s = up(B, rexp, &B->RfX.rexp, st))) return destroy(B), s;
-    build_radx(Ri, P, P, &B->RiX, tab, rexp);
-    if ((s = up(B, tab, &B->RiX.tab, st)) || (s = up(B, rexp, &B->RiX.rexp, st))) return destroy(B), s;
+    std::vector<int> rexp, kexp;
+    build_radx(Rf, P, P, &B->RfX, tab, rexp, kexp);
+    if ((s = up(B, tab, &B->RfX.tab, st)) || (s = up(B, rexp, &B->RfX.rexp, st)) || (s = up(B, kexp, &B->RfX.kexp, st)))
+      return destroy(B), s;
+    build_radx(Ri, P, P, &B->RiX, tab, rexp, kexp);
+    if ((s = up(B, tab, &B->RiX.tab, st)) || (s = up(B, rexp, &B->RiX.rexp, st)) || (s = up(B, kexp, &B->RiX.kexp, st)))
+      return destroy(B), s;
     std::vector<uint16_t> ops((size_t)radx_ops_elems(p.batch, P, ncol(B)), 0);
     std::vector<int> fx((size_t)p.batch * ncol(B) * 2, 0);
     if ((s = up(B, ops, &B->rops, st)) || (s = up(B, fx, &B->rfexp, st))) return destroy(B), s;

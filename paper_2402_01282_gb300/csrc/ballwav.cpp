@@ -225,12 +225,16 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
     for (int i = 0; i < rows; ++i)
       for (int k = 0; k < cols; ++k) MT[(size_t)k * rows + i] = M[(size_t)i * cols + k];
     std::vector<uint16_t> tab;
-    std::vector<int> rexp;
+    std::vector<int> rexp, kexp;
     s2w_status s2;
-    build_radx(M, rows, cols, X, tab, rexp);
-    if ((s2 = upload_vec(W, tab, &X->tab, st)) || (s2 = upload_vec(W, rexp, &X->rexp, st))) return s2;
-    build_radx(MT, cols, rows, XT, tab, rexp);
-    if ((s2 = upload_vec(W, tab, &XT->tab, st)) || (s2 = upload_vec(W, rexp, &XT->rexp, st))) return s2;
+    build_radx(M, rows, cols, X, tab, rexp, kexp);
+    if ((s2 = upload_vec(W, tab, &X->tab, st)) || (s2 = upload_vec(W, rexp, &X->rexp, st)) ||
+        (s2 = upload_vec(W, kexp, &X->kexp, st)))
+      return s2;
+    build_radx(MT, cols, rows, XT, tab, rexp, kexp);
+    if ((s2 = upload_vec(W, tab, &XT->tab, st)) || (s2 = upload_vec(W, rexp, &XT->rexp, st)) ||
+        (s2 = upload_vec(W, kexp, &XT->kexp, st)))
+      return s2;
     return S2W_OK;
   };
   std::vector<float2> a2, a2T;

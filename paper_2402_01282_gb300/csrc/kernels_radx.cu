@@ -6,7 +6,12 @@
 // a real Pout x Pin matrix R (P <= 256 radial nodes or coefficients) applied to every complex
 // angular coefficient column, with optional per-(row, l) weights before (wi) and after (wo).
 //
-// R is sliced once at plan time (one exponent per row, seven bf16 digits of a 47-bit fixed-point
+// The radial matrices span a huge dynamic range along the node index (the Gauss-Laguerre weights
+// grow like e^{x_i}, the basis decays like e^{-x_i/2}), so both operands are first balanced by an
+// exact power-of-two scale per reduction index q: R f = (R D^-1)(D f) with D = diag 2^{k_q},
+// k_q = -ilogb(max_o |R[o][q]|).  Fixed-point slicing then errs by ~2^-47 of the largest term of a
+// sum, as floating point does, instead of 2^-47 max|R| max|f|.
+// R D^-1 is sliced once at plan time (one exponent per row, seven bf16 digits of a 47-bit fixed-point
 // value, [row tile][K chunk][slice][128 x 16] core-matrix tiles); per call, k_radx_prep gives
 // every data column (batch, c, re|im) its exponent over the K nodes and its seven slices
 // ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm runs 28 digit-pair MMAs
@@ -46,6 +51,7 @@ struct RArgs {
   int accumulate;
   const uint16_t* tab;
   const int* rexp;
+  const int* kexp;  // [Pin] the balancing exponents k_q (data scaled by 2^k_q)
   uint16_t* ops;   // [B * cg][nkc][7][32 x 16]
   int* fexp;       // [B][ncol][2] column exponents (re, im)
   uint32_t idesc;
@@ -65,8 +71,10 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
   for (int q = 0; q < a.Pin; ++q) {
     const double2 v = inb[(int64_t)q * a.ncol];
     const double w = a.wi != nullptr ? a.wi[(int64_t)q * a.L + l] : 1.0;
-    er = max(er, ebound_prod(v.x, w));
-    ei = max(ei, ebound_prod(v.y, w));
+    const int kq = a.kexp[q];
+    const int br = ebound_prod(v.x, w), bi = ebound_prod(v.y, w);
+    if (br > 0) er = max(er, br + kq);   // |v w 2^k_q| < 2^(bound + k_q)
+    if (bi > 0) ei = max(ei, bi + kq);
     bad |= (bexp(v.x) == 0x7FF) | (bexp(v.y) == 0x7FF);
   }
   if (bad) atomicCAS(a.err, 0, (int)S2W_ENONFINITE);
@@ -88,8 +96,9 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
         if (q < a.Pin) {
           const double2 v = inb[(int64_t)q * a.ncol];
           const double w = a.wi != nullptr ? a.wi[(int64_t)q * a.L + l] : 1.0;
-          xr[v2] = fix47_prod(v.x, w, fr);
-          xi[v2] = fix47_prod(v.y, w, fi);
+          const int kq = a.kexp[q];   // round(v w 2^k_q 2^(47 - f)) = fix47_prod(v, w, f - k_q)
+          xr[v2] = fix47_prod(v.x, w, fr - kq);
+          xi[v2] = fix47_prod(v.y, w, fi - kq);
         }
       }
       uint32_t d0[kSl], d1[kSl], e0[kSl], e1[kSl];
@@ -244,26 +253,34 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
 
 }  // namespace
 
-// Host: the sliced table of a row-major Pout x Pin float64 matrix (row exponents e_o with
-// max_q |M[o][q]| < 2^e_o; zero rows get e = 0).
+// Host: the balancing exponents k_q = -ilogb(max_o |M[o][q]|) (0 for a zero column) and the sliced
+// table of the row-major Pout x Pin float64 matrix M D^-1 (row exponents e_o with
+// max_q |(M D^-1)[o][q]| < 2^e_o; zero rows get e = 0).
 void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, std::vector<uint16_t>& tab,
-                std::vector<int>& rexp) {
+                std::vector<int>& rexp, std::vector<int>& kexp) {
   map->Pout = Pout;
   map->Pin = Pin;
   map->Mt = (Pout + 127) / 128;
   map->nkc = (Pin + 15) / 16;
   tab.assign((size_t)map->Mt * map->nkc * kRAChunk, 0);
   rexp.assign((size_t)map->Mt * 128, 0);
+  kexp.assign((size_t)Pin, 0);
+  for (int q = 0; q < Pin; ++q) {
+    double mx = 0.0;
+    for (int o = 0; o < Pout; ++o) mx = std::max(mx, std::fabs(M[(size_t)o * Pin + q]));
+    if (mx > 0.0) kexp[q] = -std::ilogb(mx);
+  }
+  auto scaled = [&](int o, int q) { return std::ldexp(M[(size_t)o * Pin + q], kexp[q]); };   // exact
   for (int o = 0; o < map->Mt * 128; ++o) {
     int e = 0;
     if (o < Pout) {
       double mx = 0.0;
-      for (int q = 0; q < Pin; ++q) mx = std::max(mx, std::fabs(M[(size_t)o * Pin + q]));
+      for (int q = 0; q < Pin; ++q) mx = std::max(mx, std::fabs(scaled(o, q)));
       if (mx > 0.0) e = std::ilogb(mx) + 1;   // mx < 2^e
     }
     rexp[o] = e;
     for (int q = 0; q < map->nkc * 16; ++q) {
-      const double v = (o < Pout && q < Pin) ? M[(size_t)o * Pin + q] : 0.0;
+      const double v = (o < Pout && q < Pin) ? scaled(o, q) : 0.0;
       uint16_t d[kSl];
       host_digits(v, e, d);
       const size_t base = ((size_t)(o >> 7) * map->nkc + (q >> 4)) * kRAChunk;
@@ -295,6 +312,7 @@ cudaError_t launch_radx(const RadxMap& R, const double2* in, double2* out, int B
   a.accumulate = accumulate ? 1 : 0;
   a.tab = R.tab;
   a.rexp = R.rexp;
+  a.kexp = R.kexp;
   a.ops = ops;
   a.fexp = fexp;
   a.idesc = tc::make_idesc(128, kRN, 1, 0, 0);   // bf16 slices

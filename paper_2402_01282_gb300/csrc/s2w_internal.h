@@ -167,9 +167,10 @@ struct RadxMap {
   int Pout = 0, Pin = 0, Mt = 0, nkc = 0;
   uint16_t* tab = nullptr;
   int* rexp = nullptr;
+  int* kexp = nullptr;   // [Pin] power-of-two balancing exponents of the reduction index
 };
 void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, std::vector<uint16_t>& tab,
-                std::vector<int>& rexp);
+                std::vector<int>& rexp, std::vector<int>& kexp);
 // data-slice workspace (uint16 elements) of a radial map over B maps of ncol complex columns
 int64_t radx_ops_elems(int B, int Pin, int64_t ncol);
 // out[b][o][c] (+)= wo[o][l] sum_q R[o][q] wi[q][l] in[b][q][c] (c = l Mc + m) on the tensor cores,
