@@ -8,10 +8,11 @@
 //
 // The radial matrices span a huge dynamic range along the node index (the Gauss-Laguerre weights
 // grow like e^{x_i}, the basis decays like e^{-x_i/2}), so both operands are first balanced by an
-// exact power-of-two scale per reduction index q: R f = (R D^-1)(D f) with D = diag 2^{k_q},
-// k_q = -ilogb(max_o |R[o][q]|).  Fixed-point slicing then errs by ~2^-47 of the largest term of a
-// sum, as floating point does, instead of 2^-47 max|R| max|f|.
-// R D^-1 is sliced once at plan time (one exponent per row, seven bf16 digits of a 47-bit fixed-point
+// exact power-of-two scale per reduction index q: R f = (R D)(D^-1 f) with D = diag 2^{k_q},
+// k_q = -ilogb(max_o |R[o][q]|), so every column of R D has its largest entry in [1, 2).
+// Fixed-point slicing then errs by ~2^-47 of the largest term of a sum, as floating point does,
+// instead of 2^-47 max|R| max|f|.
+// R D is sliced once at plan time (one exponent per row, seven bf16 digits of a 47-bit fixed-point
 // value, [row tile][K chunk][slice][128 x 16] core-matrix tiles); per call, k_radx_prep gives
 // every data column (batch, c, re|im) its exponent over the K nodes and its seven slices
 // ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm runs 28 digit-pair MMAs
@@ -51,7 +52,7 @@ struct RArgs {
   int accumulate;
   const uint16_t* tab;
   const int* rexp;
-  const int* kexp;  // [Pin] the balancing exponents k_q (data scaled by 2^k_q)
+  const int* kexp;  // [Pin] the balancing exponents k_q (table column scaled by 2^k_q, data by 2^-k_q)
   uint16_t* ops;   // [B * cg][nkc][7][32 x 16]
   int* fexp;       // [B][ncol][2] column exponents (re, im)
   uint32_t idesc;
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
     const double w = a.wi != nullptr ? a.wi[(int64_t)q * a.L + l] : 1.0;
     const int kq = a.kexp[q];
     const int br = ebound_prod(v.x, w), bi = ebound_prod(v.y, w);
-    if (br > 0) er = max(er, br + kq);   // |v w 2^k_q| < 2^(bound + k_q)
-    if (bi > 0) ei = max(ei, bi + kq);
+    if (br > 0) er = max(er, br - kq);   // |v w 2^-k_q| < 2^(bound - k_q)
+    if (bi > 0) ei = max(ei, bi - kq);
     bad |= (bexp(v.x) == 0x7FF) | (bexp(v.y) == 0x7FF);
   }
   if (bad) atomicCAS(a.err, 0, (int)S2W_ENONFINITE);
@@ -96,9 +97,9 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
         if (q < a.Pin) {
           const double2 v = inb[(int64_t)q * a.ncol];
           const double w = a.wi != nullptr ? a.wi[(int64_t)q * a.L + l] : 1.0;
-          const int kq = a.kexp[q];   // round(v w 2^k_q 2^(47 - f)) = fix47_prod(v, w, f - k_q)
-          xr[v2] = fix47_prod(v.x, w, fr - kq);
-          xi[v2] = fix47_prod(v.y, w, fi - kq);
+          const int kq = a.kexp[q];   // round(v w 2^-k_q 2^(47 - f)) = fix47_prod(v, w, f + k_q)
+          xr[v2] = fix47_prod(v.x, w, fr + kq);
+          xi[v2] = fix47_prod(v.y, w, fi + kq);
         }
       }
       uint32_t d0[kSl], d1[kSl], e0[kSl], e1[kSl];
@@ -254,8 +255,8 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
 }  // namespace
 
 // Host: the balancing exponents k_q = -ilogb(max_o |M[o][q]|) (0 for a zero column) and the sliced
-// table of the row-major Pout x Pin float64 matrix M D^-1 (row exponents e_o with
-// max_q |(M D^-1)[o][q]| < 2^e_o; zero rows get e = 0).
+// table of the row-major Pout x Pin float64 matrix M D, D = diag 2^{k_q} (row exponents e_o with
+// max_q |(M D)[o][q]| < 2^e_o; zero rows get e = 0).
 void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, std::vector<uint16_t>& tab,
                 std::vector<int>& rexp, std::vector<int>& kexp) {
   map->Pout = Pout;
