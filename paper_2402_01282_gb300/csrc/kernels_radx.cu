@@ -9,15 +9,19 @@
 // The radial matrices span a huge dynamic range along the node index (the Gauss-Laguerre weights
 // grow like e^{x_i}, the basis decays like e^{-x_i/2}), so both operands are first balanced by an
 // exact power-of-two scale per reduction index q: R f = (R D)(D^-1 f) with D = diag 2^{k_q},
-// k_q = -ilogb(max_o |R[o][q]|), so every column of R D has its largest entry in [1, 2).
-// Fixed-point slicing then errs by ~2^-47 of the largest term of a sum, as floating point does,
-// instead of 2^-47 max|R| max|f|.
-// R D is sliced once at plan time (one exponent per row, seven bf16 digits of a 47-bit fixed-point
+// k_q = -ilogb(max_o |R[o][q]|), so every column of R D has its largest entry in [1, 2); a zero
+// column of R takes no part in the data's exponent.  The sums then err by ~2^-54 of their largest
+// term, as float64 does, instead of by a fixed fraction of max|R| max|f|.
+// Eight digits, not the seven of the other sliced GEMMs: the chain of maps a ball wavelet scale
+// takes (the Laguerre transform of the field, then the top radial filter's synthesis at a node
+// where the filtered basis is small) amplifies the forward map's noise floor about a hundredfold,
+// and with seven digits the digit pairs left out (q + r >= 7, ~2^-44 of a term) put it at 1e-12.
+// R D is sliced once at plan time (one exponent per row, eight bf16 digits of a 54-bit fixed-point
 // value, [row tile][K chunk][slice][128 x 16] core-matrix tiles); per call, k_radx_prep gives
-// every data column (batch, c, re|im) its exponent over the K nodes and its seven slices
-// ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm runs 28 digit-pair MMAs
-// per K step into seven exact float32 accumulators (a pair sums to <= 2^12 K <= 2^20, seven pairs
-// < 2^23) through a three-stage bulk-copy pipeline, and the epilogue forms
+// every data column (batch, c, re|im) its exponent over the K nodes and its eight slices
+// ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm runs 36 digit-pair MMAs
+// per K step into eight exact float32 accumulators (a pair sums to <= 2^12 K <= 2^20, eight pairs
+// <= 2^23) through a three-stage bulk-copy pipeline, and the epilogue forms
 // 2^(e_row + f_col - 10) sum_q 2^(-7q) D_q in compensated float32, applies wo and writes or
 // accumulates.  Every mbarrier wait is bounded; a timeout sets the plan's error word.
 #include <cmath>
@@ -32,15 +36,62 @@
 namespace s2w {
 namespace {
 
+constexpr int kRSl = 8;   // slices per value
+// kexp of a zero column of R: its data is left out of the exponent and the slices
+constexpr int kRZeroCol = 1 << 20;
+
+// round(c r 2^(54 - e)) for |c r| < 2^e: floor(Mc Mr / 2^52) by one 64 x 64 high multiply, then a
+// rounding shift s = 2044 + e - Ec - Er >= 0 (at s = 0 the truncated bits below 2^52 of the
+// 106-bit product are dropped: an error below one unit of 2^(e - 54))
+__device__ __forceinline__ long long fix54_prod(double c, double r, int e) {
+  const unsigned long long uc = (unsigned long long)__double_as_longlong(c);
+  const unsigned long long ur = (unsigned long long)__double_as_longlong(r);
+  const int Ec = (int)(uc >> 52) & 0x7FF, Er = (int)(ur >> 52) & 0x7FF;
+  if (Ec == 0 || Er == 0) return 0;
+  const int sh = 2044 + e - Ec - Er;
+  if (sh >= 63) return 0;
+  const unsigned long long Mc = (uc & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long Mr = (ur & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long H = __umul64hi(Mc << 11, Mr << 1);   // floor(Mc Mr / 2^52)
+  const long long X = (long long)(sh > 0 ? (H + (1ull << (sh - 1))) >> sh : H);
+  return ((uc ^ ur) >> 63) ? -X : X;
+}
+
+// X (|X| <= 2^54) -> eight balanced base-128 digits in [-64, 63], most significant first, as float32
+// bit patterns (upper 16 bits = the bfloat16 of the same value): the plain base-128 digits of
+// X + 64 (128^8 - 1)/127, less 64.
+constexpr long long kDigitBias8 = 36312488334073920ll;   // 64 (128^8 - 1)/127
+__device__ __forceinline__ void digits8(long long X, uint32_t (&f)[kRSl]) {
+  const unsigned long long Y = (unsigned long long)(X + kDigitBias8);
+#pragma unroll
+  for (int i = 0; i < kRSl; ++i) {
+    const unsigned int u = (unsigned int)(Y >> (7 * (kRSl - 1 - i))) & 127u;
+    f[i] = __float_as_uint(__uint_as_float(0x4B000000u | u) - 8388672.0f);   // u - 64
+  }
+}
+
+// host: the eight bf16 slices of round(v 2^(54 - e)) for |v| < 2^e, in the device convention
+inline void host_digits8(double v, int e, uint16_t (&d)[kRSl]) {
+  const long long X = std::llround(std::ldexp(v, 54 - e));
+  const unsigned long long Y = (unsigned long long)(X + kDigitBias8);
+  for (int i = 0; i < kRSl; ++i) {
+    const int u = (int)((Y >> (7 * (kRSl - 1 - i))) & 127u) - 64;
+    const float f = (float)u;
+    uint32_t bits;
+    std::memcpy(&bits, &f, sizeof(bits));
+    d[i] = (uint16_t)(bits >> 16);
+  }
+}
+
 constexpr int kRT = 128;                       // GEMM threads: one per output row of a tile
 constexpr int kRN = 32;                        // GEMM columns per CTA: 16 complex (re, im)
 constexpr int kRATile = 128 * 16;              // one table slice chunk
 constexpr int kRBTile = kRN * 16;              // one data slice chunk
-constexpr int kRAChunk = kSl * kRATile;
-constexpr int kRBChunk = kSl * kRBTile;
+constexpr int kRAChunk = kRSl * kRATile;
+constexpr int kRBChunk = kRSl * kRBTile;
 constexpr int kRStage = kRAChunk + kRBChunk;
 constexpr int kRStages = 3;
-constexpr size_t kRSmem = (size_t)kRStages * kRStage * sizeof(uint16_t);   // 107520 B
+constexpr size_t kRSmem = (size_t)kRStages * kRStage * sizeof(uint16_t);   // 122880 B
 constexpr uint32_t kRWait = 1u << 20;
 
 struct RArgs {
@@ -53,7 +104,7 @@ struct RArgs {
   const uint16_t* tab;
   const int* rexp;
   const int* kexp;  // [Pin] the balancing exponents k_q (table column scaled by 2^k_q, data by 2^-k_q)
-  uint16_t* ops;   // [B * cg][nkc][7][32 x 16]
+  uint16_t* ops;   // [B * cg][nkc][8][32 x 16]
   int* fexp;       // [B][ncol][2] column exponents (re, im)
   uint32_t idesc;
   int* err;
@@ -73,10 +124,11 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
     const double2 v = inb[(int64_t)q * a.ncol];
     const double w = a.wi != nullptr ? a.wi[(int64_t)q * a.L + l] : 1.0;
     const int kq = a.kexp[q];
+    bad |= (bexp(v.x) == 0x7FF) | (bexp(v.y) == 0x7FF);
+    if (kq == kRZeroCol) continue;
     const int br = ebound_prod(v.x, w), bi = ebound_prod(v.y, w);
     if (br > 0) er = max(er, br - kq);   // |v w 2^-k_q| < 2^(bound - k_q)
     if (bi > 0) ei = max(ei, bi - kq);
-    bad |= (bexp(v.x) == 0x7FF) | (bexp(v.y) == 0x7FF);
   }
   if (bad) atomicCAS(a.err, 0, (int)S2W_ENONFINITE);
   const int fr = e_from(er), fi = e_from(ei);
@@ -86,7 +138,7 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
   const int64_t gg = (int64_t)b * a.cg + c / 16;
   const int jr = (int)(c % 16) * 2, ji = jr + 1;
   for (int kg = 0; kg < a.nkc * 2; ++kg) {
-    uint32_t wr[kSl][4], wim[kSl][4];
+    uint32_t wr[kRSl][4], wim[kRSl][4];
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
       long long xr[2], xi[2];
@@ -94,28 +146,28 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
       for (int v2 = 0; v2 < 2; ++v2) {
         const int q = kg * 8 + u + v2;
         xr[v2] = xi[v2] = 0;
-        if (q < a.Pin) {
+        if (q < a.Pin && a.kexp[q] != kRZeroCol) {
           const double2 v = inb[(int64_t)q * a.ncol];
           const double w = a.wi != nullptr ? a.wi[(int64_t)q * a.L + l] : 1.0;
-          const int kq = a.kexp[q];   // round(v w 2^-k_q 2^(47 - f)) = fix47_prod(v, w, f + k_q)
-          xr[v2] = fix47_prod(v.x, w, fr + kq);
-          xi[v2] = fix47_prod(v.y, w, fi + kq);
+          const int kq = a.kexp[q];   // round(v w 2^-k_q 2^(54 - f)) = fix54_prod(v, w, f + k_q)
+          xr[v2] = fix54_prod(v.x, w, fr + kq);
+          xi[v2] = fix54_prod(v.y, w, fi + kq);
         }
       }
-      uint32_t d0[kSl], d1[kSl], e0[kSl], e1[kSl];
-      digits7(xr[0], d0);
-      digits7(xr[1], d1);
-      digits7(xi[0], e0);
-      digits7(xi[1], e1);
+      uint32_t d0[kRSl], d1[kRSl], e0[kRSl], e1[kRSl];
+      digits8(xr[0], d0);
+      digits8(xr[1], d1);
+      digits8(xi[0], e0);
+      digits8(xi[1], e1);
 #pragma unroll
-      for (int s = 0; s < kSl; ++s) {
+      for (int s = 0; s < kRSl; ++s) {
         wr[s][u / 2] = __byte_perm(d0[s], d1[s], 0x7632);
         wim[s][u / 2] = __byte_perm(e0[s], e1[s], 0x7632);
       }
     }
     const int64_t o = (gg * a.nkc + (kg >> 1)) * kRBChunk + (kg & 1) * 64;
 #pragma unroll
-    for (int s = 0; s < kSl; ++s) {
+    for (int s = 0; s < kRSl; ++s) {
       *reinterpret_cast<uint4*>(a.ops + o + (int64_t)s * kRBTile + (jr >> 3) * 128 + (jr & 7) * 8) =
           make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
       *reinterpret_cast<uint4*>(a.ops + o + (int64_t)s * kRBTile + (ji >> 3) * 128 + (ji & 7) * 8) =
@@ -125,7 +177,7 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
 }
 
 // CTA (row tile, column group, map): thread 0 streams the K chunks (table and data slices) through
-// three stages and issues 28 MMAs per chunk into seven 128 x 32 accumulators; then every thread
+// three stages and issues 36 MMAs per chunk into eight 128 x 32 accumulators; then every thread
 // converts its row's 32 columns.
 __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -185,7 +237,7 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
       const uint32_t A0 = tc::smem_u32(stage0 + s * kRStage), B0 = A0 + kRAChunk * 2u;
       const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
 #pragma unroll
-      for (int qq = 0; qq < kSl; ++qq)
+      for (int qq = 0; qq < kRSl; ++qq)
 #pragma unroll
         for (int sa = 0; sa <= qq; ++sa)
           tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kRATile * 2 / 16)),
@@ -215,7 +267,7 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
     Acc acc[kRN];
 #pragma unroll
     for (int j = 0; j < kRN; ++j) acc[j] = Acc{0.f, 0.f};
-    for (int qq = kSl - 1; qq >= 0; --qq) {
+    for (int qq = kRSl - 1; qq >= 0; --qq) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * qq), v);
       const float w = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
@@ -254,7 +306,7 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
 
 }  // namespace
 
-// Host: the balancing exponents k_q = -ilogb(max_o |M[o][q]|) (0 for a zero column) and the sliced
+// Host: the balancing exponents k_q = -ilogb(max_o |M[o][q]|) (kRZeroCol for a zero column) and the sliced
 // table of the row-major Pout x Pin float64 matrix M D, D = diag 2^{k_q} (row exponents e_o with
 // max_q |(M D)[o][q]| < 2^e_o; zero rows get e = 0).
 void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, std::vector<uint16_t>& tab,
@@ -269,9 +321,11 @@ void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, s
   for (int q = 0; q < Pin; ++q) {
     double mx = 0.0;
     for (int o = 0; o < Pout; ++o) mx = std::max(mx, std::fabs(M[(size_t)o * Pin + q]));
-    if (mx > 0.0) kexp[q] = -std::ilogb(mx);
+    kexp[q] = mx > 0.0 ? -std::ilogb(mx) : kRZeroCol;
   }
-  auto scaled = [&](int o, int q) { return std::ldexp(M[(size_t)o * Pin + q], kexp[q]); };   // exact
+  auto scaled = [&](int o, int q) {   // exact; a zero column stays zero
+    return kexp[q] == kRZeroCol ? 0.0 : std::ldexp(M[(size_t)o * Pin + q], kexp[q]);
+  };
   for (int o = 0; o < map->Mt * 128; ++o) {
     int e = 0;
     if (o < Pout) {
@@ -282,11 +336,11 @@ void build_radx(const std::vector<double>& M, int Pout, int Pin, RadxMap* map, s
     rexp[o] = e;
     for (int q = 0; q < map->nkc * 16; ++q) {
       const double v = (o < Pout && q < Pin) ? scaled(o, q) : 0.0;
-      uint16_t d[kSl];
-      host_digits(v, e, d);
+      uint16_t d[kRSl];
+      host_digits8(v, e, d);
       const size_t base = ((size_t)(o >> 7) * map->nkc + (q >> 4)) * kRAChunk;
       const size_t in = (size_t)((((o & 127) >> 3) * 2 + ((q & 15) >> 3)) * 64 + (o & 7) * 8 + (q & 7));
-      for (int s = 0; s < kSl; ++s) tab[base + (size_t)s * kRATile + in] = d[s];
+      for (int s = 0; s < kRSl; ++s) tab[base + (size_t)s * kRATile + in] = d[s];
     }
   }
 }
@@ -297,6 +351,7 @@ int64_t radx_ops_elems(int B, int Pin, int64_t ncol) {
 
 cudaError_t launch_radx(const RadxMap& R, const double2* in, double2* out, int B, int L, int Mc, const double* wi,
                         const double* wo, bool accumulate, uint16_t* ops, int* fexp, int* err, cudaStream_t st) {
+  if (R.Pin > 256) return cudaErrorInvalidValue;   // eight pair sums of K <= 256 terms stay below 2^24
   RArgs a{};
   a.in = in;
   a.out = out;
