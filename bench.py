@@ -179,6 +179,10 @@ PRECISIONS = {"fp64": 0, "fp64_table": 0, "fp64_native": 3, "fp32_split": 1, "bf
 # fp64_tc (every transform); one kernel in the float64 modes.  (The reduced modes, not a headline,
 # mix both: their wavelet contractions are operand prep + GEMM, their SHT one table kernel.)
 KERNELS_PER_CONTRACTION = {"fp64_tc": 3}
+# kernels of one azimuthal DFT by form (forward, inverse): 0 SIMT (one kernel); 1 direct tensor-core
+# GEMM (slicing prologue + GEMM); 2 prime-factor (forward: gamma-DFT prologue + tensor-core kernel;
+# inverse: column prologue + tensor-core kernel + gamma synthesis)
+DFT_KERNELS = {0: (1, 1), 1: (2, 2), 2: (2, 3)}
 PRECOMPUTE = {"fp64_table": 1}
 PRECISION_DOC = {
     "fp64": "float64 accuracy: Wigner-d recursion in float64; l-contractions, DFTs and colatitude "
@@ -597,12 +601,11 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
                 "d2h_bytes_per_step": int(f.numel() * 8), "max_rel_err": e2e_err},
         # the trace records one region per DFT and per contraction; a contraction region launches
-        # KERNELS_PER_CONTRACTION[precision] kernels of the library, a DFT region 2 in the direct
-        # tensor-core form (prologue + GEMM) and 1 in the prime-factor and SIMT forms (every
-        # transform's forward and inverse DFT once per step)
+        # KERNELS_PER_CONTRACTION[precision] kernels of the library; every transform's forward and
+        # inverse DFT run once per step, with DFT_KERNELS[form] (forward, inverse) kernels each
         "gpu_launches": int(sum(v[0] * KERNELS_PER_CONTRACTION.get(args.precision, 1)
                                 for k, v in trace.items() if k.startswith("wigner"))
-                            + args.steps * sum(2 if form == 1 else 1 for pair in dft_forms for form in pair)),
+                            + args.steps * sum(DFT_KERNELS[fw][0] + DFT_KERNELS[iv][1] for fw, iv in dft_forms)),
     }
     if world == 1 and not args.no_cpu_baseline:
         dt, cerr = cpu_baseline_sample()

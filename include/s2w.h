@@ -75,12 +75,14 @@ typedef enum {
  *                  precomputed Wigner-d tables and the data cut into seven 7-bit integer slices
  *                  (bf16), the slice products exact and their float32 sums exact (Ozaki's
  *                  error-free splitting); the azimuthal DFTs on the tensor cores by the same
- *                  slicing (the symmetric odd-length DFT as two GEMMs against sliced twiddle
- *                  tables) where the carried n fit (at most 16 per ring), else, and for the
- *                  gamma DFTs, compensated float32 pairs; s2w_plan_autotune may pick the
- *                  compensated DFTs where they are faster.  The tables are always precomputed
- *                  (precompute is ignored).  L <= 512 and at most 512 rings (S2W_EUNSUPPORTED
- *                  above). */
+ *                  slicing: the prime-factor form (2L - 1 = n1 n2, the n2-point stage a sliced
+ *                  GEMM, the n1-point stage and the gamma DFT in compensated float32) where
+ *                  2L - 1 factors with n2 < 128, else the direct form (the symmetric odd-length
+ *                  DFT as two GEMMs against sliced twiddle tables) where the carried n fit (at
+ *                  most 16 per ring), else compensated float32 pairs; s2w_plan_autotune picks
+ *                  among them by timing, s2w_plan_set_dft_forms forces one.  The tables are
+ *                  always precomputed (precompute is ignored).  L <= 512 and at most 512 rings
+ *                  (S2W_EUNSUPPORTED above). */
 typedef enum { S2W_FP64 = 0, S2W_FP32_SPLIT = 1, S2W_BF16 = 2, S2W_FP64_NATIVE = 3, S2W_FP64_TC = 4 } s2w_precision;
 
 /* S2W_SAMPLING_MW  McEwen-Wiaux: L rings; the forward transforms' colatitude integral is

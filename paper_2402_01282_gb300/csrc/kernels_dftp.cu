@@ -18,7 +18,7 @@
 //
 // Exactness of the GEMM: the table (scale s < 2^e_tw) and the data (one exponent f per ring,
 // max |x| < 2^f) are rounded to 47-bit fixed point and cut into seven balanced base-128 digits;
-// the 28 digit-pair MMAs with i + i' = q <= 6 of a K step go to accumulator q (seven 128 x 64
+// the 34 digit-pair MMAs with i + i' = q <= 7 of a K step go to accumulator q (eight 128 x 64
 // float32 accumulators in TMEM), whose partial sums are integers below 2^24 (K <= 128), so every
 // accumulator is exact; C = 2^(e_tw + f - 10) sum_q 2^(-7q) D_q, summed smallest weight first in
 // compensated float32.
@@ -427,12 +427,12 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
         tc::fence_after_sync();
         const uint32_t ab = A0 + (uint32_t)(c * kSl) * atile, bb = tc::smem_u32(Bs + s * kPChunk);
 #pragma unroll
-        for (int qq = 0; qq < kSl; ++qq)
+        for (int qq = 0; qq < kDiag; ++qq)
 #pragma unroll
-          for (int sa = 0; sa <= qq; ++sa)
+          for (int sa = diag_lo(qq); sa <= diag_hi(qq); ++sa)
             tc::mma_f16(tmem + (uint32_t)(64 * qq), tc::make_sdesc(ab + (uint32_t)sa * atile, 128, 256),
                         tc::make_sdesc(bb + (uint32_t)(qq - sa) * btile, 128, 256), a.idesc,
-                        (c > 0 || sa > 0) ? 1u : 0u);
+                        (c > 0 || sa > diag_lo(qq)) ? 1u : 0u);
         tc::mma_commit(&freeb[s]);
         mma = gc + 1;
         if (c == nkc - 1) tc::mma_commit(&acc_full);
@@ -477,26 +477,31 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
       }
       return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
     };
-    // the seven accumulators of one 16-column chunk, smallest weight first: two halves of 8
-    // columns, each with its 7 loads in flight before one wait
+    // the eight accumulators of one 16-column chunk, smallest weight first: two halves of 8
+    // columns, each in two groups of four accumulators with their loads in flight before one wait
     auto drain = [&](int chunk, Acc (&acc)[16]) {
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
-        uint32_t r[kSl][8];
-#pragma unroll
-        for (int qq = 0; qq < kSl; ++qq)
-          tc::tmem_ld8_nowait(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * qq + 16 * chunk + 8 * hf),
-                              r[qq]);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int qq = 0; qq < kSl; ++qq) tc::tmem_regs_ready(r[qq]);
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[8 * hf + u] = Acc{0.f, 0.f};
+#pragma unroll 1
+        for (int grp = 1; grp >= 0; --grp) {
+          uint32_t r[4][8];
 #pragma unroll
-        for (int qq = kSl - 1; qq >= 0; --qq) {
-          const float wq = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
+          for (int g4 = 0; g4 < 4; ++g4)
+            tc::tmem_ld8_nowait(tmem + ((uint32_t)(32 * quarter) << 16) +
+                                    (uint32_t)(64 * (4 * grp + g4) + 16 * chunk + 8 * hf),
+                                r[g4]);
+          tc::tmem_wait_ld();
 #pragma unroll
-          for (int u = 0; u < 8; ++u) two_sum_add(acc[8 * hf + u], __uint_as_float(r[qq][u]) * wq);
+          for (int g4 = 0; g4 < 4; ++g4) tc::tmem_regs_ready(r[g4]);
+#pragma unroll
+          for (int g4 = 3; g4 >= 0; --g4) {
+            const int qq = 4 * grp + g4;
+            const float wq = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) two_sum_add(acc[8 * hf + u], __uint_as_float(r[g4][u]) * wq);
+          }
         }
       }
     };

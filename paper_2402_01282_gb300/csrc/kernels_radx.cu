@@ -12,10 +12,10 @@
 // k_q = -ilogb(max_o |R[o][q]|), so every column of R D has its largest entry in [1, 2); a zero
 // column of R takes no part in the data's exponent.  The sums then err by ~2^-54 of their largest
 // term, as float64 does, instead of by a fixed fraction of max|R| max|f|.
-// Eight digits, not the seven of the other sliced GEMMs: the chain of maps a ball wavelet scale
-// takes (the Laguerre transform of the field, then the top radial filter's synthesis at a node
-// where the filtered basis is small) amplifies the forward map's noise floor about a hundredfold,
-// and with seven digits the digit pairs left out (q + r >= 7, ~2^-44 of a term) put it at 1e-12.
+// Eight digits (54-bit fixed point), not the seven of the other sliced GEMMs: the chain of maps a
+// ball wavelet scale takes (the Laguerre transform of the field, then the top radial filter's
+// synthesis at a node where the filtered basis is small) amplifies the forward map's noise floor
+// about a hundredfold, and 47-bit operands would leave it near 1e-13 where float64 reaches 1e-15.
 // R D is sliced once at plan time (one exponent per row, eight bf16 digits of a 54-bit fixed-point
 // value, [row tile][K chunk][slice][128 x 16] core-matrix tiles); per call, k_radx_prep gives
 // every data column (batch, c, re|im) its exponent over the K nodes and its eight slices

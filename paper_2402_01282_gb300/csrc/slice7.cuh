@@ -15,6 +15,13 @@ namespace s2w {
 namespace {
 
 constexpr int kSl = 7;   // slices per value
+// Digit-pair diagonals i + j = 0 .. 7 of a product of two sliced values are summed (34 MMAs): the
+// pairs of diagonal 7 weigh up to ~2^-44 of a term, and leaving them out would put the products'
+// error well above the 47-bit rounding of the operands; diagonals 8 and up stay below 2^-51.
+constexpr int kDiag = kSl + 1;
+// the slices (i, j = qq - i) of diagonal qq, both below kSl
+__host__ __device__ constexpr int diag_lo(int qq) { return qq > kSl - 1 ? qq - (kSl - 1) : 0; }
+__host__ __device__ constexpr int diag_hi(int qq) { return qq < kSl - 1 ? qq : kSl - 1; }
 
 __device__ __forceinline__ int core16(int r, int k) { return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
