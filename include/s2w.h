@@ -294,14 +294,56 @@ s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
  * relative), not bit for bit. */
 s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f, void* stream);
 
+/* ---- m-sharded spin SHT (Sec. 4.4: one transform spread over several GPUs) ----------------
+ * The spin SHT factors into an l-contraction that is independent for every azimuthal frequency m
+ * (the sum over l of Eq. 3 at fixed m; for the forward transform, Eq. 2, with the colatitude
+ * quadrature of each m column, Sec. 3.2) and an azimuthal DFT that is independent for every
+ * colatitude ring.  These stage calls run each part on a range of m columns or of rings, so that
+ * R ranks can split one transform: rank r contracts its columns, the ranks exchange one block of
+ * the column buffer each (an all-to-all: rank r sends the rows of rank q's rings and its own
+ * columns to rank q), and rank r transforms its rings; the forward direction runs the same steps
+ * in the opposite order.  The paper distributes its transforms the same way over the order m.
+ *
+ * Column buffer cols: [batch][R(L)][Mc] complex float64 (R(L) = L rings on MW, 2L on DH; Mc = L
+ * columns m = 0..L-1 for real maps, else 2L-1 columns m = -(L-1)..L-1), column c holding
+ * m = c + m_min, row t ring t.  A contraction call reads or writes only columns [c_begin, c_end)
+ * of cols, a DFT call only rows [ring_begin, ring_end); ranges need 0 <= begin <= end <= Mc or
+ * R(L) (S2W_EINVAL otherwise), and an empty range does nothing.  Every stage runs the
+ * float64-accurate on-the-fly path in every precision mode (the Wigner-d recursion of S2W_FP64
+ * and compensated float32 DFTs; native float64 in S2W_FP64_NATIVE), so the stages composed over
+ * all ranges match s2w_sht_forward / s2w_sht_inverse to the float64 tolerance (1e-11 relative).
+ * flm and f have the layouts of s2w_sht_forward / s2w_sht_inverse.
+ *
+ * s2w_shard_layout: the ranges of rank `rank` of `nranks` for a plan with band-limit L, spin,
+ * reality and sampling (host only: no plan, no GPU).  Columns are split into contiguous ranges of
+ * near-equal contraction work (column m costs L - max(|m|, |spin|) degrees l), rings into
+ * contiguous ranges of near-equal count (floor(r R(L) / nranks) .. floor((r + 1) R(L) / nranks)).
+ * A rank may get an empty range when nranks exceeds the columns or rings. */
+s2w_status s2w_shard_layout(int L, int spin, int reality, int sampling, int nranks, int rank, int* c_begin,
+                            int* c_end, int* ring_begin, int* ring_end);
+/* flm -> columns [c_begin, c_end) of cols (every ring). */
+s2w_status s2w_sht_inverse_columns(const s2w_plan* plan, const void* flm, void* cols, int c_begin, int c_end,
+                                   void* stream);
+/* rows [ring_begin, ring_end) of cols (every column) -> those rings of f; other rings untouched. */
+s2w_status s2w_sht_inverse_rings(const s2w_plan* plan, const void* cols, void* f, int ring_begin, int ring_end,
+                                 void* stream);
+/* rings [ring_begin, ring_end) of f -> rows [ring_begin, ring_end) of cols (every column). */
+s2w_status s2w_sht_forward_rings(const s2w_plan* plan, const void* f, void* cols, int ring_begin, int ring_end,
+                                 void* stream);
+/* columns [c_begin, c_end) of cols (every ring) -> the coefficients of those m in flm (every l,
+ * overwritten); other m untouched. */
+s2w_status s2w_sht_forward_columns(const s2w_plan* plan, const void* cols, void* flm, int c_begin, int c_end,
+                                   void* stream);
+
 /* ---- runtime: autotuner and batch executor ------------------------------------------
  * s2w_plan_autotune times, on the plan's own shapes and workspace, the candidate launch shapes
  * of its kernels (threads per block of the DFT kernels: 128, 256, 384, 512; maps per block of the
  * on-the-fly inverse contraction: 4, 8, 16) for every transform of the plan (spin SHT,
  * scaling function, each wavelet scale) and keeps the fastest.  In S2W_FP64_TC it also times
- * both forms of the azimuthal DFTs of each transform and direction (tensor-core, compensated
- * float32; both float64-accurate) and keeps the faster; without autotuning the tensor-core form
- * runs wherever its tables exist.  Synchronises the stream; allocates a pixel scratch for the
+ * the forms of the azimuthal DFTs of each transform and direction (tensor-core prime-factor,
+ * tensor-core direct, compensated float32; all float64-accurate) and keeps the fastest; without
+ * autotuning the prime-factor form runs wherever its tables exist, else the direct form.
+ * Synchronises the stream; allocates a pixel scratch for the
  * duration of the call; overwrites the plan's workspaces.  The paper has no counterpart (its
  * kernels are compiled by XLA). */
 s2w_status s2w_plan_autotune(s2w_plan* plan, void* stream);

@@ -33,7 +33,8 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint",
            "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_plan_dft_forms", "s2w_batch_create",
            "s2w_batch_launch", "s2w_batch_destroy", "s2w_plan_device_bytes",
-           "s2w_plan_inject_timeout", "s2w_plan_set_dft_forms"]
+           "s2w_plan_inject_timeout", "s2w_plan_set_dft_forms", "s2w_shard_layout", "s2w_sht_inverse_columns",
+           "s2w_sht_inverse_rings", "s2w_sht_forward_rings", "s2w_sht_forward_columns"]
 KERNEL_KINDS = 5
 
 
@@ -69,6 +70,15 @@ def rings(L: int, sampling: int = 0) -> int:
     return 2 * L if sampling == S2W_SAMPLING_DH else L
 
 
+def shard_layout(L: int, spin: int, reality: bool, sampling: int, nranks: int, rank: int):
+    """(c_begin, c_end, ring_begin, ring_end) of rank `rank` of `nranks` for the m-sharded spin
+    SHT (s2w_shard_layout: host logic of the library, no GPU needed)."""
+    lib = load()
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib.s2w_shard_layout(L, spin, int(bool(reality)), sampling, nranks, rank, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
 def load(path: str = LIB_PATH):
     """Load libs2w.so (raises if it is missing: there is no CPU path)."""
     global _lib
@@ -88,6 +98,10 @@ def load(path: str = LIB_PATH):
     lib.s2w_sht_forward.argtypes = [vp, vp, vp, vp]
     lib.s2w_sht_inverse.argtypes = [vp, vp, vp, vp]
     lib.s2w_sht_inverse_static.argtypes = [vp, vp, vp, vp]
+    lib.s2w_shard_layout.argtypes = [ctypes.c_int] * 6 + [ip] * 4
+    for name in ("s2w_sht_inverse_columns", "s2w_sht_inverse_rings", "s2w_sht_forward_rings",
+                 "s2w_sht_forward_columns"):
+        getattr(lib, name).argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.s2w_wigner_forward.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.s2w_wigner_inverse.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.s2w_check.argtypes = [vp]
@@ -290,6 +304,39 @@ class Plan:
         """s2w_sht_inverse with its scratch in the library's fixed device array (allocates nothing)."""
         _check(_lib.s2w_sht_inverse_static(self._h, _ptr(flm, False, "flm", self._n_flm()),
                                            _ptr(f, self.real, "f", self._n_map()), _stream(stream)))
+
+    # ---------------------------------------------- m-sharded spin SHT stages (include/s2w.h)
+    def _n_cols(self):
+        return self.batch * self.R * self.Mc
+
+    def empty_cols(self, device="cuda"):
+        """Column buffer [batch, R(L), Mc] of the sharded SHT stages."""
+        import torch
+        return torch.empty((self.batch, self.R, self.Mc), dtype=torch.complex128, device=device)
+
+    def sht_inverse_columns(self, flm, cols, c_begin: int, c_end: int, stream=None):
+        """flm -> columns [c_begin, c_end) of cols (column c holds m = c + m_min)."""
+        _check(_lib.s2w_sht_inverse_columns(self._h, _ptr(flm, False, "flm", self._n_flm()),
+                                            _ptr(cols, False, "cols", self._n_cols()), c_begin, c_end,
+                                            _stream(stream)))
+
+    def sht_inverse_rings(self, cols, f, ring_begin: int, ring_end: int, stream=None):
+        """Rows [ring_begin, ring_end) of cols -> those rings of f."""
+        _check(_lib.s2w_sht_inverse_rings(self._h, _ptr(cols, False, "cols", self._n_cols()),
+                                          _ptr(f, self.real, "f", self._n_map()), ring_begin, ring_end,
+                                          _stream(stream)))
+
+    def sht_forward_rings(self, f, cols, ring_begin: int, ring_end: int, stream=None):
+        """Rings [ring_begin, ring_end) of f -> those rows of cols."""
+        _check(_lib.s2w_sht_forward_rings(self._h, _ptr(f, self.real, "f", self._n_map()),
+                                          _ptr(cols, False, "cols", self._n_cols()), ring_begin, ring_end,
+                                          _stream(stream)))
+
+    def sht_forward_columns(self, cols, flm, c_begin: int, c_end: int, stream=None):
+        """Columns [c_begin, c_end) of cols -> the coefficients of those m in flm."""
+        _check(_lib.s2w_sht_forward_columns(self._h, _ptr(cols, False, "cols", self._n_cols()),
+                                            _ptr(flm, False, "flm", self._n_flm()), c_begin, c_end,
+                                            _stream(stream)))
 
     def wigner_forward(self, s: int, f, flmn, stream=None):
         _check(_lib.s2w_wigner_forward(self._h, s, _ptr(f, self.real, "f", self._n_scale(s)),

@@ -455,6 +455,166 @@ s2w_status s2w_sht_inverse(const s2w_plan* cP, const void* flm, void* f, void* s
   return inv_transform(P, P->sht, in, f, P->map_elems, st);
 }
 
+// ---- m-sharded spin SHT: the stages of s2w_sht_inverse / s2w_sht_forward on a range of m
+// columns or of rings, on the float64-accurate on-the-fly kernels of every mode.
+
+s2w_status s2w_shard_layout(int L, int spin, int reality, int sampling, int nranks, int rank, int* c_begin,
+                            int* c_end, int* ring_begin, int* ring_end) {
+  if (L < 2 || nranks < 1 || rank < 0 || rank >= nranks) return fail(S2W_EINVAL, "need L >= 2 and 0 <= rank < nranks");
+  if (std::abs(spin) >= L || (reality && spin != 0)) return fail(S2W_EINVAL, "need |spin| < L (0 for real maps)");
+  if (sampling != S2W_SAMPLING_MW && sampling != S2W_SAMPLING_DH) return fail(S2W_EINVAL, "unknown sampling");
+  const int Mc = reality ? L : 2 * L - 1, mlo = reality ? 0 : -(L - 1), as = std::abs(spin);
+  // contraction work of column c: the degrees l = max(|m|, |spin|) .. L-1 (at least one)
+  auto cost = [&](int c) { return (int64_t)(L - std::max(std::abs(mlo + c), as)); };
+  int64_t total = 0;
+  for (int c = 0; c < Mc; ++c) total += cost(c);
+  // first column of part r: the smallest c whose preceding work reaches r/nranks of the total
+  auto bound = [&](int r) {
+    if (r >= nranks) return Mc;
+    int64_t cum = 0;
+    for (int c = 0; c < Mc; ++c) {
+      if (cum * nranks >= (int64_t)r * total) return c;
+      cum += cost(c);
+    }
+    return Mc;
+  };
+  const int nr = rings_of(sampling, L);
+  if (c_begin) *c_begin = bound(rank);
+  if (c_end) *c_end = bound(rank + 1);
+  if (ring_begin) *ring_begin = (int)((int64_t)rank * nr / nranks);
+  if (ring_end) *ring_end = (int)((int64_t)(rank + 1) * nr / nranks);
+  return S2W_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the SHT's transform with every tensor-core and table path switched off: the recursion kernels
+TransformSpec shard_spec(const s2w_plan* P) {
+  TransformSpec t = P->sht;
+  t.tc = nullptr;
+  t.tab = nullptr;
+  t.tcx = nullptr;
+  return t;
+}
+
+s2w_status shard_args(const s2w_plan* P, const void* a, bool a_real, const char* an, const void* b, bool b_real,
+                      const char* bn, int begin, int end, int limit) {
+  if (P == nullptr) return fail(S2W_EINVAL, "plan is NULL");
+  s2w_status s;
+  if ((s = check_ptr(a, a_real, an)) || (s = check_ptr(b, b_real, bn))) return s;
+  if (begin < 0 || begin > end || end > limit) return fail(S2W_EINVAL, "range outside 0 <= begin <= end <= limit");
+  return S2W_OK;
+}
+
+// column args for columns [c0, c1) of a [batch][R(L)][Mc] buffer
+ColumnArgs shard_cols(const s2w_plan* P, const TransformSpec& t, void* G, int c0, int c1) {
+  ColumnArgs c = cols(P, t.nact, P->p.L);
+  c.B = P->p.batch;
+  c.G = static_cast<double2*>(G) + c0;
+  c.mlo += c0;
+  c.ncol = c1 - c0;
+  return c;
+}
+
+// one map's rows [r0, r1) of a [batch][R(L)][Mc] buffer, and the matching pixel rings
+ColumnArgs shard_rows(const s2w_plan* P, const TransformSpec& t, const void* G, int b, int r0, int r1) {
+  ColumnArgs c = cols(P, t.nact, P->p.L);
+  c.B = 1;
+  c.G = const_cast<double2*>(static_cast<const double2*>(G)) + ((int64_t)b * c.nr + r0) * c.Mc;
+  c.nr = r1 - r0;
+  return c;
+}
+char* shard_pix(const s2w_plan* P, const void* f, int b, int r0) {
+  const size_t el = P->real ? sizeof(double) : sizeof(double2);
+  return const_cast<char*>(static_cast<const char*>(f)) +
+         ((int64_t)b * P->map_elems + (int64_t)r0 * (2 * P->p.L - 1)) * el;
+}
+
+}  // namespace
+
+extern "C" {
+
+s2w_status s2w_sht_inverse_columns(const s2w_plan* cP, const void* flm, void* cols_, int c_begin, int c_end,
+                                   void* stream) {
+  s2w_status s;
+  if ((s = shard_args(cP, flm, false, "flm", cols_, false, "cols", c_begin, c_end, cP ? cP->Mc : 0))) return s;
+  if (c_begin == c_end) return S2W_OK;
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const TransformSpec t = shard_spec(P);
+  CoefArgs in = flm_ws_args(P);
+  in.coef = static_cast<const double2*>(flm);
+  S2W_CUDA(launch_wigner_inverse(P, grid_of(P, t), t, in, shard_cols(P, t, cols_, c_begin, c_end), st),
+           "inverse contraction (column range)");
+  return S2W_OK;
+}
+
+s2w_status s2w_sht_inverse_rings(const s2w_plan* cP, const void* cols_, void* f, int ring_begin, int ring_end,
+                                 void* stream) {
+  s2w_status s;
+  const int nr = cP ? rings_of(cP->p.sampling, cP->p.L) : 0;
+  if ((s = shard_args(cP, cols_, false, "cols", f, cP && cP->real, "f", ring_begin, ring_end, nr))) return s;
+  if (ring_begin == ring_end) return S2W_OK;
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const TransformSpec t = shard_spec(P);
+  const GridTables& g = grid_of(P, t);
+  for (int b = 0; b < P->p.batch; ++b) {
+    const ColumnArgs c = shard_rows(P, t, cols_, b, ring_begin, ring_end);
+    void* pix = shard_pix(P, f, b, ring_begin);
+    S2W_CUDA(P->native64 ? launch_dft_inverse(P, g, t, c, pix, P->map_elems, P->real, st)
+                         : launch_dftc_inverse(g, t, c, pix, P->map_elems, P->real, st, false),
+             "azimuthal DFT (inverse, ring range)");
+  }
+  return S2W_OK;
+}
+
+s2w_status s2w_sht_forward_rings(const s2w_plan* cP, const void* f, void* cols_, int ring_begin, int ring_end,
+                                 void* stream) {
+  s2w_status s;
+  const int nr = cP ? rings_of(cP->p.sampling, cP->p.L) : 0;
+  if ((s = shard_args(cP, f, cP && cP->real, "f", cols_, false, "cols", ring_begin, ring_end, nr))) return s;
+  if (ring_begin == ring_end) return S2W_OK;
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const TransformSpec t = shard_spec(P);
+  const GridTables& g = grid_of(P, t);
+  for (int b = 0; b < P->p.batch; ++b) {
+    const ColumnArgs c = shard_rows(P, t, cols_, b, ring_begin, ring_end);
+    const void* pix = shard_pix(P, f, b, ring_begin);
+    S2W_CUDA(P->native64 ? launch_dft_forward(P, g, t, pix, P->map_elems, P->real, c, st)
+                         : launch_dftc_forward(g, t, pix, P->map_elems, P->real, c, st, false),
+             "azimuthal DFT (forward, ring range)");
+  }
+  return S2W_OK;
+}
+
+s2w_status s2w_sht_forward_columns(const s2w_plan* cP, const void* cols_, void* flm, int c_begin, int c_end,
+                                   void* stream) {
+  s2w_status s;
+  if ((s = shard_args(cP, cols_, false, "cols", flm, false, "flm", c_begin, c_end, cP ? cP->Mc : 0))) return s;
+  if (c_begin == c_end) return S2W_OK;
+  s2w_plan* P = const_cast<s2w_plan*>(cP);
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const TransformSpec t = shard_spec(P);
+  // the contraction accumulates: clear this range's coefficients of every (map, l) first
+  S2W_CUDA(cudaMemset2DAsync(static_cast<double2*>(flm) + c_begin, (size_t)P->Mc * sizeof(double2), 0,
+                             (size_t)(c_end - c_begin) * sizeof(double2), (size_t)P->p.batch * P->p.L, st),
+           "zero flm (column range)");
+  CoefArgs out = flm_ws_args(P);
+  out.coef = static_cast<double2*>(flm);
+  S2W_CUDA(launch_wigner_forward(P, grid_of(P, t), t,
+                                 shard_cols(P, t, const_cast<void*>(cols_), c_begin, c_end), out, st),
+           "forward contraction (column range)");
+  return S2W_OK;
+}
+
 static CoefArgs raw_args(const s2w_plan* P, int sc, const void* flmn) {
   const int Lj = P->Lj[sc], Nj = P->Nj[sc], Mcj = Mc_at(P, Lj);
   CoefArgs c;

@@ -181,6 +181,7 @@ struct WigInvArgs {
   int nact;
   double2* G;            // [B][nact][nr][Mc]
   int B, L, nr, Mc, mlo;
+  int ncol;              // columns launched (grid.x), a sub-range of a row of Mc
   RecTables T;
 };
 
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(kInvThreads) k_wig_inv(WigInvArgs a) {
 struct WigFwdArgs {
   const double2* G;      // [B][nact][nr][Mc]
   int B, L, nr, Mc, mlo;
+  int ncol;              // columns launched (grid.x), a sub-range of a row of Mc
   const int* nvals;
   int nact;
   const double2* mult;   // [L][nact]
@@ -537,7 +539,7 @@ int pick_mb(int B, int cap) {
 
 template <int MB>
 cudaError_t launch_inv_mb(const WigInvArgs& a, int nact, bool c32, cudaStream_t st) {
-  dim3 grid(a.Mc, nact, (a.nr + kInvThreads - 1) / kInvThreads);
+  dim3 grid(a.ncol, nact, (a.nr + kInvThreads - 1) / kInvThreads);
   if (c32) k_wig_inv<MB, true><<<grid, kInvThreads, 0, st>>>(a);
   else k_wig_inv<MB, false><<<grid, kInvThreads, 0, st>>>(a);
   return cudaGetLastError();
@@ -549,7 +551,7 @@ cudaError_t launch_fwd_k(const WigFwdArgs& a, int nact, cudaStream_t st) {
   const size_t smem = (size_t)a.nr * MB * sizeof(double2) + (size_t)LT * a.nr * sizeof(double) + 4 * LT * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_wig_fwd<MB, LT, C32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.Mc, nact);
+  dim3 grid(a.ncol, nact);
   k_wig_fwd<MB, LT, C32><<<grid, threads < 32 ? 32 : threads, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -646,6 +648,7 @@ cudaError_t launch_wigner_inverse(const s2w_plan* P, const GridTables& g, const 
   a.nr = out.nr;
   a.Mc = out.Mc;
   a.mlo = out.mlo;
+  a.ncol = out.ncol > 0 ? out.ncol : out.Mc;
   a.T = rec_tables(g);
   switch (pick_mb(out.B, t.inv_mb)) {
     case 1: return launch_inv_mb<1>(a, t.nact, !P->native64, st);
@@ -666,6 +669,7 @@ cudaError_t launch_wigner_forward(const s2w_plan* P, const GridTables& g, const 
   a.nr = in.nr;
   a.Mc = in.Mc;
   a.mlo = in.mlo;
+  a.ncol = in.ncol > 0 ? in.ncol : in.Mc;
   a.nvals = t.nvals;
   a.nact = t.nact;
   a.mult = t.mult_fwd;

@@ -264,6 +264,9 @@ struct ColumnArgs {
   // A column buffer G[b][nact][nr][Mc] (complex) on the SO(3)/S2 grid at L with nr rings.
   double2* G;
   int B, nact, L, nr, Mc, mlo;
+  // columns the float64 contractions launch (0: all Mc).  With G advanced by c0 columns and mlo
+  // by c0, they cover the sub-range [c0, c0 + ncol) of a row of Mc (Mc stays the row stride).
+  int ncol = 0;
 };
 
 // Pixel -> columns: azimuthal DFT (length 2L-1) and gamma DFT (length 2N-1), scaled by
