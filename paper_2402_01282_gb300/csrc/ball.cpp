@@ -220,6 +220,9 @@ s2w_status s2w_ball_plan_create(const s2w_ball_params* prm, void* stream, s2w_ba
     delete B;
     return s;
   }
+  // the radial maps amplify the sphere transforms' error about a hundredfold: in S2W_FP64_TC the
+  // sliced GEMMs of this plan also sum the digit-pair diagonal 7
+  B->sphere->slice_diag7 = 1;
   B->Mc = p.reality ? p.L : 2 * p.L - 1;
   const int P = p.P;
   const double tau = p.tau;

@@ -180,6 +180,9 @@ s2w_status s2w_ball_wav_plan_create(const s2w_ball_wav_params* prm, void* stream
     delete W;
     return s;
   }
+  // the radial maps amplify the sphere transforms' error about a hundredfold: in S2W_FP64_TC the
+  // sliced GEMMs of this plan also sum the digit-pair diagonal 7
+  W->sph->slice_diag7 = 1;
   cudaStream_t st = (cudaStream_t)stream;
   const int P = p.P, L = p.L;
   W->Mc = p.reality ? L : 2 * L - 1;

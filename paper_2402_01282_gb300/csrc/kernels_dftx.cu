@@ -11,7 +11,8 @@
 // shared by every ring, map and carried n: the columns.  Both GEMMs run exactly on bf16
 // tensor cores with float32 accumulators in TMEM: the twiddle tables (plan time) and the
 // folded data (every call) are cut into seven balanced base-128 digits of a 47-bit fixed-point
-// value, and the 34 digit-pair products with i + i' <= 7 are summed exactly (K <= 512).
+// value, and the 28 digit-pair products with i + i' <= 6 (34 with i + i' = 7 where the plan asks
+// for it) are summed exactly (K <= 512).
 //
 // Per call and direction, two kernels:
 //   k_dftx_fwd_prep / k_dftx_inv_prep (one block per ring and map): the gamma DFT on the map side
@@ -19,7 +20,7 @@
 //     per carried n >= 0 for real maps), the fold a, b in the integer domain, the column
 //     exponents and the seven slices of every column;
 //   k_dftx_gemm (one CTA per 128 frequencies and 32 columns): the cos GEMM, then the sin GEMM,
-//     through a three-stage bulk-copy pipeline into eight 128 x 32 TMEM accumulators; the
+//     through a three-stage bulk-copy pipeline into seven (eight) 128 x 32 TMEM accumulators; the
 //     epilogue forms X(k), X(n-k) and writes the columns G (forward) or, after the gamma
 //     synthesis over the carried n (inverse), the pixels.
 // Columns: ring (map b, ring t) and job q (a carried n, with its -n partner for real maps) give
@@ -79,6 +80,7 @@ struct XArgs {
   int e_tw;                 // table row exponent
   uint32_t idesc;
   int* err;
+  int ndiag;   // digit-pair diagonals summed: 7 (28 MMAs per K step) or 8 (34)
 };
 
 // 8 consecutive values (index pairs p0 .. p0+7) of one column -> one 16-byte core-matrix row per
@@ -367,15 +369,17 @@ __global__ void __launch_bounds__(kXT) k_dftx_gemm(XArgs a) {
       tc::fence_after_sync();
       const uint32_t A0 = tc::smem_u32(stage0 + s * kXStage), B0 = A0 + kXAChunk * 2u;
       // the slice operands of a stage differ only in their start address: descriptors by offset
-      // (address field = byte address / 16), all 34 MMAs unrolled
+      // (address field = byte address / 16), all 28 (34) MMAs unrolled
       const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
       const uint32_t acc0 = c > 0 ? 1u : 0u;
 #pragma unroll
-      for (int qq = 0; qq < kDiag; ++qq)
+      for (int qq = 0; qq < kDiag; ++qq) {
+        if (qq >= a.ndiag) break;   // uniform
 #pragma unroll
         for (int sa = diag_lo(qq); sa <= diag_hi(qq); ++sa)
           tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kXATile * 2 / 16)),
                       dB + (uint64_t)((qq - sa) * (kXBTile * 2 / 16)), a.idesc, sa > diag_lo(qq) ? 1u : acc0);
+      }
       tc::mma_commit(&bar_mma[s]);
       pend_mma |= 1u << s;
       if (c + kXStages - 1 < nkc) {
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(kXT) k_dftx_gemm(XArgs a) {
   auto drain = [&](Acc (&acc)[kXN / 2]) {
 #pragma unroll
     for (int j = 0; j < kXN / 2; ++j) acc[j] = Acc{0.f, 0.f};
-    for (int qq = kDiag - 1; qq >= 0; --qq) {
+    for (int qq = a.ndiag - 1; qq >= 0; --qq) {
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(32 * qq + 16 * half), v);
       const float w = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
@@ -572,6 +576,7 @@ XArgs make_xargs(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
   a.e_tw = tab.e;
   a.idesc = tc::make_idesc(128, kXN, 1, 0, 0);   // bf16 slices
   a.err = P->err_word;
+  a.ndiag = P->slice_diag7 ? kDiag : kDiag - 1;
   return a;
 }
 

@@ -9,17 +9,18 @@
 // (X = sum_i s_i 128^(6 - i), s_0 most significant).  Digits are exact in bf16 and the
 // product of two digits (|s t| <= 2^12) is exact in the MMA.
 //
-// Exact accumulation.  The pairs (i, i') of slices with i + i' = q (q = 0..7, 34 pairs) are
+// Exact accumulation.  The pairs (i, i') of slices with i + i' = q (q = 0..6, 28 pairs) are
 // summed into one float32 TMEM accumulator D_q: over K <= 512 reduction terms one pair sums
 // to |.| <= 2^21 and at most seven pairs share an accumulator, so every partial sum is an
 // integer below 2^24 and float32 holds it exactly, whatever the order of the additions.  The
-// six pairs of diagonal 7 are kept: together they can reach ~2^-44 of a term, above the operands'
-// own 47-bit rounding; the pairs with i + i' >= 8 stay below ~2^-51 and are dropped.  Then
-//   C[r][j] = 2^(e_r + f_j - 10) sum_{q=0..7} 2^(-7 q) D_q[r][j]
+// six pairs of diagonal 7 can reach ~2^-44 of a term together, above the operands' own 47-bit
+// rounding: they are summed where the plan asks for it (the ball's sphere plans), else dropped
+// with the pairs i + i' >= 8 (below ~2^-51).  Then
+//   C[r][j] = 2^(e_r + f_j - 10) sum_q 2^(-7 q) D_q[r][j]
 // (e_r: table row exponent, f_j: data column exponent), summed from the smallest weight up in
-// compensated float32 and converted to float64: each output carries ~2^-47 of
-// max_k|A[r][k]| max_k|B[k][j]| per reduction term, the float64 accuracy class of the rest of
-// the path.
+// compensated float32 and converted to float64: each output carries ~2^-44 (2^-47 with diagonal
+// 7) of max_k|A[r][k]| max_k|B[k][j]| per reduction term, the float64 accuracy class of the
+// rest of the path.
 //
 // The GEMMs are those of the reduced modes (one per (m, n), 128-row tiles, 32 columns = 16
 // maps x re/im): inverse rows beta, K = l (tables d^l_mn(beta)); forward rows l, K = beta'
@@ -29,8 +30,8 @@
 //          ((t nkc + c) 7 + s) 2048 + ((r/8) 2 + k/8) 64 + (r%8) 8 + k%8
 //   data   (chunk c, slice s): element (j, k) at (c 7 + s) 512 + ((j/8) 2 + k/8) 64 + (j%8) 8 + k%8
 // k_tcx_gemm: one CTA of 128 threads per (row tile, m, n); thread 0 drives a three-stage
-// pipeline of bulk copies (35 KB per stage: 7 table slices + 7 data slices) and 34 MMAs per
-// chunk; 105 KB of shared memory and 256 TMEM columns per CTA let two CTAs share an SM; every
+// pipeline of bulk copies (35 KB per stage: 7 table slices + 7 data slices) and 28 (or 34) MMAs
+// per chunk; 105 KB of shared memory and 256 TMEM columns per CTA let two CTAs share an SM; every
 // mbarrier wait is bounded and a timeout sets the plan's error word.
 #include "comp32.cuh"
 #include "s2w_internal.h"
@@ -291,6 +292,7 @@ struct GemmArgs {
   uint32_t idesc;
   int* err;
   int inject_timeout;       // test hook (s2w_plan_inject_timeout): make a bounded wait run out
+  int ndiag;                // digit-pair diagonals summed: 7 (28 MMAs per K step) or 8 (34)
 };
 
 template <bool FWD>
@@ -371,15 +373,17 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
         tc::fence_after_sync();
         const uint32_t A0 = tc::smem_u32(stage0 + s * kStageElems), B0 = A0 + kAChunk * 2u;
         // the slice operands of a stage differ only in their start address: descriptors by
-        // offset (address field = byte address / 16), all 34 MMAs unrolled
+        // offset (address field = byte address / 16), all 28 (34) MMAs unrolled
         const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
         const uint32_t acc0 = c > 0 ? 1u : 0u;
 #pragma unroll
-        for (int qq = 0; qq < kDiag; ++qq)
+        for (int qq = 0; qq < kDiag; ++qq) {
+          if (qq >= a.ndiag) break;   // uniform
 #pragma unroll
           for (int sa = diag_lo(qq); sa <= diag_hi(qq); ++sa)
             tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kATile * 2 / 16)),
                         dB + (uint64_t)((qq - sa) * (kBTile * 2 / 16)), a.idesc, sa > diag_lo(qq) ? 1u : acc0);
+        }
         tc::mma_commit(&bar_mma[s]);
         pend_mma |= 1u << s;
         if (c + kStages - 1 < nkc) {
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
     Acc acc[kN];
 #pragma unroll
     for (int j = 0; j < kN; ++j) acc[j] = Acc{0.f, 0.f};
-    for (int qq = kDiag - 1; qq >= 0; --qq) {
+    for (int qq = a.ndiag - 1; qq >= 0; --qq) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * qq), v);
       const float w = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
@@ -565,6 +569,7 @@ cudaError_t launch_tcx_inverse(const s2w_plan* P, const GridTables& g, const Tra
   a.lmin = tab.lmin;
   a.err = P->err_word;
   a.inject_timeout = P->inject_timeout;
+  a.ndiag = P->slice_diag7 ? kDiag : kDiag - 1;
   e = cudaFuncSetAttribute(k_tcx_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
   k_tcx_gemm<false><<<dim3(tab.Lb / 128, out.Mc, t.nact), kThreads, kSmem, st>>>(a);
@@ -627,6 +632,7 @@ cudaError_t launch_tcx_forward(const s2w_plan* P, const GridTables& g, const Tra
   a.lmin = tab.lmin;
   a.err = P->err_word;
   a.inject_timeout = P->inject_timeout;
+  a.ndiag = P->slice_diag7 ? kDiag : kDiag - 1;
   e = cudaFuncSetAttribute(k_tcx_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
   if (tab.klf_max == 0) return cudaSuccess;

@@ -15,9 +15,10 @@ namespace s2w {
 namespace {
 
 constexpr int kSl = 7;   // slices per value
-// Digit-pair diagonals i + j = 0 .. 7 of a product of two sliced values are summed (34 MMAs): the
-// pairs of diagonal 7 weigh up to ~2^-44 of a term, and leaving them out would put the products'
-// error well above the 47-bit rounding of the operands; diagonals 8 and up stay below 2^-51.
+// Digit-pair diagonals i + j = 0 .. 6 of a product of two sliced values are always summed (28
+// MMAs per K step); diagonal 7 (six more) when the plan asks for it.  The pairs of diagonal 7
+// weigh up to ~2^-44 of a term, above the operands' own 47-bit rounding; diagonals 8 and up stay
+// below 2^-51.  Accumulator q of diagonal q is exact either way.
 constexpr int kDiag = kSl + 1;
 // the slices (i, j = qq - i) of diagonal qq, both below kSl
 __host__ __device__ constexpr int diag_lo(int qq) { return qq > kSl - 1 ? qq - (kSl - 1) : 0; }
