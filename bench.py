@@ -291,7 +291,7 @@ def run_batching(torch, s2w, stream, flush, steps, autotune):
     plans, fd, wavs, scals, outs = [], [], [], [], []
     for L in (64, 128, 256, 512):
         for spin in (0, 2):
-            p = s2w.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8)
+            p = s2w.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8, precision=PRECISIONS["fp64_tc"])
             if autotune:
                 p.autotune()
             flm = np.stack([synth.flm_random(L, synth.rng_for(3, 16 * L + 2 * b + spin // 2), spin=spin,
@@ -331,7 +331,8 @@ def run_batching(torch, s2w, stream, flush, steps, autotune):
     for p in plans:
         p.close()
     return {"workload": "64 complex maps, L in {64,128,256,512} x 16, spin 0/2 alternating, N=4, lambda=2, "
-                        "white a_lm; 8 plans x 8 maps, precision fp64 (on-the-fly recursion)",
+                        "white a_lm; 8 plans x 8 maps, precision fp64_tc (the headline's: tables precomputed "
+                        "at plan creation, contractions and DFTs on the tensor cores)",
             "unit": "transforms/s (fwd+inv)", "autotuned": bool(autotune), "max_rel_err": err, **res}
 
 
@@ -660,6 +661,30 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_footprint():
+    """Precompute cost of the float64-accurate tensor-core mode (the paper's precompute mode,
+    Sec. 4.2): plan creation time and the device bytes of the sliced tables and workspaces for
+    one real map at L in {64, 128, 256, 512} with N = 4 and N = 8 (lambda = 2, J0 = 2).  One JSON
+    line; nothing is timed on the transforms."""
+    import time
+
+    import torch
+    import paper_2402_01282_gb300 as s2w
+    s2w.load()
+    rows = []
+    for n_dir in (4, 8):
+        for Lf in (64, 128, 256, 512):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan = s2w.Plan(Lf, n_dir, 2.0, 2, reality=True, batch=1, precision=PRECISIONS["fp64_tc"])
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            tab, ws = plan.device_bytes()
+            rows.append({"L": Lf, "N": n_dir, "create_s": dt, "table_bytes": tab, "workspace_bytes_1map": ws})
+            plan.close()
+    print(json.dumps({"footprint": "fp64_tc plans, one real map, lambda=2, J0=2", "plans": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -677,7 +702,12 @@ def main():
     ap.add_argument("--maps", type=int, default=B,
                     help="maps per GPU (default 16, the headline workload; smaller batches are for "
                          "profiler captures of single kernels, not bench lines)")
+    ap.add_argument("--footprint", action="store_true",
+                    help="only report plan creation time and table bytes of fp64_tc plans at L = 64..512")
     args = ap.parse_args()
+    if args.footprint:
+        run_footprint()
+        return
     if args.maps != B:
         globals()["B"] = args.maps
     world, rank, local = dist_init()

@@ -7,6 +7,7 @@ Definitions followed
 * Forward Wigner transform (Sec. 2.2, Eq. 4): F^l_mn = int f(rho) D^l_mn(rho) dOmega(rho)
   (no conjugate), inverse (Eq. 5): f = sum (2l+1)/(8 pi^2) F^l_mn D^l*_mn.
 * D^l_mn(alpha, beta, gamma) = d^l_mn(beta) exp(-i(m alpha + n gamma)) (Sec. 5.2, Eq. 47).
+* ``wigner_inverse_ring``: Eq. 5 at a single colatitude, for sampled checks of large transforms.
 * sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) exp(i m phi) (the MW
   convention; the paper is silent).  For s = 0 this is the Condon-Shortley Y_lm.
 
@@ -120,6 +121,29 @@ def wigner_inverse(flmn: np.ndarray, L: int, N: int, samp: str = "mw") -> np.nda
     Eg = np.exp(1j * np.outer(ns, sampling.gammas(N)))               # [n, g]
     H = np.einsum('nmb,ma->nba', G, Ea)                              # alpha sum
     return np.einsum('nba,ng->gba', H, Eg)                           # gamma sum
+
+
+def wigner_inverse_ring(flmn: np.ndarray, L: int, N: int, beta: float) -> np.ndarray:
+    """The inverse Wigner transform (Eq. 5) at one colatitude beta: f(alpha_a, beta, gamma_g) as
+    [2N-1 gamma, 2L-1 alpha].  The same sum as ``wigner_inverse``, evaluated at one beta: d^l_mn(beta)
+    = (-i)^(m-n) sum_j V[m, j] V[n, j] exp(-i lambda_j beta) from the J_x eigenvectors (the route
+    of ``wigner.fourier_coeffs``, summed at this beta), then the l, m and n sums, so a single ring
+    of a large transform costs O(N L^3) multiply-adds and no [n, m, k] array."""
+    ms = _mrange(L)
+    ns = np.arange(-(N - 1), N)
+    H = np.zeros((2 * N - 1, 2 * L - 1), dtype=np.complex128)        # [n, m]
+    for l in range(L):
+        ok = np.abs(ns) <= l
+        nsv = ns[ok]
+        _, V = wigner.jx_eigen(l)
+        Vr = V[:, ::-1]                                              # column k + l: eigenvalue -k
+        k = np.arange(-l, l + 1)
+        d = wigner._phase(np.arange(-l, l + 1), nsv) * ((Vr * np.exp(1j * k * beta)[None, :]) @ Vr[nsv + l].T)
+        sl = slice(L - 1 - l, L + l)
+        H[ok, sl] += (2 * l + 1) / (8 * np.pi ** 2) * flmn[ok, l, sl] * d.T
+    Ea = np.exp(1j * np.outer(ms, sampling.phis(L)))                  # [m, a]
+    Eg = np.exp(1j * np.outer(ns, sampling.gammas(N)))               # [n, g]
+    return Eg.T @ (H @ Ea)                                           # [g, a]
 
 
 def wigner_forward(f: np.ndarray, L: int, N: int, samp: str = "mw") -> np.ndarray:

@@ -30,24 +30,39 @@ def analysis(f: np.ndarray, L: int, N: int, lam: float, J0: int, spin: int = 0,
     R is the ring count of the sampling (``samp``: "mw" or "dh") at each band-limit."""
     flm = harmonic.sht_forward(f, L, spin, samp)
     LP = filters.scaling_bandlimit(L, lam, J0)
+    wphi = harmonic.sht_inverse(scaling_coefficients(flm, L, lam, J0, spin), LP, 0, samp)
+    wavs = []
+    for (j, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0):
+        coef = scale_coefficients(flm, L, N, lam, j, Lj, Nj, spin)
+        w = harmonic.wigner_inverse(coef, Lj, Nj, samp)
+        wavs.append(w.real.copy() if reality else w)
+    return wavs, (wphi.real.copy() if reality else wphi)
+
+
+def scaling_coefficients(flm: np.ndarray, L: int, lam: float, J0: int, spin: int = 0) -> np.ndarray:
+    """The harmonic coefficients of the scaling map (Eq. 29): sqrt(4 pi/(2l+1)) Phi_l0 f_lm for
+    l < L_Phi, as [L_Phi, 2L_Phi-1]; W^Phi is their spin-0 inverse SHT (Eq. 41)."""
+    LP = filters.scaling_bandlimit(L, lam, J0)
     phi = filters.scaling_filter(L, lam, J0, spin)
     wphi_lm = np.zeros((LP, 2 * LP - 1), dtype=np.complex128)
     sl = _embed_slice(LP, L)
     for l in range(LP):
         wphi_lm[l] = math.sqrt(4 * math.pi / (2 * l + 1)) * phi[l] * flm[l, sl]
-    wphi = harmonic.sht_inverse(wphi_lm, LP, 0, samp)
-    wavs = []
-    for (j, Lj, Nj) in filters.scale_bandlimits(L, N, lam, J0):
-        psi = filters.wavelet_filter(L, N, lam, j, spin)
-        coef = np.zeros((2 * Nj - 1, Lj, 2 * Lj - 1), dtype=np.complex128)
-        slj = _embed_slice(Lj, L)
-        for l in range(Lj):
-            for n in range(-(Nj - 1), Nj):
-                coef[n + Nj - 1, l] = (8 * math.pi ** 2 / (2 * l + 1)) * flm[l, slj] * \
-                    np.conj(psi[l, n + N - 1])
-        w = harmonic.wigner_inverse(coef, Lj, Nj, samp)
-        wavs.append(w.real.copy() if reality else w)
-    return wavs, (wphi.real.copy() if reality else wphi)
+    return wphi_lm
+
+
+def scale_coefficients(flm: np.ndarray, L: int, N: int, lam: float, j: int, Lj: int, Nj: int,
+                       spin: int = 0) -> np.ndarray:
+    """The Wigner coefficients of wavelet scale j (Eq. 27): (8 pi^2/(2l+1)) f_lm conj(Psi^j_ln) for
+    l < L_j, |n| < N_j, as [2N_j-1, L_j, 2L_j-1]; W^j is their inverse Wigner transform (Eq. 40)."""
+    psi = filters.wavelet_filter(L, N, lam, j, spin)
+    coef = np.zeros((2 * Nj - 1, Lj, 2 * Lj - 1), dtype=np.complex128)
+    slj = _embed_slice(Lj, L)
+    for l in range(Lj):
+        for n in range(-(Nj - 1), Nj):
+            coef[n + Nj - 1, l] = (8 * math.pi ** 2 / (2 * l + 1)) * flm[l, slj] * \
+                np.conj(psi[l, n + N - 1])
+    return coef
 
 
 def synthesis(wavs, wphi: np.ndarray, L: int, N: int, lam: float, J0: int, spin: int = 0,

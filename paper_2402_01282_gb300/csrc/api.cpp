@@ -220,7 +220,9 @@ namespace s2w {
 int dft_form_used(const s2w_plan* P, const TransformSpec& t, bool fwd) {
   if (!P->tcx) return kDftComp;
   const int f = fwd ? t.dft_form_fwd : t.dft_form_inv;
-  const bool pfa = (fwd ? (const void*)t.dftp_fwd : (const void*)t.dftp_inv) != nullptr;
+  // the prime-factor kernel sums the digit-pair diagonals 0..6 only: plans that also sum
+  // diagonal 7 (the ball's) take the direct form
+  const bool pfa = !P->slice_diag7 && (fwd ? (const void*)t.dftp_fwd : (const void*)t.dftp_inv) != nullptr;
   const bool gemm = (fwd ? (const void*)t.dftx_fwd : (const void*)t.dftx_inv) != nullptr;
   if (f == kDftComp) return kDftComp;
   if (f == kDftPfa && pfa) return kDftPfa;

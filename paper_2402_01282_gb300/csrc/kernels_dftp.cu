@@ -18,9 +18,9 @@
 //
 // Exactness of the GEMM: the table (scale s < 2^e_tw) and the data (one exponent f per ring,
 // max |x| < 2^f) are rounded to 47-bit fixed point and cut into seven balanced base-128 digits;
-// the 28 digit-pair MMAs with i + i' = q <= 6 of a K step (34 with q = 7 where the plan asks for
-// it) go to accumulator q (seven or eight 128 x 64 float32 accumulators in TMEM), whose partial
-// sums are integers below 2^24 (K <= 128), so every accumulator is exact; C = 2^(e_tw + f - 10) sum_q 2^(-7q) D_q, summed smallest weight first in
+// the 28 digit-pair MMAs with i + i' = q <= 6 of a K step go to accumulator q (seven 128 x 64
+// float32 accumulators in TMEM), whose partial sums are integers below 2^24 (K <= 128), so every
+// accumulator is exact (plans that also sum the diagonal i + i' = 7 use the direct form); C = 2^(e_tw + f - 10) sum_q 2^(-7q) D_q, summed smallest weight first in
 // compensated float32.
 //
 // GEMM columns come in passes of 64: slots of W = 2 n1 rounded up to a power of two columns
@@ -87,7 +87,6 @@ struct PArgs {
   int* fexp;                // [rings] ring exponents (0: an all-zero ring)
   float4* zbuf;             // inverse: [rings][job][n] Z_q(alpha), unscaled pairs
   int* err;
-  int ndiag;   // digit-pair diagonals summed: 7 (28 MMAs per K step) or 8 (34)
 };
 
 // n1-point DFT X(k) = sum_p Y(p) w^(SIGN p k), w = exp(2 pi i/N1), of compensated complex values
@@ -428,14 +427,12 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
         tc::fence_after_sync();
         const uint32_t ab = A0 + (uint32_t)(c * kSl) * atile, bb = tc::smem_u32(Bs + s * kPChunk);
 #pragma unroll
-        for (int qq = 0; qq < kDiag; ++qq) {
-          if (qq >= a.ndiag) break;   // uniform
+        for (int qq = 0; qq < kSl; ++qq)
 #pragma unroll
-          for (int sa = diag_lo(qq); sa <= diag_hi(qq); ++sa)
+          for (int sa = 0; sa <= qq; ++sa)
             tc::mma_f16(tmem + (uint32_t)(64 * qq), tc::make_sdesc(ab + (uint32_t)sa * atile, 128, 256),
                         tc::make_sdesc(bb + (uint32_t)(qq - sa) * btile, 128, 256), a.idesc,
-                        (c > 0 || sa > diag_lo(qq)) ? 1u : 0u);
-        }
+                        (c > 0 || sa > 0) ? 1u : 0u);
         tc::mma_commit(&freeb[s]);
         mma = gc + 1;
         if (c == nkc - 1) tc::mma_commit(&acc_full);
@@ -480,35 +477,26 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
       }
       return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
     };
-    // the seven (eight) accumulators of one 16-column chunk, smallest weight first: two halves of 8
-    // columns, each in two groups of four accumulators with their loads in flight before one wait
+    // the seven accumulators of one 16-column chunk, smallest weight first: two halves of 8
+    // columns, each with its 7 loads in flight before one wait
     auto drain = [&](int chunk, Acc (&acc)[16]) {
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
+        uint32_t r[kSl][8];
+#pragma unroll
+        for (int qq = 0; qq < kSl; ++qq)
+          tc::tmem_ld8_nowait(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * qq + 16 * chunk + 8 * hf),
+                              r[qq]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int qq = 0; qq < kSl; ++qq) tc::tmem_regs_ready(r[qq]);
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[8 * hf + u] = Acc{0.f, 0.f};
-#pragma unroll 1
-        for (int grp = 1; grp >= 0; --grp) {
-          uint32_t r[4][8];
 #pragma unroll
-          for (int g4 = 0; g4 < 4; ++g4)
-            tc::tmem_ld8_nowait(tmem + ((uint32_t)(32 * quarter) << 16) +
-                                    (uint32_t)(64 * (4 * grp + g4) + 16 * chunk + 8 * hf),
-                                r[g4]);
-          tc::tmem_wait_ld();
+        for (int qq = kSl - 1; qq >= 0; --qq) {
+          const float wq = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
 #pragma unroll
-          for (int g4 = 0; g4 < 4; ++g4) tc::tmem_regs_ready(r[g4]);
-#pragma unroll
-          for (int g4 = 3; g4 >= 0; --g4) {
-            const int qq = 4 * grp + g4;
-            // accumulator 7 holds no MMA result when diagonal 7 is not summed: its bits are
-            // replaced by zero (a select, so whatever it holds never enters the sum)
-            const bool use = qq < a.ndiag;
-            const float wq = __uint_as_float((uint32_t)(127 - 7 * qq) << 23);   // 2^(-7 qq)
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              two_sum_add(acc[8 * hf + u], use ? __uint_as_float(r[g4][u]) * wq : 0.f);
-          }
+          for (int u = 0; u < 8; ++u) two_sum_add(acc[8 * hf + u], __uint_as_float(r[qq][u]) * wq);
         }
       }
     };
@@ -751,7 +739,6 @@ PArgs make_pargs(const s2w_plan* P, const GridTables& g, const TransformSpec& t,
   a.fexp = P->dftp_fexp;
   a.zbuf = P->dftp_z;
   a.err = P->err_word;
-  a.ndiag = P->slice_diag7 ? kDiag : kDiag - 1;
   return a;
 }
 

@@ -104,7 +104,8 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
       int& threads = fwd ? t->dft_threads_fwd : t->dft_threads_inv;
       std::vector<int> forms = {kDftComp};
       if (P->tcx && (fwd ? (const void*)t->dftx_fwd : (const void*)t->dftx_inv) != nullptr) forms.push_back(kDftGemm);
-      if (P->tcx && (fwd ? (const void*)t->dftp_fwd : (const void*)t->dftp_inv) != nullptr) forms.push_back(kDftPfa);
+      if (P->tcx && !P->slice_diag7 && (fwd ? (const void*)t->dftp_fwd : (const void*)t->dftp_inv) != nullptr)
+        forms.push_back(kDftPfa);
       if (!P->tcx) forms = {kDftAuto};
       float best = 1e30f;
       int pick_th = threads, pick_form = form;
@@ -169,6 +170,7 @@ s2w_status s2w_plan_set_dft_forms(s2w_plan* P, int transform, int fwd, int inv) 
     if (code == 0) return kDftComp;
     const void* tab = code == 2 ? (f ? (const void*)t.dftp_fwd : (const void*)t.dftp_inv)
                                 : (f ? (const void*)t.dftx_fwd : (const void*)t.dftx_inv);
+    if (code == 2 && P->slice_diag7) return -1;   // the prime-factor kernel sums diagonals 0..6 only
     return (P->tcx && tab != nullptr) ? (code == 2 ? kDftPfa : kDftGemm) : -1;
   };
   const int ff = to_form(fwd, true), fi = to_form(inv, false);

@@ -6,14 +6,16 @@ executor (s2w_batch_*: several plans of mixed band-limit and spin replayed as on
 * A mixed batch (band-limits, spins, real and complex maps, batch sizes) run as one graph gives
   every plan's wavelet coefficients within 1e-11 of the oracle and its round trip within 1e-11.
 * The batching study's configuration (64 complex maps, L in {64, 128, 256, 512} x 16, spin 0 and
-  2 alternating, N = 4, white coefficients) as one graph: the round trip of every map within
-  1e-11, and one L = 64 map of it against the oracle.
+  2 alternating, N = 4, white coefficients) as one graph in the float64-accurate tensor-core
+  mode: the round trip of every map within 1e-11, and one map of each band-limit against the
+  oracle (every scale for L <= 256; at L = 512 the scaling map, every scale with L_j <= 256 and
+  two rings of each scale at L_j = 512, through the oracle's single-ring inverse transform).
 """
 import numpy as np
 import pytest
 
 import synth
-from oracle import harmonic, wavelet
+from oracle import filters, harmonic, sampling, wavelet
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -97,33 +99,54 @@ def test_batch_mixed_plans(lib):
 
 
 def test_batching_study_config(lib):
-    """64 complex maps, L in {64, 128, 256, 512} (16 each, spin 0 and 2 alternating), N = 4."""
-    import torch
-    plans, fd, wavs, scals, outs, f64 = [], [], [], [], [], None
+    """64 complex maps, L in {64, 128, 256, 512} (16 each, spin 0 and 2 alternating), N = 4, in
+    S2W_FP64_TC (the headline's precision): the DFT forms at these sizes are the prime-factor
+    kernels (127 = 1 x 127, 255 = 3 x 85, 511 = 7 x 73) and the direct form at 1023."""
+    plans, fd, wavs, scals, outs, checked = [], [], [], [], [], []
     for L in (64, 128, 256, 512):
         for spin in (0, 2):
-            p = lib.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8)
+            p = lib.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8, precision=lib.S2W_FP64_TC)
             flm = np.stack([synth.flm_random(L, synth.rng_for(3, 16 * L + 2 * b + spin // 2), spin=spin,
                                              variance=lambda l: np.ones_like(l)) for b in range(8)])
             x = p.empty_map()
             p.sht_inverse(to_dev(flm), x)   # timing-free input synthesis (band-limited maps)
+            if spin == {64: 2, 128: 0, 256: 2, 512: 0}[L]:   # one map per band-limit
+                f0 = harmonic.sht_inverse(flm[0], L, spin)   # the oracle's samples, shared by both sides
+                x[0] = to_dev(f0)
+                checked.append((len(plans), L, spin, f0))
             plans.append(p)
             fd.append(x)
             wavs.append(p.empty_wav())
             scals.append(p.empty_scal())
             outs.append(p.empty_map())
-            if L == 64 and spin == 2:
-                f64 = harmonic.sht_inverse(flm[0], L, spin)
     batch = lib.Batch(plans, fd, wavs, scals, outs, what=2)
     batch.launch()
     for p in plans:
         p.check()
     for x, o in zip(fd, outs):
         assert float((o - x).abs().max() / x.abs().max()) < TOL
-    # one map of the batch against the oracle (L = 64, spin 2, map 0)
-    p, w = plans[1], wavs[1].cpu().numpy()
-    W_ref, _ = wavelet.analysis(f64, 64, 4, 2.0, 0, 2, False)
-    for s in range(p.nscales):
-        got = w[0, p.wav_offsets[s]:p.wav_offsets[s + 1]].reshape(p.scale_shape(s))
-        assert rel(got, W_ref[s]) < TOL, s
+    for k, L, spin, f0 in checked:
+        p, w, sc = plans[k], wavs[k][0].cpu().numpy(), scals[k][0].cpu().numpy()
+        got = [w[p.wav_offsets[s]:p.wav_offsets[s + 1]].reshape(p.scale_shape(s)) for s in range(p.nscales)]
+        if L <= 256:
+            W_ref, Wp_ref = wavelet.analysis(f0, L, 4, 2.0, 0, spin, False)
+            for s in range(p.nscales):
+                assert rel(got[s], W_ref[s]) < TOL, (L, s)
+            assert rel(sc.reshape(Wp_ref.shape), Wp_ref) < TOL, L
+            continue
+        flm = harmonic.sht_forward(f0, L, spin)
+        LP = filters.scaling_bandlimit(L, 2.0, 0)
+        Wp_ref = harmonic.sht_inverse(wavelet.scaling_coefficients(flm, L, 2.0, 0, spin), LP, 0)
+        assert rel(sc.reshape(Wp_ref.shape), Wp_ref) < TOL
+        for s, (j, Lj, Nj) in enumerate(filters.scale_bandlimits(L, 4, 2.0, 0)):
+            assert (Lj, Nj) == (p.Lj[s], p.Nj[s])
+            coef = wavelet.scale_coefficients(flm, L, 4, 2.0, j, Lj, Nj, spin)
+            if Lj <= 256:
+                assert rel(got[s], harmonic.wigner_inverse(coef, Lj, Nj)) < TOL, (L, s)
+                continue
+            th = sampling.thetas(Lj)
+            rings = {t: harmonic.wigner_inverse_ring(coef, Lj, Nj, th[t]) for t in (3, 301)}
+            scale = max(np.abs(r).max() for r in rings.values())
+            for t, ring in rings.items():
+                assert np.abs(got[s][:, t, :] - ring).max() < TOL * scale, (L, s, t)
     batch.close()

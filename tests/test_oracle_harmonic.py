@@ -112,6 +112,43 @@ def test_wigner_inverse_bruteforce():
                 assert abs(got[g, b, a] - ref) < 1e-13
 
 
+def test_wigner_inverse_ring_bruteforce():
+    """One ring of Eq. 5 at an arbitrary colatitude (not a grid ring) against Wigner's explicit
+    sum for d^l_mn, term by term."""
+    L, N, beta = 5, 3, 0.7345
+    flmn = synth.flmn_random(L, N, synth.rng_for(104, 0))
+    al, ga = sampling.phis(L), sampling.gammas(N)
+    got = harmonic.wigner_inverse_ring(flmn, L, N, beta)
+    for g in range(2 * N - 1):
+        for a in range(2 * L - 1):
+            ref = 0j
+            for l in range(L):
+                for m in range(-l, l + 1):
+                    for n in range(-min(l, N - 1), min(l, N - 1) + 1):
+                        D = d_explicit(l, m, n, beta) * np.exp(-1j * (m * al[a] + n * ga[g]))
+                        ref += (2 * l + 1) / (8 * math.pi ** 2) * flmn[n + N - 1, l, m + L - 1] * np.conj(D)
+            assert abs(got[g, a] - ref) < 1e-13
+
+
+@pytest.mark.parametrize("L,N,samp", [(12, 4, "mw"), (9, 9, "dh"), (16, 2, "mw")])
+def test_wigner_inverse_ring_matches_every_ring(L, N, samp):
+    """Every grid ring of the full inverse transform, and the pole: at beta = 0, d^l_mn = delta_mn,
+    so f(alpha, 0, gamma) = sum_l (2l+1)/(8 pi^2) sum_{|m| < N} f^l_mm exp(i m (alpha + gamma))."""
+    flmn = synth.flmn_random(L, N, synth.rng_for(105, L))
+    full = harmonic.wigner_inverse(flmn, L, N, samp)
+    th = sampling.thetas_for(L, samp)
+    scale = np.abs(full).max()
+    for t in range(len(th)):
+        assert np.abs(harmonic.wigner_inverse_ring(flmn, L, N, th[t]) - full[:, t]).max() < 1e-13 * scale
+    al, ga = sampling.phis(L), sampling.gammas(N)
+    pole = np.zeros((2 * N - 1, 2 * L - 1), dtype=np.complex128)
+    for l in range(L):
+        for m in range(-min(l, N - 1), min(l, N - 1) + 1):
+            pole += (2 * l + 1) / (8 * math.pi ** 2) * flmn[m + N - 1, l, m + L - 1] * \
+                np.exp(1j * m * (al[None, :] + ga[:, None]))
+    assert np.abs(harmonic.wigner_inverse_ring(flmn, L, N, 0.0) - pole).max() < 1e-13 * scale
+
+
 @pytest.mark.parametrize("L,N", [(1, 1), (3, 2), (8, 3), (10, 10)])
 def test_wigner_forward_exact_on_bandlimited(L, N):
     flmn = synth.flmn_random(L, N, synth.rng_for(104, L))
