@@ -704,9 +704,21 @@ def main():
                          "profiler captures of single kernels, not bench lines)")
     ap.add_argument("--footprint", action="store_true",
                     help="only report plan creation time and table bytes of fp64_tc plans at L = 64..512")
+    ap.add_argument("--ball-only", type=int, default=0, metavar="LP",
+                    help="only run the ball study, at L = P = LP (128 is the study's size; smaller sizes are "
+                         "for profiler captures of single kernels, not bench lines)")
     args = ap.parse_args()
     if args.footprint:
         run_footprint()
+        return
+    if args.ball_only:
+        import torch
+        import paper_2402_01282_gb300 as s2w
+        s2w.load()
+        globals().update(BALL_L=args.ball_only, BALL_P=args.ball_only)
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        print(json.dumps(run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)), flush=True)
         return
     if args.maps != B:
         globals()["B"] = args.maps
