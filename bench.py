@@ -285,13 +285,13 @@ def run_sampling(torch, s2w, stream, flush, steps, flm, precision, autotune):
 
 # Batching study: 64 complex maps, L in {64, 128, 256, 512} x 16 (spin 0 and 2 alternating),
 # N = 4, lambda = 2, white coefficients; 8 plans of 8 maps.
-def run_batching(torch, s2w, stream, flush, steps, autotune):
+def run_batching(torch, s2w, stream, flush, steps, autotune, precision="fp64_tc"):
     import numpy as np
     import synth
     plans, fd, wavs, scals, outs = [], [], [], [], []
     for L in (64, 128, 256, 512):
         for spin in (0, 2):
-            p = s2w.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8, precision=PRECISIONS["fp64_tc"])
+            p = s2w.Plan(L, 4, 2.0, 0, spin=spin, reality=False, batch=8, precision=PRECISIONS[precision])
             if autotune:
                 p.autotune()
             flm = np.stack([synth.flm_random(L, synth.rng_for(3, 16 * L + 2 * b + spin // 2), spin=spin,
@@ -331,8 +331,8 @@ def run_batching(torch, s2w, stream, flush, steps, autotune):
     for p in plans:
         p.close()
     return {"workload": "64 complex maps, L in {64,128,256,512} x 16, spin 0/2 alternating, N=4, lambda=2, "
-                        "white a_lm; 8 plans x 8 maps, precision fp64_tc (the headline's: tables precomputed "
-                        "at plan creation, contractions and DFTs on the tensor cores)",
+                        f"white a_lm; 8 plans x 8 maps, precision {precision}",
+            "precision_detail": PRECISION_DOC[precision],
             "unit": "transforms/s (fwd+inv)", "autotuned": bool(autotune), "max_rel_err": err, **res}
 
 
@@ -544,6 +544,11 @@ def run_ours(args, world, rank, local):
     batching = None
     if not args.no_batching:
         batching = run_batching(torch, s2w, stream, flush, max(3, args.steps // 2), not args.no_autotune)
+        # the study's "FP32 contractions with FP64 recursion" arm: split-precision tensor-core
+        # contractions against tables computed by the float64 recursion
+        batching["fp32_split"] = {k: v for k, v in run_batching(torch, s2w, stream, flush, max(3, args.steps // 2),
+                                                                not args.no_autotune, "fp32_split").items()
+                                  if k in ("max_rel_err", "sequential_one_stream", "graph")}
     samplings = None
     if not args.no_sampling:
         samplings = run_sampling(torch, s2w, stream, flush, max(3, args.steps // 2), flm, args.precision,

@@ -70,7 +70,7 @@ typedef enum {
  * S2W_BF16         split-bf16: the same with bf16 hi + lo pairs for the tables and the data
  *                  (three MMAs per K step, float32 accumulation; 1e-3 target).
  *                  Both reduced modes keep the spin SHT Y, Y^-1 float64-accurate and
- *                  support L <= 256 (S2W_EUNSUPPORTED above).
+ *                  support L and the ring count <= 512 (S2W_EUNSUPPORTED above).
  * S2W_FP64_TC      float64 accuracy (1e-11 target) with every l-contraction on the tensor cores:
  *                  precomputed Wigner-d tables and the data cut into seven 7-bit integer slices
  *                  (bf16), the slice products exact and their float32 sums exact (Ozaki's

@@ -256,19 +256,29 @@ __device__ void stage2_sym(const float4* tmp0, float4* AB0, const float4* tw, in
     Acc cr{x0.x, x0.y}, ci{x0.z, x0.w}, sr{0.f, 0.f}, si{0.f, 0.f};
     const int step = (n1 * kk) % n;
     if (PLAIN) {
-      // float32 arithmetic: the twiddles cos, sin(2 pi j kk/n2) by the rotation recurrence
-      // (error ~j 2^-24, far below the reduced modes' budgets) instead of a table load per j
+      // float32 arithmetic: the twiddles cos, sin(2 pi p kk/n2) by the rotation recurrence
+      // instead of a table load per p, re-seeded from the table every 16 steps so that its error
+      // stays ~16 2^-24 whatever the length (a plain recurrence errs ~p 2^-24)
       const float4 w1 = tw[step];
       float wr = w1.x, wi = w1.z;
+      int e = step;   // table index of the twiddle of pair p = j + 1
       for (int j = 0; j < h2; ++j) {
         const float4 a = ab[2 * j], b = ab[2 * j + 1];
         cr.s = fmaf(a.x, wr, cr.s);
         ci.s = fmaf(a.z, wr, ci.s);
         sr.s = fmaf(b.x, wi, sr.s);
         si.s = fmaf(b.z, wi, si.s);
-        const float t = fmaf(wr, w1.x, -wi * w1.z);
-        wi = fmaf(wr, w1.z, wi * w1.x);
-        wr = t;
+        e += step;
+        if (e >= n) e -= n;
+        if ((j & 15) == 15) {
+          const float4 w = tw[e];
+          wr = w.x;
+          wi = w.z;
+        } else {
+          const float t = fmaf(wr, w1.x, -wi * w1.z);
+          wi = fmaf(wr, w1.z, wi * w1.x);
+          wr = t;
+        }
       }
     } else {
       int e = step;

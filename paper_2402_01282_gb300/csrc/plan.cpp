@@ -648,8 +648,8 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     err = "unknown precision mode";
     return S2W_EINVAL;
   }
-  if ((p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16) && p.L > 256) {
-    err = "the reduced-precision tensor-core modes support L <= 256 in this build";
+  if ((p.precision == S2W_FP32_SPLIT || p.precision == S2W_BF16) && std::max(p.L, rings_of(p.sampling, p.L)) > 512) {
+    err = "the reduced-precision tensor-core modes support L and the ring count <= 512 in this build";
     return S2W_EUNSUPPORTED;
   }
   if (p.precompute != 0 && p.precompute != 1) { err = "precompute must be 0 or 1"; return S2W_EINVAL; }

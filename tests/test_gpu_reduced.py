@@ -3,12 +3,13 @@ compared with the float64 oracle as max|x - x_ref| / max|x_ref| per output.
 
 S2W_FP32_SPLIT (fp16 hi/lo tables and data, float32 accumulation) is held to its 1e-5
 target everywhere, S2W_BF16 (split-bf16: bf16 hi/lo tables and data) to its 1e-3 target:
-every wavelet map, the round trip and the small operator tests."""
+every wavelet map, the round trip and the small operator tests, at the L = 256 workload (the
+first and last map of the batch) and at L = 512 (one map; the top scales sampled on two rings)."""
 import numpy as np
 import pytest
 
 import synth
-from oracle import harmonic, wavelet
+from oracle import filters, harmonic, sampling, wavelet
 
 pytestmark = pytest.mark.gpu
 SPLIT, BF16 = 1, 2
@@ -92,4 +93,59 @@ def test_full_size_reduced(lib, oracle_256, mode):
     rt = max(rel(x, y) for x, y in zip(f2.cpu().numpy(), f))
     print(f"mode {mode}: per-scale rel err {['%.2e' % e for e in errs]}, round trip {rt:.2e}")
     assert max(errs) < TOLS_MAPS[mode] and rt < TOLS_ROUND_TRIP[mode]
+    # the last map of the batch too, every scale and the scaling map
+    W15, Wp15 = wavelet.analysis(f[B - 1], L, N, lam, J0, 0, True)
+    wv = wav[B - 1].cpu().numpy()
+    for s, w_ref in enumerate(W15):
+        got = wv[plan.wav_offsets[s]:plan.wav_offsets[s + 1]].reshape(plan.scale_shape(s))
+        assert rel(got, w_ref) < TOLS_MAPS[mode], s
+    assert rel(scal[B - 1].cpu().numpy(), Wp15) < TOLS_MAPS[mode]
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_512():
+    """One real map at L = 512 (N = 4, lambda = 2, J0 = 2) and its oracle wavelet coefficients:
+    every scale with L_j <= 256 in full, two rings of each scale at L_j = 512 (the oracle's
+    single-ring inverse Wigner transform), and the scaling map."""
+    L, N, J0 = 512, 4, 2
+    a = synth.flm_random(L, synth.rng_for(802, L), reality=True)
+    f = harmonic.sht_inverse(a, L).real
+    flm = harmonic.sht_forward(f, L)
+    scales = []
+    for (j, Lj, Nj) in filters.scale_bandlimits(L, N, 2.0, J0):
+        coef = wavelet.scale_coefficients(flm, L, N, 2.0, j, Lj, Nj, 0)
+        if Lj <= 256:
+            scales.append(("full", harmonic.wigner_inverse(coef, Lj, Nj).real))
+        else:
+            th = sampling.thetas(Lj)
+            scales.append(("rings", {t: harmonic.wigner_inverse_ring(coef, Lj, Nj, th[t]).real for t in (5, 400)}))
+    LP = filters.scaling_bandlimit(L, 2.0, J0)
+    Wp = harmonic.sht_inverse(wavelet.scaling_coefficients(flm, L, 2.0, J0, 0), LP, 0).real
+    return f, scales, Wp
+
+
+@pytest.mark.parametrize("mode", [SPLIT, BF16])
+def test_reduced_L512(lib, oracle_512, mode):
+    """The reduced modes at L = 512 (2L - 1 = 1023 samples per ring: the plain-float32 DFTs
+    re-seed their twiddle recurrence every 16 steps, so its error stays ~16 2^-24)."""
+    f, scales, Wp = oracle_512
+    L, N, J0 = 512, 4, 2
+    plan = lib.Plan(L, N, 2.0, J0, reality=True, batch=1, precision=mode)
+    wav, scal, f2 = plan.empty_wav(), plan.empty_scal(), plan.empty_map()
+    plan.forward(to_dev(f[None]), wav, scal)
+    plan.inverse(wav, scal, f2)
+    plan.check()
+    tol = TOLS_MAPS[mode]
+    assert plan.nscales == len(scales)
+    for s, (kind, ref) in enumerate(scales):
+        got = plan.scale_view(wav, s)[0].cpu().numpy()
+        if kind == "full":
+            assert rel(got, ref) < tol, s
+        else:
+            scale = max(np.abs(r).max() for r in ref.values())
+            for t, r in ref.items():
+                assert np.abs(got[:, t, :] - r).max() < tol * scale, (s, t)
+    assert rel(scal[0].cpu().numpy(), Wp) < tol
+    assert rel(f2[0].cpu().numpy(), f) < TOLS_ROUND_TRIP[mode]
     plan.close()
