@@ -294,7 +294,7 @@ s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
  * relative), not bit for bit. */
 s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f, void* stream);
 
-/* ---- m-sharded spin SHT (Sec. 4.4: one transform spread over several GPUs) ----------------
+/* ---- m-sharded spin SHT (Sec. 4.3: one transform spread over several GPUs) ----------------
  * The spin SHT factors into an l-contraction that is independent for every azimuthal frequency m
  * (the sum over l of Eq. 3 at fixed m; for the forward transform, Eq. 2, with the colatitude
  * quadrature of each m column, Sec. 3.2) and an azimuthal DFT that is independent for every
@@ -302,7 +302,8 @@ s2w_status s2w_sht_inverse_static(const s2w_plan* plan, const void* flm, void* f
  * R ranks can split one transform: rank r contracts its columns, the ranks exchange one block of
  * the column buffer each (an all-to-all: rank r sends the rows of rank q's rings and its own
  * columns to rank q), and rank r transforms its rings; the forward direction runs the same steps
- * in the opposite order.  The paper distributes its transforms the same way over the order m.
+ * in the opposite order.  The paper distributes its transforms over GPUs without naming the
+ * index it splits; the order m is the reading taken here.
  *
  * Column buffer cols: [batch][R(L)][Mc] complex float64 (R(L) = L rings on MW, 2L on DH; Mc = L
  * columns m = 0..L-1 for real maps, else 2L-1 columns m = -(L-1)..L-1), column c holding

@@ -21,7 +21,7 @@
 // every data column (batch, c, re|im) its exponent over the K nodes and its eight slices
 // ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm runs 36 digit-pair MMAs
 // per K step into eight exact float32 accumulators (a pair sums to <= 2^12 K <= 2^20, eight pairs
-// <= 2^23) through a three-stage bulk-copy pipeline, and the epilogue forms
+// <= 2^23) through a two-stage bulk-copy pipeline (two CTAs per SM), and the epilogue forms
 // 2^(e_row + f_col - 10) sum_q 2^(-7q) D_q in compensated float32, applies wo and writes or
 // accumulates.  Every mbarrier wait is bounded; a timeout sets the plan's error word.
 #include <cmath>
@@ -90,8 +90,8 @@ constexpr int kRBTile = kRN * 16;              // one data slice chunk
 constexpr int kRAChunk = kRSl * kRATile;
 constexpr int kRBChunk = kRSl * kRBTile;
 constexpr int kRStage = kRAChunk + kRBChunk;
-constexpr int kRStages = 3;
-constexpr size_t kRSmem = (size_t)kRStages * kRStage * sizeof(uint16_t);   // 122880 B
+constexpr int kRStages = 2;   // 80 KB: two CTAs (and 2 x 256 TMEM columns) per SM
+constexpr size_t kRSmem = (size_t)kRStages * kRStage * sizeof(uint16_t);   // 81920 B
 constexpr uint32_t kRWait = 1u << 20;
 
 struct RArgs {
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
 }
 
 // CTA (row tile, column group, map): thread 0 streams the K chunks (table and data slices) through
-// three stages and issues 36 MMAs per chunk into eight 128 x 32 accumulators; then every thread
+// two stages and issues 36 MMAs per chunk into eight 128 x 32 accumulators; then every thread
 // converts its row's 32 columns.
 __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
   const int nkc = a.nkc;
   bool ok = true;
   if (tid == 0) {
-    uint32_t ph_ld[kRStages] = {0u, 0u, 0u}, ph_mma[kRStages] = {0u, 0u, 0u};
+    uint32_t ph_ld[kRStages] = {}, ph_mma[kRStages] = {};
     unsigned pend_ld = 0u, pend_mma = 0u;
     const uint16_t* A = a.tab + (int64_t)rt * nkc * kRAChunk;
     const uint16_t* Bq = a.ops + gg * nkc * kRBChunk;

@@ -1,11 +1,12 @@
 """m-sharded spin SHT over torch.distributed ranks.
 
-The paper spreads one transform over several GPUs (Sec. 4.4) by splitting its work over the
-order m.  Here rank r of R owns a contiguous range of m columns of near-equal contraction work
-and a contiguous range of colatitude rings (s2w_shard_layout).  The inverse transform contracts
-the rank's columns over l for every ring (s2w_sht_inverse_columns), exchanges column blocks in
-one all-to-all (rank r sends rank q the rows of q's rings in r's columns) and takes the
-azimuthal DFT of the rank's rings (s2w_sht_inverse_rings).  The forward transform runs the
+The paper spreads its transforms over several GPUs (Sec. 4.3; timings on three GPUs in Sec. 4.4);
+here the work is split over the order m.  Rank r of R owns a contiguous range of m columns of
+near-equal contraction work and a contiguous range of colatitude rings (s2w_shard_layout).
+The inverse transform contracts the rank's columns over l for every ring
+(s2w_sht_inverse_columns), exchanges column blocks in one all-to-all (rank r sends rank q the
+rows of q's rings in r's columns) and takes the azimuthal DFT of the rank's rings
+(s2w_sht_inverse_rings).  The forward transform runs the
 same steps in the opposite order: DFT of the rank's rings, all-to-all, contraction with the
 colatitude quadrature of the rank's columns.
 
