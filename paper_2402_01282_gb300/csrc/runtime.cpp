@@ -96,8 +96,9 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
     c.Mc = P->real ? t->L : 2 * t->L - 1;
     c.mlo = P->real ? 0 : -(t->L - 1);
     const int64_t pix_sb = (int64_t)(2 * t->N - 1) * g.nr * (2 * t->L - 1);
-    // S2W_FP64_TC: every DFT form with tables for the transform is timed (prime-factor tensor-core
-    // kernel: fixed launch shape; direct tensor-core GEMM and compensated float32: each thread count)
+    // S2W_FP64_TC: every DFT form with tables for the transform is timed, each with every thread
+    // count (the block size of the per-ring kernels: the prime-factor form's prologues and
+    // synthesis, the direct form's prologues, the compensated kernels)
     for (int dir = 0; dir < 2; ++dir) {
       const bool fwd = dir == 0;
       int& form = fwd ? t->dft_form_fwd : t->dft_form_inv;
@@ -111,7 +112,6 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
       int pick_th = threads, pick_form = form;
       for (int fm : forms)
         for (int th : cand_threads) {
-          if (fm == kDftPfa && th != cand_threads[0]) continue;   // one launch shape
           threads = th;
           form = fm;
           const float ms = time_best(st, tm, 3, [&] {
