@@ -209,13 +209,15 @@ DIFF_L, DIFF_N, DIFF_J0, DIFF_B = 512, 4, 3, 8
 BALL_L, BALL_P, BALL_N = 128, 128, 4
 
 
-def run_ball(torch, s2w, stream, flush, steps, precision):
+def run_ball(torch, s2w, stream, flush, steps, precision, autotune=True):
     """Ball wavelet round trips per second (analysis + synthesis of one field, device time,
     L2 flushed) and the round-trip error."""
     import numpy as np
     import synth
     plan = s2w.BallWavPlan(BALL_L, BALL_N, BALL_P, 2.0, 2.0, 0, 0, batch=1, precision=PRECISIONS[precision],
                            precompute=PRECOMPUTE.get(precision, 0))
+    if autotune:
+        plan.autotune()
     bp = s2w.BallPlan(BALL_L, BALL_P, reality=True, batch=1)
     flmp = synth.flmp_random(BALL_L, BALL_P, synth.rng_for(5, 0), reality=True)[None, :, :, BALL_L - 1:]
     f = plan.empty_field()
@@ -249,7 +251,7 @@ def run_ball(torch, s2w, stream, flush, steps, precision):
                        "f_lmp ~ N(0, (l+1)^-2 (p+1)^-2)",
            "value": len(ms) / (sum(ms) * 1e-3), "unit": "ball transforms/s (fwd+inv)",
            "ms_per_step": mean_ms, "precision": precision, "max_rel_err": err,
-           "wavelet_coefficients_bytes": int(plan.wav_elems * 8),
+           "wavelet_coefficients_bytes": int(plan.wav_elems * 8), "autotuned": bool(autotune),
            "roofline": {"bound": "hbm", "algorithmic_bytes_per_step": int(alg), "achieved": achieved,
                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src}}
     plan.close()
@@ -555,12 +557,12 @@ def run_ours(args, world, rank, local):
                                  not args.no_autotune)
     ball = None
     if not args.no_ball:
-        ball = run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)
+        ball = run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision, not args.no_autotune)
         # the ball study's split-precision arm: reduced sphere contractions, radial maps on the
         # tensor cores
         ball["fp32_split"] = {k: v for k, v in run_ball(torch, s2w, stream, flush, max(3, args.steps // 2),
-                                                        "fp32_split").items() if k in ("value", "ms_per_step",
-                                                                                       "max_rel_err")}
+                                                        "fp32_split", not args.no_autotune).items()
+                              if k in ("value", "ms_per_step", "max_rel_err")}
 
     if rank != 0:
         if dist:
@@ -723,7 +725,8 @@ def main():
         globals().update(BALL_L=args.ball_only, BALL_P=args.ball_only)
         stream = torch.cuda.current_stream()
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-        print(json.dumps(run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision)), flush=True)
+        print(json.dumps(run_ball(torch, s2w, stream, flush, max(3, args.steps // 2), args.precision,
+                                  not args.no_autotune)), flush=True)
         return
     if args.maps != B:
         globals()["B"] = args.maps

@@ -275,6 +275,10 @@ s2w_status s2w_ball_inverse_adjoint(const s2w_ball_wav_plan* plan, const void* g
                                     void* stream);
 /* s2w_check of the plan's sphere transforms (synchronises, reads the device error word). */
 s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* plan);
+/* s2w_plan_autotune on the plan's sphere transforms (the batch of B P node maps): launch shapes
+ * and, in S2W_FP64_TC, the DFT form of each transform and direction.  Same contract as
+ * s2w_plan_autotune (synchronises, overwrites the workspaces); the paper has no counterpart. */
+s2w_status s2w_ball_wav_plan_autotune(s2w_ball_wav_plan* plan, void* stream);
 
 /* The inverse spin SHT of s2w_sht_inverse, for callers that cannot allocate device memory
  * when they need it (a host application that owns every device allocation and forbids new

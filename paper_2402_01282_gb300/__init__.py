@@ -34,7 +34,8 @@ EXPORTS = ["s2w_plan_create", "s2w_plan_destroy", "s2w_query_layout", "s2w_forwa
            "s2w_ball_wav_check", "s2w_plan_autotune", "s2w_plan_launch_shapes", "s2w_plan_dft_forms", "s2w_batch_create",
            "s2w_batch_launch", "s2w_batch_destroy", "s2w_plan_device_bytes",
            "s2w_plan_inject_timeout", "s2w_plan_set_dft_forms", "s2w_shard_layout", "s2w_sht_inverse_columns",
-           "s2w_sht_inverse_rings", "s2w_sht_forward_rings", "s2w_sht_forward_columns"]
+           "s2w_sht_inverse_rings", "s2w_sht_forward_rings", "s2w_sht_forward_columns",
+           "s2w_ball_wav_plan_autotune"]
 KERNEL_KINDS = 5
 
 
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
     for name in ("s2w_ball_forward", "s2w_ball_inverse", "s2w_ball_forward_adjoint", "s2w_ball_inverse_adjoint"):
         getattr(lib, name).argtypes = [vp, vp, vp, vp, vp]
     lib.s2w_ball_wav_check.argtypes = [vp]
+    lib.s2w_ball_wav_plan_autotune.argtypes = [vp, vp]
     lib.s2w_plan_autotune.argtypes = [vp, vp]
     lib.s2w_plan_launch_shapes.argtypes = [vp, ctypes.c_int, ip, ip, ip]
     lib.s2w_plan_dft_forms.argtypes = [vp, ctypes.c_int, ip, ip]
@@ -594,6 +596,10 @@ class BallWavPlan:
 
     def check(self):
         _check(_lib.s2w_ball_wav_check(self._h))
+
+    def autotune(self, stream=None):
+        """s2w_ball_wav_plan_autotune: launch shapes and DFT forms of the sphere transforms."""
+        _check(_lib.s2w_ball_wav_plan_autotune(self._h, _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -449,4 +449,9 @@ s2w_status s2w_ball_wav_check(const s2w_ball_wav_plan* W) {
   return s2w_check(W->sph);
 }
 
+s2w_status s2w_ball_wav_plan_autotune(s2w_ball_wav_plan* W, void* stream) {
+  if (W == nullptr) return record_error(S2W_EINVAL, "plan is NULL");
+  return s2w_plan_autotune(W->sph, stream);
+}
+
 }  // extern "C"

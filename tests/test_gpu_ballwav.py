@@ -137,12 +137,14 @@ def test_ball_adjoints(lib, L, N, P, nu, J0, J0r, B, mode):
         assert abs(lhs - inner(x[b], fs)) < TOL * np.linalg.norm(x[b]) * (np.linalg.norm(gw) + np.linalg.norm(gs)) * 10
 
 
-@pytest.mark.parametrize("mode", [0, 4])   # S2W_FP64, and S2W_FP64_TC (the ball study's mode)
-def test_ball_full_size_config(lib, mode):
+@pytest.mark.parametrize("mode,tune", [(0, False), (4, False), (4, True)])   # S2W_FP64; S2W_FP64_TC (the
+def test_ball_full_size_config(lib, mode, tune):                             # study's mode), also autotuned
     """L = P = 128, N = 4, lambda = nu = 2, J0 = J0' = 0, one real field."""
     import torch
     L, N, P, lam, nu = 128, 4, 128, 2.0, 2.0
     plan = lib.BallWavPlan(L, N, P, lam, nu, 0, 0, batch=1, precision=mode)
+    if tune:
+        plan.autotune()   # the sphere transforms' launch shapes and DFT forms, as the bench runs them
     _, _, K = laguerre.quadrature(P)
     pq = [1, 5, 37, 127]   # p = 1 reaches the lowest radial scale (kappa^0(1) = 1)
     a = [synth.flm_random(L, synth.rng_for(5, q), reality=True) for q in range(len(pq))]
