@@ -161,8 +161,10 @@ __device__ __forceinline__ void store_pass_slices(const PArgs& a, int pass, int 
 // ------------------------------------------------------------------ forward prologue
 // Block (ring t, map b).  H_q(alpha) = sum_g W(alpha, gamma_g) exp(-i n_q gamma_g) for every job q,
 // the ring exponent, then the slices of the ring's columns (job q, p1, re|im) over p2.
+// (64 registers for real maps: four 256-thread blocks per SM instead of three; the complex
+// variant keeps its 128)
 template <bool REAL>
-__global__ void k_dftp_fwd_prep(PArgs a) {
+__global__ void __launch_bounds__(512, REAL ? 2 : 1) k_dftp_fwd_prep(PArgs a) {
   extern __shared__ float4 HZ[];   // [nj][n]
   __shared__ int jn[kMaxJobs], jp[kMaxJobs], njs, emax;
   const int n = a.n, t = blockIdx.x, b = blockIdx.y;
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
 // Block (ring t, map b): W(alpha, gamma_g) = sum_q Z_q(alpha) exp(+i n_q gamma_g) (real maps: the
 // n, -n pair contributes 2 Re, n = 0 Re), scaled by the ring's exponent.
 template <bool REAL>
-__global__ void k_dftp_synth(PArgs a) {
+__global__ void __launch_bounds__(512, 2) k_dftp_synth(PArgs a) {
   extern __shared__ float4 Zs[];   // [nj][n]
   __shared__ int jn[kMaxJobs], jp[kMaxJobs], njs;
   __shared__ float4 Ph[kJobChunk * kPMaxNg];
