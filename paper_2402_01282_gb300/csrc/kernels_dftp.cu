@@ -528,14 +528,24 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
         dft_small<N1, FWD ? -1 : 1>(yr, yi, a.tw1, xr, xi);
         if (FWD) {
           const int ke = a.e_tw + a.fexp[rf] - 10;
-          double2* const o = reinterpret_cast<double2*>(OUT) + (size_t)sl * n;
+          double2* const o = reinterpret_cast<double2*>(OUT) + (size_t)sl * (n + 1);
 #pragma unroll
           for (int k1 = 0; k1 < N1; ++k1) {
             const int k = ka[k1] + kb >= n ? ka[k1] + kb - n : ka[k1] + kb;
-            o[k] = make_double2(pair_dbl(xr[k1], ke), pair_dbl(xi[k1], ke));
+            const double2 v = make_double2(pair_dbl(xr[k1], ke), pair_dbl(xi[k1], ke));
+            if (REAL) {
+              // staged as the two columns the write-out copies whole: A[m] = X(m), m <= h
+              // (column n) and B[m] = conj X((n - m) mod n), m <= h (column -n), at o[0..h] and
+              // o[h+1 .. 2h+1]
+              if (k <= h) o[k] = v;
+              if (k == 0 || k > h) o[h + 1 + (k == 0 ? 0 : n - k)] = make_double2(v.x, -v.y);
+            } else {
+              const int mm = k + h >= n ? k + h - n : k + h;   // m = k or k - n, stored at m + h
+              o[mm] = v;
+            }
           }
         } else {
-          float4* const o = reinterpret_cast<float4*>(OUT) + (size_t)sl * n;
+          float4* const o = reinterpret_cast<float4*>(OUT) + (size_t)sl * (n + 1);
 #pragma unroll
           for (int k1 = 0; k1 < N1; ++k1) {
             const int k = ka[k1] + kb >= n ? ka[k1] + kb - n : ka[k1] + kb;
@@ -551,6 +561,7 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
       // after a barrier from flags written before it
       const bool okw = warp_wait(&acc_full, (uint32_t)(i & 1));
       if (lane == 0 && !okw) t_abort = 1;
+      if (tt == 0) tc::bulk_wait_read0();   // the previous pass's copies have read OUT
       asm volatile("bar.sync 1, %0;" ::"n"(kPTmemWarps * 32) : "memory");
       if (t_abort) break;
       tc::fence_after_sync();
@@ -561,36 +572,37 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_empty);
       if (warp_live) stage_b(gp, chunk, acc);
+      tc::fence_proxy_async();   // this thread's OUT writes before the copies' async-proxy reads
       asm volatile("bar.sync 1, %0;" ::"n"(kPTmemWarps * 32) : "memory");
-      // coalesced write-out of the pass's staged outputs
-      for (int sl = 0; sl < rpp * nj; ++sl) {
-        const int rip = sl / nj, q = sl - rip * nj, rf = gp * rpp + rip;
-        if (rf >= rings) break;
-        const int bb = rf / a.nr, t = rf - bb * a.nr;
-        if (FWD) {
-          const double2* o = reinterpret_cast<const double2*>(OUT) + (size_t)sl * n;
-          double2* Gn = a.Gout + (((int64_t)bb * a.nact + jn[q]) * a.nr + t) * Mc;
-          if (REAL) {
-            // G_{m, n} = X(m), m <= h; G_{m, -n} = conj X((n - m) mod n), m <= h
-            double2* Gp = jp[q] >= 0 ? a.Gout + (((int64_t)bb * a.nact + jp[q]) * a.nr + t) * Mc : nullptr;
-            for (int m = tt; m <= h; m += kPTmemWarps * 32) {
-              Gn[m] = o[m];
-              if (Gp != nullptr) {
-                const double2 x = o[m == 0 ? 0 : n - m];
-                Gp[m] = make_double2(x.x, -x.y);
-              }
+      // the pass's staged outputs to global memory as bulk copies of whole columns, issued by one
+      // thread while the others go on to the next pass; that pass rewrites OUT only after these
+      // copies have read it (the wait at its top, before its first barrier)
+      if (tt == 0) {
+        for (int sl = 0; sl < rpp * nj; ++sl) {
+          const int rip = sl / nj, q = sl - rip * nj, rf = gp * rpp + rip;
+          if (rf >= rings) break;
+          const int bb = rf / a.nr, t = rf - bb * a.nr;
+          if (FWD) {
+            const double2* o = reinterpret_cast<const double2*>(OUT) + (size_t)sl * (n + 1);
+            double2* Gn = a.Gout + (((int64_t)bb * a.nact + jn[q]) * a.nr + t) * Mc;
+            if (REAL) {
+              // G_{m, n} = X(m) and G_{m, -n} = conj X((n - m) mod n), m <= h
+              tc::bulk_s2g(Gn, o, (uint32_t)(h + 1) * 16u);
+              if (jp[q] >= 0)
+                tc::bulk_s2g(a.Gout + (((int64_t)bb * a.nact + jp[q]) * a.nr + t) * Mc, o + h + 1,
+                             (uint32_t)(h + 1) * 16u);
+            } else {
+              tc::bulk_s2g(Gn, o, (uint32_t)n * 16u);   // m = -h .. h at m + h
             }
           } else {
-            for (int m = -h + tt; m <= h; m += kPTmemWarps * 32) Gn[m - a.mlo] = o[m < 0 ? m + n : m];
+            tc::bulk_s2g(a.zbuf + ((int64_t)rf * nj + q) * n,
+                         reinterpret_cast<const float4*>(OUT) + (size_t)sl * (n + 1), (uint32_t)n * 16u);
           }
-        } else {
-          const float4* o = reinterpret_cast<const float4*>(OUT) + (size_t)sl * n;
-          float4* z = a.zbuf + ((int64_t)rf * nj + q) * n;
-          for (int al = tt; al < n; al += kPTmemWarps * 32) z[al] = o[al];
         }
+        tc::bulk_commit();
       }
-      asm volatile("bar.sync 1, %0;" ::"n"(kPTmemWarps * 32) : "memory");   // OUT is reused by the next pass
     }
+    if (tt == 0) tc::bulk_wait_read0();   // OUT stays allocated until the last copies have read it
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -692,7 +704,7 @@ size_t tc_smem_bytes(int n, int n1, int nj) {
   const int n2 = n / n1, Rs = ((n2 + 1 + 7) / 8) * 8, nkc = (n2 + 15) / 16;
   const int rpp = (kPN / slot_width(n1)) / nj;
   const size_t abytes = (size_t)nkc * kSl * Rs * 32, boff = (abytes + 1023) & ~(size_t)1023;
-  return boff + (size_t)kPStages * kPChunk * 2 + (size_t)rpp * nj * n * 16;
+  return boff + (size_t)kPStages * kPChunk * 2 + (size_t)rpp * nj * (n + 1) * 16;   // OUT: n + 1 per slot
 }
 
 int num_sms() {

@@ -99,6 +99,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // 32 lanes x 32 consecutive float32 columns of TMEM into registers (one warp, its lane quarter).
+// Bulk copy shared -> global through the async proxy, tracked by bulk groups (both addresses
+// 16-byte aligned, bytes a multiple of 16).  The generic-proxy writes of the source must be
+// ordered before it by fence_proxy_async in the writing threads and a barrier.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed bulk group has finished reading its shared-memory source (the buffer may be
+// rewritten); a hardware wait on copies this thread issued, which always complete
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
