@@ -471,13 +471,15 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
     int ka[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) ka[k1] = (int)(((int64_t)k1 * a.e1) % n);
-    auto warp_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
-      int ok = 1;
-      if (lane == 0) {
-        if (s_abort) ok = 0;
-        else if (!tc::mbar_wait_backoff(bar, parity, kPWait)) ok = 0, on_timeout();
+    // one thread polls (a plain bounded try-wait: nothing else polls, so it need not back off);
+    // the named barrier after it releases the other TMEM warps
+    auto poll_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+      if (s_abort) return false;
+      if (!tc::mbar_wait(bar, parity, kPWait)) {
+        on_timeout();
+        return false;
       }
-      return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+      return true;
     };
     // the seven accumulators of one 16-column chunk, smallest weight first: two halves of 8
     // columns, each with its 7 loads in flight before one wait
@@ -559,9 +561,10 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
       const int gp = (int)blockIdx.x + i * G;
       // the TMEM warps meet at named barriers below: one abort decision for all of them, taken
       // after a barrier from flags written before it
-      const bool okw = warp_wait(&acc_full, (uint32_t)(i & 1));
-      if (lane == 0 && !okw) t_abort = 1;
-      if (tt == 0) tc::bulk_wait_read0();   // the previous pass's copies have read OUT
+      if (tt == 0) {
+        if (!poll_wait(&acc_full, (uint32_t)(i & 1))) t_abort = 1;
+        tc::bulk_wait_read0();   // the previous pass's copies have read OUT
+      }
       asm volatile("bar.sync 1, %0;" ::"n"(kPTmemWarps * 32) : "memory");
       if (t_abort) break;
       tc::fence_after_sync();
