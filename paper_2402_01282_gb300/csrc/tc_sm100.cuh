@@ -154,23 +154,5 @@ __device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[8]) {
   asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
 }
 
-// Bounded wait with exponential nanosleep back-off between polls (for roles whose waits are long
-// and whose polling would take issue slots from the warps doing the work).
-__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* mbar, uint32_t parity, uint32_t max_iter) {
-  uint32_t ns = 32;
-  for (uint32_t it = 0; it < max_iter; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
-  }
-  return false;
-}
-
 }  // namespace tc
 }  // namespace s2w
