@@ -80,7 +80,7 @@ struct XArgs {
   int e_tw;                 // table row exponent
   uint32_t idesc;
   int* err;
-  int ndiag;   // digit-pair diagonals summed: 7 (28 MMAs per K step) or 8 (34)
+  int ndiag;   // digit-pair diagonals summed: 7 (28 pairs per K step) or 8 (34)
 };
 
 // 8 consecutive values (index pairs p0 .. p0+7) of one column -> one 16-byte core-matrix row per
@@ -369,16 +369,21 @@ __global__ void __launch_bounds__(kXT) k_dftx_gemm(XArgs a) {
       tc::fence_after_sync();
       const uint32_t A0 = tc::smem_u32(stage0 + s * kXStage), B0 = A0 + kXAChunk * 2u;
       // the slice operands of a stage differ only in their start address: descriptors by offset
-      // (address field = byte address / 16), all 28 (34) MMAs unrolled
+      // (address field = byte address / 16)
       const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
       const uint32_t acc0 = c > 0 ? 1u : 0u;
+      // one MMA per twiddle slice sa against the data slices 0 .. 6 - sa side by side (contiguous
+      // 32-row blocks: one N = 32 (7 - sa) operand), pair (sa, sb) into accumulator sa + sb at
+      // TMEM columns 32 (sa + sb); diagonal 7 as in kernels_tcx.cu (pair (1, 6) first, alone)
+      const bool d7 = a.ndiag > kSl;   // uniform
 #pragma unroll
-      for (int qq = 0; qq < kDiag; ++qq) {
-        if (qq >= a.ndiag) break;   // uniform
-#pragma unroll
-        for (int sa = diag_lo(qq); sa <= diag_hi(qq); ++sa)
-          tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kXATile * 2 / 16)),
-                      dB + (uint64_t)((qq - sa) * (kXBTile * 2 / 16)), a.idesc, sa > diag_lo(qq) ? 1u : acc0);
+      for (int sa = 0; sa < kSl; ++sa) {
+        const uint64_t dAs = dA + (uint64_t)(sa * (kXATile * 2 / 16));
+        if (d7 && sa == 1)
+          tc::mma_f16(tmem + (uint32_t)(32 * kSl), dAs, dB + (uint64_t)((kSl - 1) * (kXBTile * 2 / 16)),
+                      tc::make_idesc(128, kXN, 1, 0, 0), acc0);
+        const int nb = kSl - sa + ((d7 && sa >= 2) ? 1 : 0);
+        tc::mma_f16(tmem + (uint32_t)(32 * sa), dAs, dB, tc::make_idesc(128, kXN * nb, 1, 0, 0), sa > 0 ? 1u : acc0);
       }
       tc::mma_commit(&bar_mma[s]);
       pend_mma |= 1u << s;

@@ -19,8 +19,9 @@
 // R D is sliced once at plan time (one exponent per row, eight bf16 digits of a 54-bit fixed-point
 // value, [row tile][K chunk][slice][128 x 16] core-matrix tiles); per call, k_radx_prep gives
 // every data column (batch, c, re|im) its exponent over the K nodes and its eight slices
-// ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm runs 36 digit-pair MMAs
-// per K step into eight exact float32 accumulators (a pair sums to <= 2^12 K <= 2^20, eight pairs
+// ([column group of 16 complex][K chunk][slice][32 x 16]); k_radx_gemm sums the 36 digit pairs
+// of a K step with eight MMAs (one per table slice, N = 256 .. 32 over the data slices side by
+// side) into eight exact float32 accumulators (a pair sums to <= 2^12 K <= 2^20, eight pairs
 // <= 2^23) through a two-stage bulk-copy pipeline (two CTAs per SM), and the epilogue forms
 // 2^(e_row + f_col - 10) sum_q 2^(-7q) D_q in compensated float32, applies wo and writes or
 // accumulates.  Every mbarrier wait is bounded; a timeout sets the plan's error word.
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(128) k_radx_prep(RArgs a) {
 }
 
 // CTA (row tile, column group, map): thread 0 streams the K chunks (table and data slices) through
-// two stages and issues 36 MMAs per chunk into eight 128 x 32 accumulators; then every thread
+// two stages and issues eight MMAs (the 36 digit pairs) per chunk into eight 128 x 32 accumulators;
+// then every thread
 // converts its row's 32 columns.
 __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -236,12 +238,13 @@ __global__ void __launch_bounds__(kRT) k_radx_gemm(RArgs a) {
       tc::fence_after_sync();
       const uint32_t A0 = tc::smem_u32(stage0 + s * kRStage), B0 = A0 + kRAChunk * 2u;
       const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
+      // one MMA per table slice sa against the data slices 0 .. 7 - sa side by side (contiguous
+      // 32-row blocks: one N = 32 (8 - sa) operand), pair (sa, sb) into accumulator sa + sb at TMEM
+      // columns 32 (sa + sb): eight MMAs per K chunk for the 36 digit pairs
 #pragma unroll
-      for (int qq = 0; qq < kRSl; ++qq)
-#pragma unroll
-        for (int sa = 0; sa <= qq; ++sa)
-          tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kRATile * 2 / 16)),
-                      dB + (uint64_t)((qq - sa) * (kRBTile * 2 / 16)), a.idesc, (c > 0 || sa > 0) ? 1u : 0u);
+      for (int sa = 0; sa < kRSl; ++sa)
+        tc::mma_f16(tmem + (uint32_t)(32 * sa), dA + (uint64_t)(sa * (kRATile * 2 / 16)), dB,
+                    tc::make_idesc(128, kRN * (kRSl - sa), 1, 0, 0), (c > 0 || sa > 0) ? 1u : 0u);
       tc::mma_commit(&bar_mma[s]);
       pend_mma |= 1u << s;
       if (c + kRStages - 1 < nkc) {

@@ -30,8 +30,9 @@
 //          ((t nkc + c) 7 + s) 2048 + ((r/8) 2 + k/8) 64 + (r%8) 8 + k%8
 //   data   (chunk c, slice s): element (j, k) at (c 7 + s) 512 + ((j/8) 2 + k/8) 64 + (j%8) 8 + k%8
 // k_tcx_gemm: one CTA of 128 threads per (row tile, m, n); thread 0 drives a three-stage
-// pipeline of bulk copies (35 KB per stage: 7 table slices + 7 data slices) and 28 (or 34) MMAs
-// per chunk; 105 KB of shared memory and 256 TMEM columns per CTA let two CTAs share an SM; every
+// pipeline of bulk copies (35 KB per stage: 7 table slices + 7 data slices) and seven MMAs per
+// chunk (one per table slice, N = 224 .. 32 over the data slices side by side: the 28 pairs; 8
+// MMAs for the 34 with diagonal 7); 105 KB of shared memory and 256 TMEM columns per CTA let two CTAs share an SM; every
 // mbarrier wait is bounded and a timeout sets the plan's error word.
 #include "comp32.cuh"
 #include "s2w_internal.h"
@@ -292,7 +293,7 @@ struct GemmArgs {
   uint32_t idesc;
   int* err;
   int inject_timeout;       // test hook (s2w_plan_inject_timeout): make a bounded wait run out
-  int ndiag;                // digit-pair diagonals summed: 7 (28 MMAs per K step) or 8 (34)
+  int ndiag;                // digit-pair diagonals summed: 7 (28 pairs per K step) or 8 (34)
 };
 
 template <bool FWD>
@@ -373,16 +374,24 @@ __global__ void __launch_bounds__(kThreads) k_tcx_gemm(GemmArgs a) {
         tc::fence_after_sync();
         const uint32_t A0 = tc::smem_u32(stage0 + s * kStageElems), B0 = A0 + kAChunk * 2u;
         // the slice operands of a stage differ only in their start address: descriptors by
-        // offset (address field = byte address / 16), all 28 (34) MMAs unrolled
+        // offset (address field = byte address / 16)
         const uint64_t dA = tc::make_sdesc(A0, 128, 256), dB = tc::make_sdesc(B0, 128, 256);
         const uint32_t acc0 = c > 0 ? 1u : 0u;
+        // One MMA per table slice sa against the data slices 0 .. 6 - sa side by side: the data
+        // slices of a chunk are contiguous 32-row blocks with one row-group stride, so they form one
+        // N = 32 (7 - sa) operand, and pair (sa, sb) lands in accumulator sa + sb at TMEM columns
+        // 32 (sa + sb).  Seven MMAs per K chunk read each table slice once (the 28 pairs, exactly).
+        // Diagonal 7 (ndiag = 8): slices sa >= 2 take one more data slice (7 - sa); pair (1, 6)
+        // goes first, alone, so that it initialises accumulator 7 at the first chunk.
+        const bool d7 = a.ndiag > kSl;   // uniform
 #pragma unroll
-        for (int qq = 0; qq < kDiag; ++qq) {
-          if (qq >= a.ndiag) break;   // uniform
-#pragma unroll
-          for (int sa = diag_lo(qq); sa <= diag_hi(qq); ++sa)
-            tc::mma_f16(tmem + (uint32_t)(32 * qq), dA + (uint64_t)(sa * (kATile * 2 / 16)),
-                        dB + (uint64_t)((qq - sa) * (kBTile * 2 / 16)), a.idesc, sa > diag_lo(qq) ? 1u : acc0);
+        for (int sa = 0; sa < kSl; ++sa) {
+          const uint64_t dAs = dA + (uint64_t)(sa * (kATile * 2 / 16));
+          if (d7 && sa == 1)
+            tc::mma_f16(tmem + (uint32_t)(32 * kSl), dAs, dB + (uint64_t)((kSl - 1) * (kBTile * 2 / 16)),
+                        tc::make_idesc(128, kN, 1, 0, 0), acc0);
+          const int nb = kSl - sa + ((d7 && sa >= 2) ? 1 : 0);
+          tc::mma_f16(tmem + (uint32_t)(32 * sa), dAs, dB, tc::make_idesc(128, kN * nb, 1, 0, 0), sa > 0 ? 1u : acc0);
         }
         tc::mma_commit(&bar_mma[s]);
         pend_mma |= 1u << s;

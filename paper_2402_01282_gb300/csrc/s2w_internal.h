@@ -225,8 +225,8 @@ struct s2w_plan {
   int64_t g_ws_elems = 0;
   int* err_word = nullptr;             // device error word
   int inject_timeout = 0;              // test hook: tensor-core contraction waits run out (s2w_plan_inject_timeout)
-  // S2W_FP64_TC: the sliced GEMMs also sum the digit-pair diagonal 7 (34 MMAs per K step instead
-  // of 28, ~2^-47 instead of ~2^-44 of a term): the contractions and the direct-form DFTs; such
+  // S2W_FP64_TC: the sliced GEMMs also sum the digit-pair diagonal 7 (34 digit pairs per K step
+  // instead of 28, ~2^-47 instead of ~2^-44 of a term): the contractions and the direct-form DFTs; such
   // plans do not use the prime-factor DFT kernel (diagonals 0..6 only).  Set for the sphere plans
   // inside the ball plans, whose radial maps amplify the sphere transforms' error about a
   // hundredfold.

@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kSl = 7;   // slices per value
 // Digit-pair diagonals i + j = 0 .. 6 of a product of two sliced values are always summed (28
-// MMAs per K step); diagonal 7 (six more) when the plan asks for it.  The pairs of diagonal 7
+// pairs per K step); diagonal 7 (six more) when the plan asks for it.  The pairs of diagonal 7
 // weigh up to ~2^-44 of a term, above the operands' own 47-bit rounding; diagonals 8 and up stay
 // below 2^-51.  Accumulator q of diagonal q is exact either way.
 constexpr int kDiag = kSl + 1;
