@@ -18,10 +18,11 @@
 //
 // Exactness of the GEMM: the table (scale s < 2^e_tw) and the data (one exponent f per ring,
 // max |x| < 2^f) are rounded to 47-bit fixed point and cut into seven balanced base-128 digits;
-// the 28 digit-pair MMAs with i + i' = q <= 6 of a K step go to accumulator q (seven 128 x 64
-// float32 accumulators in TMEM), whose partial sums are integers below 2^24 (K <= 128), so every
-// accumulator is exact (plans that also sum the diagonal i + i' = 7 use the direct form); C = 2^(e_tw + f - 10) sum_q 2^(-7q) D_q, summed smallest weight first in
-// compensated float32.
+// the 28 digit pairs with i + i' = q <= 6 of a K step (10 MMAs: one per table slice and group of
+// up to four data slices side by side) go to accumulator q (seven 128 x 64 float32 accumulators
+// in TMEM), whose partial sums are integers below 2^24 (K <= 128), so every accumulator is exact
+// (plans that also sum the diagonal i + i' = 7 use the direct form);
+// C = 2^(e_tw + f - 10) sum_q 2^(-7q) D_q, summed smallest weight first in compensated float32.
 //
 // GEMM columns come in passes of 64: slots of W = 2 n1 rounded up to a power of two columns
 // (one ring and job each: p1 < n1, re|im), S = 64/W slots, rpp = S/nj rings per pass.  Per call:
@@ -428,13 +429,19 @@ __global__ void __launch_bounds__(kPT, 1) k_dftp_tc(PArgs a) {
         if (!ok) break;
         tc::fence_after_sync();
         const uint32_t ab = A0 + (uint32_t)(c * kSl) * atile, bb = tc::smem_u32(Bs + s * kPChunk);
+        // one MMA per table slice sa and group of at most four data slices side by side (the 64-row
+        // slices are contiguous with one row-group stride: N = 64 x group size <= 256); pair
+        // (sa, sb) lands in accumulator sa + sb at TMEM columns 64 (sa + sb): 10 MMAs per K chunk
+        // for the 28 pairs, each table slice read once or twice
 #pragma unroll
-        for (int qq = 0; qq < kSl; ++qq)
+        for (int sa = 0; sa < kSl; ++sa)
 #pragma unroll
-          for (int sa = 0; sa <= qq; ++sa)
-            tc::mma_f16(tmem + (uint32_t)(64 * qq), tc::make_sdesc(ab + (uint32_t)sa * atile, 128, 256),
-                        tc::make_sdesc(bb + (uint32_t)(qq - sa) * btile, 128, 256), a.idesc,
+          for (int g0 = 0; g0 < kSl - sa; g0 += 4) {
+            const int gn = (kSl - sa - g0) < 4 ? (kSl - sa - g0) : 4;
+            tc::mma_f16(tmem + (uint32_t)(64 * (sa + g0)), tc::make_sdesc(ab + (uint32_t)sa * atile, 128, 256),
+                        tc::make_sdesc(bb + (uint32_t)g0 * btile, 128, 256), tc::make_idesc(128, kPN * gn, 1, 0, 0),
                         (c > 0 || sa > 0) ? 1u : 0u);
+          }
         tc::mma_commit(&freeb[s]);
         mma = gc + 1;
         if (c == nkc - 1) tc::mma_commit(&acc_full);
