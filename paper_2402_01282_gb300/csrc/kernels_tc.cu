@@ -230,7 +230,7 @@ struct GemmArgs {
   double2* out;           // forward output (accumulated)
   int64_t s_b, s_n, s_l;
   int mlo_out;
-  uint32_t idesc;
+  uint32_t idesc, idesc2;   // N = 32 and N = 64 (the operand's hi and lo tiles side by side)
   int* err;
 };
 
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
       tc::mbar_init(&bar_mma[s], 1);
     }
   }
-  if (warp == 0) tc::tmem_alloc(&tbase, 32);
+  if (warp == 0) tc::tmem_alloc(&tbase, 64);   // hi*hi + lo*hi at columns 0..31, hi*lo at 32..63
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -304,8 +304,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
         for (int ks = 0; ks < kKc / 16; ++ks) {
           const uint32_t o = (uint32_t)ks * 256u;
           const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-          tc::mma_f16(tmem, tc::make_sdesc(A0 + o, 128, 1024), tc::make_sdesc(B0 + o, 128, 1024), a.idesc, acc);
-          tc::mma_f16(tmem, tc::make_sdesc(A0 + o, 128, 1024), tc::make_sdesc(B1 + o, 128, 1024), a.idesc, 1);
+          // the operand's hi and lo tiles are adjacent 32-row blocks with one row-group stride: one
+          // N = 64 MMA of the table's hi against both (hi*hi into columns 0..31, hi*lo into 32..63),
+          // then lo*hi into columns 0..31; the epilogue adds the two halves
+          tc::mma_f16(tmem, tc::make_sdesc(A0 + o, 128, 1024), tc::make_sdesc(B0 + o, 128, 1024), a.idesc2, acc);
           tc::mma_f16(tmem, tc::make_sdesc(A1 + o, 128, 1024), tc::make_sdesc(B0 + o, 128, 1024), a.idesc, 1);
         }
         tc::mma_commit(&bar_mma[s]);
@@ -321,8 +323,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
     ok = __syncthreads_and(ok);
     if (!ok) break;
     tc::fence_after_sync();
-    float v[32];
+    float v[32], w[32];
     tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, w);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] += w[j];
     const float sc = a.scale[(int64_t)q * a.Mc * a.nact + idx];
     const float un = 1.f / (sc * (float)(FWD ? kFwdScale : kInvScale));   // a power of two
     const int row = rt * 128 + warp * 32 + lane;
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 constexpr size_t kGemmSmem = 2 * (2 * kTileElems + 2 * kOpElems) * sizeof(uint16_t);   // 80 KB
@@ -395,6 +400,7 @@ GemmArgs gemm_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab
   a.mlo = mlo;
   a.B = B;
   a.idesc = tc::make_idesc(128, kTcN, fp16 ? 0 : 1, 0, 0);
+  a.idesc2 = tc::make_idesc(128, 2 * kTcN, fp16 ? 0 : 1, 0, 0);
   a.err = P->err_word;
   return a;
 }
