@@ -68,7 +68,8 @@ typedef enum {
  *                  precomputed Wigner-d tables stored as fp16 hi + lo pairs, data as fp16
  *                  pairs, float32 accumulation (1e-5 target); plain float32 DFTs there.
  * S2W_BF16         split-bf16: the same with bf16 hi + lo pairs for the tables and the data
- *                  (three MMAs per K step, float32 accumulation; 1e-3 target).
+ *                  (the products hi*hi, hi*lo, lo*hi per K step, float32 accumulation; 1e-3
+ *                  target).
  *                  Both reduced modes keep the spin SHT Y, Y^-1 float64-accurate and
  *                  support L and the ring count <= 512 (S2W_EUNSUPPORTED above).
  * S2W_FP64_TC      float64 accuracy (1e-11 target) with every l-contraction on the tensor cores:
