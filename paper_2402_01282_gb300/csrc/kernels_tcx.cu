@@ -180,7 +180,7 @@ __device__ __forceinline__ double2 prep_pair(const PrepArgs& a, int mi, int ni, 
 //           consecutive k of one column form one 16-byte row of a core matrix (one vector store
 //           per slice).
 constexpr int kPrepM = 8;
-constexpr int kPrepK = 32;   // reduction indices per block (two or more waves of blocks at the top scales)
+constexpr int kPrepK = 16;   // reduction indices per block (two or more waves of blocks at the top scales)
 
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_tcxe(PrepArgs a, int ks_n) {
