@@ -528,6 +528,7 @@ cudaError_t launch(K kern, dim3 grid, size_t smem, cudaStream_t st, const DftcAr
 
 cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, const void* pix, int64_t pix_sb,
                                 bool real, ColumnArgs c, cudaStream_t st, bool plain) {
+  if (plain && dftf_usable(g, t, real, true)) return launch_dftf_forward(g, t, pix, pix_sb, real, c, st);
   DftcArgs a = make_args(g, t, c);
   a.pix_in = pix;
   a.pix_out = nullptr;
@@ -549,6 +550,7 @@ cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, con
 
 cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, ColumnArgs c, void* pix,
                                 int64_t pix_sb, bool real, cudaStream_t st, bool plain) {
+  if (plain && dftf_usable(g, t, real, false)) return launch_dftf_inverse(g, t, c, pix, pix_sb, real, st);
   DftcArgs a = make_args(g, t, c);
   a.pix_in = nullptr;
   a.pix_out = pix;

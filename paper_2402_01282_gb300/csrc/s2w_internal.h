@@ -374,5 +374,12 @@ cudaError_t launch_dftc_forward(const GridTables& g, const TransformSpec& t, con
                                 bool real, ColumnArgs c, cudaStream_t st, bool plain = false);
 cudaError_t launch_dftc_inverse(const GridTables& g, const TransformSpec& t, ColumnArgs c, void* pix,
                                 int64_t pix_sb, bool real, cudaStream_t st, bool plain = false);
+// The plain-float32 DFTs of the reduced-precision modes (kernels_dftf.cu): usable when the
+// shape fits their shared-memory layout; launch_dftc_* take them for plain = true.
+bool dftf_usable(const GridTables& g, const TransformSpec& t, bool real, bool fwd);
+cudaError_t launch_dftf_forward(const GridTables& g, const TransformSpec& t, const void* pix, int64_t pix_sb,
+                                bool real, ColumnArgs c, cudaStream_t st);
+cudaError_t launch_dftf_inverse(const GridTables& g, const TransformSpec& t, ColumnArgs c, void* pix,
+                                int64_t pix_sb, bool real, cudaStream_t st);
 
 }  // namespace s2w

@@ -52,7 +52,8 @@ def test_sht_reduced(lib, L, spin, real, B, mode):
 
 
 @pytest.mark.parametrize("mode", [SPLIT, BF16])
-@pytest.mark.parametrize("L,N,lam,J0,spin,real,B", [(32, 4, 2.0, 0, 0, True, 1), (16, 3, 2.0, 1, 2, False, 2)])
+@pytest.mark.parametrize("L,N,lam,J0,spin,real,B", [(32, 4, 2.0, 0, 0, True, 1), (16, 3, 2.0, 1, 2, False, 2),
+                                                     (23, 5, 2.0, 0, 1, False, 1), (48, 6, 2.0, 1, 0, True, 2)])
 def test_wavelet_reduced(lib, L, N, lam, J0, spin, real, B, mode):
     plan = lib.Plan(L, N, lam, J0, spin=spin, reality=real, batch=B, precision=mode)
     flms = [synth.flm_random(L, synth.rng_for(801, b), spin=spin, reality=real) for b in range(B)]
