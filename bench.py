@@ -175,10 +175,20 @@ def cpu_baseline_sample():
 
 
 PRECISIONS = {"fp64": 0, "fp64_table": 0, "fp64_native": 3, "fp32_split": 1, "bf16": 2, "fp64_tc": 4}
-# kernels per contraction region of the launch trace: exponent pass + slicing pass + GEMM in
-# fp64_tc (every transform); one kernel in the float64 modes.  (The reduced modes, not a headline,
-# mix both: their wavelet contractions are operand prep + GEMM, their SHT one table kernel.)
-KERNELS_PER_CONTRACTION = {"fp64_tc": 3}
+
+
+def contraction_kernels_per_step(precision, nscales):
+    """Library kernels of the 2 (nscales + 2) contractions of one step (analysis + synthesis: the
+    SHT, the scaling transform and every wavelet scale, each once per direction): exponent pass +
+    slicing pass + GEMM on the sliced path (fp64_tc: every transform; the reduced modes: the SHT
+    and the scaling transform), operand preparation + GEMM for the reduced modes' wavelet scales,
+    one kernel in the float64 modes."""
+    if precision == "fp64_tc":
+        return 3 * 2 * (nscales + 2)
+    if precision in ("fp32_split", "bf16"):
+        return 3 * 2 * 2 + 2 * 2 * nscales
+    return 2 * (nscales + 2)
+
 # kernels of one azimuthal DFT by form (forward, inverse): 0 SIMT (one kernel); 1 direct tensor-core
 # GEMM (slicing prologue + GEMM); 2 prime-factor (forward: gamma-DFT prologue + tensor-core kernel;
 # inverse: column prologue + tensor-core kernel + gamma synthesis)
@@ -192,9 +202,11 @@ PRECISION_DOC = {
                   "colatitude quadrature folded into the forward tables) in float pairs; "
                   "compensated-float32 table contractions and DFTs",
     "fp32_split": "reduced: tcgen05 contractions on precomputed Wigner-d tiles, fp16 hi/lo operands "
-                  "(3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
+                  "(3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT and scaling transform "
+                  "float64-accurate (the fp64_tc kernels)",
     "bf16": "reduced: split-bf16, tcgen05 contractions on precomputed Wigner-d tiles, bf16 hi/lo tables "
-            "and data (3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT float64-accurate",
+            "and data (3 MMAs), float32 accumulation; plain float32 DFTs; spin SHT and scaling transform "
+            "float64-accurate (the fp64_tc kernels)",
     "fp64_tc": "float64 accuracy on the tensor cores: precomputed Wigner-d tables and the data cut into "
                "seven 7-bit integer slices (bf16), 28 slice products per K step summed exactly in float32 "
                "TMEM accumulators (error-free splitting); azimuthal DFTs on the tensor cores by the same "
@@ -619,12 +631,10 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "e2e": {"value": maps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 8),
                 "d2h_bytes_per_step": int(f.numel() * 8), "max_rel_err": e2e_err},
-        # the trace records one region per DFT and per contraction; a contraction region launches
-        # KERNELS_PER_CONTRACTION[precision] kernels of the library; every transform's forward and
-        # inverse DFT run once per step, with DFT_KERNELS[form] (forward, inverse) kernels each
-        "gpu_launches": int(sum(v[0] * KERNELS_PER_CONTRACTION.get(args.precision, 1)
-                                for k, v in trace.items() if k.startswith("wigner"))
-                            + args.steps * sum(DFT_KERNELS[fw][0] + DFT_KERNELS[iv][1] for fw, iv in dft_forms)),
+        # per step: the contractions' kernels (contraction_kernels_per_step) and every
+        # transform's forward and inverse DFT, with DFT_KERNELS[form] (forward, inverse) kernels
+        "gpu_launches": int(args.steps * (contraction_kernels_per_step(args.precision, plan.nscales)
+                                          + sum(DFT_KERNELS[fw][0] + DFT_KERNELS[iv][1] for fw, iv in dft_forms))),
     }
     if world == 1 and not args.no_cpu_baseline:
         dt, cerr = cpu_baseline_sample()

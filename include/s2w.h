@@ -70,7 +70,8 @@ typedef enum {
  * S2W_BF16         split-bf16: the same with bf16 hi + lo pairs for the tables and the data
  *                  (the products hi*hi, hi*lo, lo*hi per K step, float32 accumulation; 1e-3
  *                  target).
- *                  Both reduced modes keep the spin SHT Y, Y^-1 float64-accurate and
+ *                  Both reduced modes keep the spin SHT Y, Y^-1 and the scaling transform
+ *                  float64-accurate (on the sliced tensor-core kernels of S2W_FP64_TC) and
  *                  support L and the ring count <= 512 (S2W_EUNSUPPORTED above).
  * S2W_FP64_TC      float64 accuracy (1e-11 target) with every l-contraction on the tensor cores:
  *                  precomputed Wigner-d tables and the data cut into seven 7-bit integer slices
@@ -391,7 +392,8 @@ s2w_status s2w_batch_destroy(s2w_batch* batch);
  *   S2W_ETIMEOUT    a bounded mbarrier wait of a tensor-core kernel ran out (the kernel set the
  *                   word, let its own copies and MMAs in flight land, freed its tensor memory and
  *                   returned; the outputs of that call are undefined, the context stays usable);
- *   S2W_ENONFINITE  S2W_FP64_TC only: the exponent pass that reads every value before the
+ *   S2W_ENONFINITE  S2W_FP64_TC (and the reduced modes' SHT and scaling transform, which run
+ *                   on its kernels): the exponent pass that reads every value before the
  *                   tensor-core slicing met a NaN or Inf (in the input, or produced from it), so
  *                   the outputs of that call are not meaningful.  The other modes do not check and
  *                   propagate NaN and Inf to the outputs. */

@@ -218,7 +218,7 @@ size_t pix_bytes(const s2w_plan* P) { return P->real ? sizeof(double) : sizeof(d
 
 namespace s2w {
 int dft_form_used(const s2w_plan* P, const TransformSpec& t, bool fwd) {
-  if (!P->tcx) return kDftComp;
+  if (!P->tcx && t.tcx == nullptr) return kDftComp;   // the reduced modes' wavelet scales
   const int f = fwd ? t.dft_form_fwd : t.dft_form_inv;
   // the prime-factor kernel sums the digit-pair diagonals 0..6 only: plans that also sum
   // diagonal 7 (the ball's) take the direct form

@@ -177,6 +177,7 @@ __device__ void f_stage2(const FLayout& l, const float2* s2, int n1, int n2, int
       sr[u] = 0.f;
       si[u] = 0.f;
     }
+#pragma unroll 2
     for (int j = 0; j < l.h2; ++j) {
       const float2 a = A[j * l.Rp + r], b = B[j * l.Rp + r];
       const float4 c4 = cs[j * l.Q + qg], s4 = sn[j * l.Q + qg];
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(512) k_dftf_fwd(DftfArgs a) {
         hr[q] = w0.x;
         hi[q] = w0.y;
       }
+#pragma unroll 4
       for (int g = 1; g <= hg; ++g) {
         const float2 xp = f_pix(a.pix_in, REAL, base + g * ring + al);
         const float2 xm = f_pix(a.pix_in, REAL, base + (Ng - g) * ring + al);

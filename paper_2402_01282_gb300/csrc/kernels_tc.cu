@@ -6,7 +6,7 @@
 // the fp16 range; 22 bits per pair) and "bf16" (split-bf16, 16 bits per pair).
 //
 // Both directions are one GEMM per (m, n) pair: rows x 32 columns (16 maps x re/im), in K
-// chunks of 64:
+// chunks of 32:
 //   inverse  rows beta, K = l:   G[beta][map] = sum_l 2^8 d^l_mn(beta) * s F[l][map]
 //   forward  rows l, K = beta':  F[l][map]    = sum_b' 2^10 (M^T d^l_mn)(beta') * s G[beta'][map]
 // The forward tables carry the colatitude quadrature folded in (as the float64 table mode
@@ -16,14 +16,15 @@
 // k_tcp: the data operand of every (m, n) and 16-map chunk, prepared once in float32 (a
 // power-of-two scale per operand into the fp16 range, the hi/lo split) into a plan workspace.
 // k_tc_gemm: one CTA of 128 threads per (row tile of 128, m, n); thread 0 runs a two-stage
-// pipeline of bulk asynchronous copies (TMA engine, 40 KB per stage: table hi/lo + operand
-// hi/lo) and MMAs; 80 KB of shared memory lets two CTAs share an SM; every mbarrier wait is
-// bounded and a timeout sets the plan's error word.
+// pipeline of bulk asynchronous copies (TMA engine, 20 KB per stage: table hi/lo + operand
+// hi/lo) and MMAs; 40 KB of shared memory lets five CTAs share an SM, so that the short CTAs
+// (at most eight K chunks each) overlap one another's pipeline fill and epilogue; every
+// mbarrier wait is bounded and a timeout sets the plan's error word.
 //
 // Packed layouts (core matrices of 8 rows x 8 elements, K-major, no swizzle; see tc_sm100.cuh):
-//   table chunk (row tile t, K chunk c): 128 x 64 elements, element (r, k) at
-//     ((r / 8) * 8 + k / 8) * 64 + (r % 8) * 8 + k % 8, chunks ordered [t][c]
-//   operand chunk c: 32 x 64 elements, element (j, k) at ((j / 8) * 8 + k / 8) * 64 + (j % 8) * 8 + k % 8
+//   table chunk (row tile t, K chunk c): 128 x 32 elements, element (r, k) at
+//     ((r / 8) * 4 + k / 8) * 64 + (r % 8) * 8 + k % 8, chunks ordered [t][c]
+//   operand chunk c: 32 x 32 elements, element (j, k) at ((j / 8) * 4 + k / 8) * 64 + (j % 8) * 8 + k % 8
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -38,12 +39,15 @@ constexpr double kInvScale = 256.0;    // inverse tables hold 2^8 d
 constexpr double kFwdScale = 1024.0;   // forward tables hold 2^10 M^T d
 constexpr int kTcThreads = 128;
 constexpr int kTcN = 32;               // MMA N: 16 maps x (re, im)
-constexpr int kKc = 64;                // K chunk
+constexpr int kKc = 32;                // K chunk (the K extents are multiples of 64)
 constexpr int kTileElems = 128 * kKc;  // table chunk elements
 constexpr int kOpElems = kTcN * kKc;   // operand chunk elements
 constexpr uint32_t kWaitIter = 1u << 26;
 
-__device__ __forceinline__ int tile_index(int r, int k) { return ((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+constexpr uint32_t kSbo = (kKc / 8) * 128;   // bytes between 8-row core-matrix groups
+__device__ __forceinline__ int tile_index(int r, int k) {
+  return ((r >> 3) * (kKc / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
 
 // hi and lo of x in fp16 (FP16 = true) or bf16
 template <bool FP16>
@@ -214,6 +218,87 @@ __global__ void k_tcp(PrepArgs a) {
   }
 }
 
+// The same in one pass over the source: each thread holds its kTcpVpt values in registers
+// between the block maximum and the scaled write, and issues all of its loads before the first
+// use (the sources are read with a stride of a whole row, so the two-pass form waited on one
+// L2 or DRAM latency per value, twice).  MP = 2: a block prepares the operands of two adjacent
+// m (thread pairs read the two neighbouring complex values of one 32-byte sector instead of one
+// value per sector); thread t serves m0 + t % MP throughout.  TH * kTcpVpt >= MP * 32 K
+// (host-checked).
+constexpr int kTcpVpt = 32;
+template <bool FWD, bool FP16, int TH, int MP>
+__global__ void __launch_bounds__(TH) k_tcp1(PrepArgs a) {
+  __shared__ float red[TH / 32][MP];
+  __shared__ int kmax_s;
+  const int ni = blockIdx.y, q = blockIdx.z, sub = threadIdx.x % MP;
+  const int mi = blockIdx.x * MP + sub, nn = a.nvals[ni];
+  int Kmax = 0;
+#pragma unroll
+  for (int s = 0; s < MP; ++s) {
+    const int ms = blockIdx.x * MP + s;
+    const int kls = ms < a.Mc ? a.kl[ms * a.nact + ni] : 0;
+    Kmax = max(Kmax, kls == 0 ? 0 : (FWD ? a.Lk : kls));
+  }
+  if (Kmax == 0) return;
+  const int idx = mi * a.nact + ni;
+  const int kl = mi < a.Mc ? a.kl[idx] : 0;
+  const int K = kl == 0 ? 0 : (FWD ? a.Lk : kl);   // this thread's m
+  const int m = a.mlo + mi;
+  const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
+  const int total = kTcN * Kmax;                    // values per m
+  const int map0 = q * (kTcN / 2);
+  float v[kTcpVpt];
+#pragma unroll
+  for (int i = 0; i < kTcpVpt; ++i) {
+    const int e = threadIdx.x / MP + i * (TH / MP);
+    const int j = e / Kmax, k = e - j * Kmax;
+    v[i] = (e < total && k < K) ? prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0) : 0.f;
+  }
+  float mx = 0.f;
+#pragma unroll
+  for (int i = 0; i < kTcpVpt; ++i) mx = fmaxf(mx, fabsf(v[i]));
+  for (int o = 16; o >= MP; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) < MP) red[threadIdx.x >> 5][sub] = mx;
+  if (threadIdx.x == 0) kmax_s = Kmax;
+  __syncthreads();
+  // the write loop recomputes its indices from the shared copy of the extent, so that the load
+  // loop's addresses need not stay live across the barrier (they would double the registers)
+  const int Kw = kmax_s, totw = kTcN * Kw;
+  float bm = red[0][sub];
+  for (int w = 1; w < TH / 32; ++w) bm = fmaxf(bm, red[w][sub]);
+  if (K == 0) return;
+  const float sc = pow2_scale_f(bm);
+  if (threadIdx.x < MP) a.scale[(int64_t)q * a.Mc * a.nact + idx] = sc;
+  const int64_t base = (int64_t)q * a.qstride + (FWD ? (int64_t)idx * a.Lk * kTcN : a.off_i[idx] / a.Lb * kTcN);
+#pragma unroll
+  for (int i = 0; i < kTcpVpt; ++i) {
+    const int e = threadIdx.x / MP + i * (TH / MP);
+    const int j = e / Kw, k = e - j * Kw;
+    if (e < totw && k < K)
+      put_pair<FP16>(a.hi, a.lo, base + (int64_t)(k / kKc) * kOpElems + tile_index(j, k % kKc), v[i] * sc);
+  }
+}
+
+// operand preparation with the largest K extent kmax: the one-pass kernel where its registers
+// hold a block's values (two m per block up to K = 256), else the two-pass one
+template <bool FWD>
+void launch_tcp(const PrepArgs& pa, int Mc, int nact, int nq, int kmax, bool fp16, cudaStream_t st) {
+  const dim3 g1(Mc, nact, nq), g2((Mc + 1) / 2, nact, nq);
+  if (2 * kTcN * kmax <= 256 * kTcpVpt) {
+    if (fp16) k_tcp1<FWD, true, 256, 2><<<g2, 256, 0, st>>>(pa);
+    else k_tcp1<FWD, false, 256, 2><<<g2, 256, 0, st>>>(pa);
+  } else if (2 * kTcN * kmax <= 512 * kTcpVpt) {
+    if (fp16) k_tcp1<FWD, true, 512, 2><<<g2, 512, 0, st>>>(pa);
+    else k_tcp1<FWD, false, 512, 2><<<g2, 512, 0, st>>>(pa);
+  } else if (kTcN * kmax <= 512 * kTcpVpt) {
+    if (fp16) k_tcp1<FWD, true, 512, 1><<<g1, 512, 0, st>>>(pa);
+    else k_tcp1<FWD, false, 512, 1><<<g1, 512, 0, st>>>(pa);
+  } else {
+    if (fp16) k_tcp<FWD, true><<<g1, 256, 0, st>>>(pa);
+    else k_tcp<FWD, false><<<g1, 256, 0, st>>>(pa);
+  }
+}
+
 // ------------------------------------------------------------------ GEMM
 struct GemmArgs {
   const uint16_t *A_hi, *A_lo;
@@ -300,15 +385,15 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
         if (!ok) break;
         tc::fence_after_sync();
         const uint32_t A0 = tc::smem_u32(stage0 + s * kStageElems), A1 = A0 + kTileElems * 2u;
-        const uint32_t B0 = A1 + kTileElems * 2u, B1 = B0 + kOpElems * 2u;
+        const uint32_t B0 = A1 + kTileElems * 2u;   // operand hi, then lo one 32-row block further
         for (int ks = 0; ks < kKc / 16; ++ks) {
           const uint32_t o = (uint32_t)ks * 256u;
           const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
           // the operand's hi and lo tiles are adjacent 32-row blocks with one row-group stride: one
           // N = 64 MMA of the table's hi against both (hi*hi into columns 0..31, hi*lo into 32..63),
           // then lo*hi into columns 0..31; the epilogue adds the two halves
-          tc::mma_f16(tmem, tc::make_sdesc(A0 + o, 128, 1024), tc::make_sdesc(B0 + o, 128, 1024), a.idesc2, acc);
-          tc::mma_f16(tmem, tc::make_sdesc(A1 + o, 128, 1024), tc::make_sdesc(B0 + o, 128, 1024), a.idesc, 1);
+          tc::mma_f16(tmem, tc::make_sdesc(A0 + o, 128, kSbo), tc::make_sdesc(B0 + o, 128, kSbo), a.idesc2, acc);
+          tc::mma_f16(tmem, tc::make_sdesc(A1 + o, 128, kSbo), tc::make_sdesc(B0 + o, 128, kSbo), a.idesc, 1);
         }
         tc::mma_commit(&bar_mma[s]);
         if (c + 1 < nkc) {
@@ -363,7 +448,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(GemmArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
-constexpr size_t kGemmSmem = 2 * (2 * kTileElems + 2 * kOpElems) * sizeof(uint16_t);   // 80 KB
+constexpr size_t kGemmSmem = 2 * (2 * kTileElems + 2 * kOpElems) * sizeof(uint16_t);   // 40 KB
 
 PrepArgs prep_args(const s2w_plan* P, const TransformSpec& t, const TcTable& tab, int nr, int Mc, int mlo, int B) {
   PrepArgs a{};
@@ -454,9 +539,7 @@ cudaError_t launch_tc_inverse(const s2w_plan* P, const GridTables& g, const Tran
   pa.mlo_in = in.mlo;
   pa.mult = t.mult_inv;
   pa.qstride = tab.op_i;
-  dim3 pg(out.Mc, t.nact, nq);
-  if (fp16) k_tcp<false, true><<<pg, 256, 0, st>>>(pa);
-  else k_tcp<false, false><<<pg, 256, 0, st>>>(pa);
+  launch_tcp<false>(pa, out.Mc, t.nact, nq, (t.L + 63) / 64 * 64, fp16, st);   // inverse K extents: at most L rounded up to 64
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GemmArgs a = gemm_args(P, t, tab, out.nr, out.Mc, out.mlo, out.B, fp16);
@@ -483,9 +566,7 @@ cudaError_t launch_tc_forward(const s2w_plan* P, const GridTables& g, const Tran
   pa.kl = tab.klf;
   pa.G = in.G;
   pa.qstride = tab.op_f;
-  dim3 pg(in.Mc, t.nact, nq);
-  if (fp16) k_tcp<true, true><<<pg, 256, 0, st>>>(pa);
-  else k_tcp<true, false><<<pg, 256, 0, st>>>(pa);
+  launch_tcp<true>(pa, in.Mc, t.nact, nq, tab.Lk, fp16, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GemmArgs a = gemm_args(P, t, tab, in.nr, in.Mc, in.mlo, in.B, fp16);

@@ -343,9 +343,9 @@ s2w_status alloc_dev(s2w_plan* P, size_t n, T** d, std::string& err) {
 
 // Reduced-precision modes: packed Wigner-d tiles for the wavelet-scale Wigner transforms
 // (cached per band-limit and n set, so scales with equal (L_j, N_j) share them) and packed
-// quadrature matrices.  The spin SHT and the scaling transform stay on the float64-accurate
-// path: Y f sets the accuracy of every small high-l coefficient the top scales see, and with a
-// steep spectrum a 16-bit quantisation relative to f_00 would swamp them.
+// quadrature matrices.  The spin SHT and the scaling transform stay float64-accurate (the
+// sliced tensor-core kernels): Y f sets the accuracy of every small high-l coefficient the top
+// scales see, and with a steep spectrum a 16-bit quantisation relative to f_00 would swamp them.
 s2w_status make_tab(s2w_plan* P, const TransformSpec& t, TabTable* tab, cudaStream_t st, std::string& err);
 
 // Tensor-core tables of the reduced modes for every wavelet scale (specs with the same (L, n
@@ -423,13 +423,14 @@ s2w_status build_tc_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
   return S2W_OK;
 }
 
-// S2W_FP64_TC: sliced tables for every transform (the SHT, the scaling function and the
-// wavelet scales; specs with the same (L, n values) share one), packed from temporary
-// float-pair tables (make_tab) that are freed once packed; plus the data-slice workspace.
-s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+// Sliced tables for the SHT, the scaling function and (S2W_FP64_TC: with_wavelets) the wavelet
+// scales; specs with the same (L, n values) share one.  Packed from temporary float-pair tables
+// (make_tab) that are freed once packed; plus the data-slice workspace.
+s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err, bool with_wavelets) {
   std::map<std::tuple<int, std::vector<int>, int>, TcxTable*> cache;
   std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
-  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+  if (with_wavelets)
+    for (TransformSpec& t : P->wav_t) specs.push_back(&t);
   int64_t op_max = 0, fx_max = 0;
   const int nq = (P->p.batch + 15) / 16;
   for (TransformSpec* t : specs) {
@@ -502,14 +503,17 @@ s2w_status build_tcx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
   return S2W_OK;
 }
 
-// S2W_FP64_TC: sliced twiddle tables of the tensor-core DFTs for every transform whose carried n
+// Sliced twiddle tables of the tensor-core DFTs for the SHT, the scaling function and
+// (S2W_FP64_TC: with_wavelets) the wavelet scales and raw Wigner transforms, where the carried n
 // values fit (dftx_shape_ok): per band-limit one inverse table (scale 1) and one forward table
 // per normalisation (2 pi/(2L-1)) gscale, shared between specs; plus the data-slice workspace.
-s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err) {
+s2w_status build_dftx_tables(s2w_plan* P, cudaStream_t st, std::string& err, bool with_wavelets) {
   std::map<std::pair<int, double>, DftxTable*> cache;
   std::vector<TransformSpec*> specs = {&P->sht, &P->scal_t};
-  for (TransformSpec& t : P->wav_t) specs.push_back(&t);
-  for (TransformSpec& t : P->raw_t) specs.push_back(&t);
+  if (with_wavelets) {
+    for (TransformSpec& t : P->wav_t) specs.push_back(&t);
+    for (TransformSpec& t : P->raw_t) specs.push_back(&t);
+  }
   int64_t ops = 0, fx = 0;
   auto table = [&](int L, double scale, const DftxTable** out) -> s2w_status {
     auto key = std::make_pair(L, scale);
@@ -760,10 +764,13 @@ s2w_status build_plan(const s2w_params& p, cudaStream_t st, s2w_plan* P, std::st
     S2W_TRY(build_spec(P, st, P->raw_t[sc], Lj, Nj, gidx[Lj], all, ri, rf, 2.0 * kPi / (2.0 * Nj - 1.0), err));
   }
 
+  // the reduced modes run their SHT and scaling transform on the float64-accurate sliced
+  // tensor-core kernels of S2W_FP64_TC (contractions and DFTs), the wavelet scales on the
+  // reduced-precision tables
   if (P->tensor) S2W_TRY(build_tc_tables(P, st, err));
-  if (P->tcx) S2W_TRY(build_tcx_tables(P, st, err));
-  if (P->tcx) S2W_TRY(build_dftx_tables(P, st, err));
-  if (P->precompute || P->tensor) S2W_TRY(build_tab_tables(P, st, err, !P->tensor));
+  if (P->tcx || P->tensor) S2W_TRY(build_tcx_tables(P, st, err, P->tcx));
+  if (P->tcx || P->tensor) S2W_TRY(build_dftx_tables(P, st, err, P->tcx));
+  if (P->precompute) S2W_TRY(build_tab_tables(P, st, err, true));
 
   // workspaces
   const int64_t B = p.batch;

@@ -103,11 +103,13 @@ s2w_status s2w_plan_autotune(s2w_plan* P, void* stream) {
       const bool fwd = dir == 0;
       int& form = fwd ? t->dft_form_fwd : t->dft_form_inv;
       int& threads = fwd ? t->dft_threads_fwd : t->dft_threads_inv;
+      // sliced transforms: S2W_FP64_TC's, and the reduced modes' SHT and scaling transform
+      const bool sliced = P->tcx || t->tcx != nullptr;
       std::vector<int> forms = {kDftComp};
-      if (P->tcx && (fwd ? (const void*)t->dftx_fwd : (const void*)t->dftx_inv) != nullptr) forms.push_back(kDftGemm);
-      if (P->tcx && !P->slice_diag7 && (fwd ? (const void*)t->dftp_fwd : (const void*)t->dftp_inv) != nullptr)
+      if (sliced && (fwd ? (const void*)t->dftx_fwd : (const void*)t->dftx_inv) != nullptr) forms.push_back(kDftGemm);
+      if (sliced && !P->slice_diag7 && (fwd ? (const void*)t->dftp_fwd : (const void*)t->dftp_inv) != nullptr)
         forms.push_back(kDftPfa);
-      if (!P->tcx) forms = {kDftAuto};
+      if (!sliced) forms = {kDftAuto};
       float best = 1e30f;
       int pick_th = threads, pick_form = form;
       for (int fm : forms)
@@ -171,11 +173,11 @@ s2w_status s2w_plan_set_dft_forms(s2w_plan* P, int transform, int fwd, int inv) 
     const void* tab = code == 2 ? (f ? (const void*)t.dftp_fwd : (const void*)t.dftp_inv)
                                 : (f ? (const void*)t.dftx_fwd : (const void*)t.dftx_inv);
     if (code == 2 && P->slice_diag7) return -1;   // the prime-factor kernel sums diagonals 0..6 only
-    return (P->tcx && tab != nullptr) ? (code == 2 ? kDftPfa : kDftGemm) : -1;
+    return ((P->tcx || t.tcx != nullptr) && tab != nullptr) ? (code == 2 ? kDftPfa : kDftGemm) : -1;
   };
   const int ff = to_form(fwd, true), fi = to_form(inv, false);
   if (ff < 0 || fi < 0)
-    return record_error(S2W_EUNSUPPORTED, "that DFT form has no tables for this transform (S2W_FP64_TC only)");
+    return record_error(S2W_EUNSUPPORTED, "that DFT form has no tables for this transform (S2W_FP64_TC, and the SHT and scaling transform of the reduced modes)");
   t.dft_form_fwd = ff;
   t.dft_form_inv = fi;
   return S2W_OK;
