@@ -80,13 +80,14 @@ __device__ __forceinline__ void put_pair_d(uint16_t* hi, uint16_t* lo, int64_t i
 // float64 -> float without the float64 pipe (hi part of the integer split, 2^-24 relative)
 __device__ __forceinline__ float to_f(double x) { return split1_bits(x).x; }
 
-// float -> float64 with integer operations (exact for normal floats; subnormals give 0)
+// float -> float64 with integer operations (exact for normal floats; subnormals give 0; Inf and
+// NaN carried over)
 __device__ __forceinline__ double f2d(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int e = (u >> 23) & 0xFFu;
   if (e == 0u) return 0.0;
   const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+                               ((unsigned long long)(e == 0xFFu ? 0x7FFu : e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)b);
 }
 

@@ -89,3 +89,36 @@ def test_nonfinite_input_is_reported(lib, value):
         plan.check()
     assert ei.value.status == 6
     plan.close()
+
+
+@pytest.mark.parametrize("value", [float("nan"), float("inf")])
+@pytest.mark.parametrize("mode", [1, 2])   # S2W_FP32_SPLIT, S2W_BF16
+def test_reduced_modes_report_nonfinite_input(lib, mode, value):
+    """The reduced modes run their SHT on the sliced float64-accurate kernels, whose exponent
+    pass reads every input value: a non-finite pixel is reported, and a clean map is not.  A
+    non-finite wavelet coefficient passes the reduced-precision scale as a non-finite value (the
+    integer float64 <-> float32 conversions carry Inf and NaN over) and is reported by the
+    exponent pass of the final inverse SHT."""
+    import torch
+    L, N, J0, B = 32, 4, 1, 2
+    plan = lib.Plan(L, N, 2.0, J0, reality=True, batch=B, precision=mode)
+    f = _map(L, B, 612)
+    bad = f.copy()
+    bad[1, 5, 9] = value
+    wav, scal = plan.empty_wav(), plan.empty_scal()
+    plan.forward(torch.from_numpy(bad).cuda(), wav, scal)
+    with pytest.raises(lib.S2WError) as ei:
+        plan.check()
+    assert ei.value.status == 6, str(ei.value)
+    plan.forward(torch.from_numpy(f).cuda(), wav, scal)
+    plan.check()
+    wbad = wav.clone()
+    wbad[0, wbad.shape[1] - 5] = value   # the top wavelet scale of map 0
+    f2 = plan.empty_map()
+    plan.inverse(wbad, scal, f2)
+    with pytest.raises(lib.S2WError) as ei:
+        plan.check()
+    assert ei.value.status == 6, str(ei.value)
+    plan.inverse(wav, scal, f2)
+    plan.check()
+    plan.close()
