@@ -246,14 +246,23 @@ __global__ void __launch_bounds__(TH) k_tcp1(PrepArgs a) {
   const int K = kl == 0 ? 0 : (FWD ? a.Lk : kl);   // this thread's m
   const int m = a.mlo + mi;
   const int l0 = max(abs(m), abs(nn)), l0a = l0 & ~7;
-  const int total = kTcN * Kmax;                    // values per m
   const int map0 = q * (kTcN / 2);
+  // value i of this thread is element e = tq + i TH/MP = j Kmax + k of its m; (j, k) are stepped
+  // instead of divided (e < total exactly when j < kTcN)
+  const int tq = threadIdx.x / MP, sj = (TH / MP) / Kmax, sk = (TH / MP) - sj * Kmax;
   float v[kTcpVpt];
+  {
+    int j = tq / Kmax, k = tq - j * Kmax;
 #pragma unroll
-  for (int i = 0; i < kTcpVpt; ++i) {
-    const int e = threadIdx.x / MP + i * (TH / MP);
-    const int j = e / Kmax, k = e - j * Kmax;
-    v[i] = (e < total && k < K) ? prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0) : 0.f;
+    for (int i = 0; i < kTcpVpt; ++i) {
+      v[i] = (j < kTcN && k < K) ? prep_value<FWD>(a, mi, ni, m, l0, l0a, j, k, map0) : 0.f;
+      k += sk;
+      j += sj;
+      if (k >= Kmax) {
+        k -= Kmax;
+        ++j;
+      }
+    }
   }
   float mx = 0.f;
 #pragma unroll
@@ -264,19 +273,24 @@ __global__ void __launch_bounds__(TH) k_tcp1(PrepArgs a) {
   __syncthreads();
   // the write loop recomputes its indices from the shared copy of the extent, so that the load
   // loop's addresses need not stay live across the barrier (they would double the registers)
-  const int Kw = kmax_s, totw = kTcN * Kw;
+  const int Kw = kmax_s, swj = (TH / MP) / Kw, swk = (TH / MP) - swj * Kw;
   float bm = red[0][sub];
   for (int w = 1; w < TH / 32; ++w) bm = fmaxf(bm, red[w][sub]);
   if (K == 0) return;
   const float sc = pow2_scale_f(bm);
   if (threadIdx.x < MP) a.scale[(int64_t)q * a.Mc * a.nact + idx] = sc;
   const int64_t base = (int64_t)q * a.qstride + (FWD ? (int64_t)idx * a.Lk * kTcN : a.off_i[idx] / a.Lb * kTcN);
+  int j = tq / Kw, k = tq - j * Kw;
 #pragma unroll
   for (int i = 0; i < kTcpVpt; ++i) {
-    const int e = threadIdx.x / MP + i * (TH / MP);
-    const int j = e / Kw, k = e - j * Kw;
-    if (e < totw && k < K)
+    if (j < kTcN && k < K)
       put_pair<FP16>(a.hi, a.lo, base + (int64_t)(k / kKc) * kOpElems + tile_index(j, k % kKc), v[i] * sc);
+    k += swk;
+    j += swj;
+    if (k >= Kw) {
+      k -= Kw;
+      ++j;
+    }
   }
 }
 
